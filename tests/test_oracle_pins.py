@@ -1,0 +1,308 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by
+mathematics (no GPU).  Each test names what it pins.
+
+Section II-A (Eq. 1-2) defines the decomposition; the oracle follows it level
+by level.  These tests check it against an independent dense statement, closed
+forms, invariants and the hand-worked 1D example of Fig. 2.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import dense
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_coords(rng, shape):
+    out = []
+    for n in shape:
+        inner = np.sort(rng.uniform(0.0, 1.0, n - 2))
+        out.append(np.concatenate([[0.0], inner, [1.0]]))
+    return out
+
+
+def _relmax(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+# ---------------------------------------------------------------- worked example
+
+def test_worked_example_1d_fig2():
+    """Fig. 2 function y = x^2-5x+6 on x = 0..4, two levels, worked by hand."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "worked_example_1d.txt"))
+            if l.strip() and not l.startswith("#")]
+    x, u, want = (np.array([float(v) for v in r]) for r in rows)
+    got = oracle.decompose(u, coords=[x])
+    assert np.array_equal(got, want)
+    # the Thomas divisions round (1/3-type pivots), so the way back is exact
+    # only to FP64 rounding
+    np.testing.assert_allclose(oracle.recompose(want, coords=[x]), u, rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("shape", [(17,), (9, 17), (9, 5, 17)])
+def test_quadratic_closed_form(shape):
+    """u = sum_k x_k^2: the finest coefficient at a node odd in the set S of
+    dimensions is -sum_{k in S} h_k^2 (multilinear interpolation of x^2)."""
+    coords = [np.arange(n) * (0.5 + k) for k, n in enumerate(shape)]
+    h = [c[1] - c[0] for c in coords]
+    u = np.zeros(shape)
+    for k, c in enumerate(coords):
+        s = [1] * len(shape)
+        s[k] = shape[k]
+        u = u + (c ** 2).reshape(s)
+    out = oracle.decompose(u, nlevels=1, coords=coords)
+    want = np.zeros(shape)
+    any_odd = np.zeros(shape, dtype=bool)
+    for k, n in enumerate(shape):
+        s = [1] * len(shape)
+        s[k] = n
+        odd_k = (np.arange(n) % 2 == 1).reshape(s)
+        want = want - np.where(odd_k, h[k] ** 2, 0.0)
+        any_odd = any_odd | odd_k
+    np.testing.assert_allclose(out[any_odd], want[any_odd], rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("shape,l0", [((33,), 2), ((17, 9), 1), ((9, 9, 17), 1), ((17, 17, 9), 0)])
+def test_piecewise_multilinear_input_has_zero_finer_coefficients(shape, l0):
+    """u piecewise multilinear on N_{l0}: every coefficient above level l0 is
+    exactly zero and the N_{l0} values come out as the l0-level
+    decomposition of the coarse data (dyadic values keep it exact)."""
+    rng = np.random.default_rng(3)
+    L = oracle.max_levels(shape)
+    stride = 1 << (L - l0)
+    cshape = tuple((n - 1) // stride + 1 for n in shape)
+    coarse = rng.integers(-8, 9, size=cshape).astype(np.float64)
+    # exact dyadic prolongation on the uniform grid, one dimension at a time
+    u = coarse
+    for k in range(len(shape)):
+        for _ in range(L - l0):
+            n = u.shape[k]
+            new_shape = list(u.shape)
+            new_shape[k] = 2 * n - 1
+            v = np.zeros(new_shape)
+            sl = [slice(None)] * len(shape)
+            sl[k] = slice(0, None, 2)
+            v[tuple(sl)] = u
+            a = [slice(None)] * len(shape)
+            b = [slice(None)] * len(shape)
+            o = [slice(None)] * len(shape)
+            a[k] = slice(0, -1)
+            b[k] = slice(1, None)
+            o[k] = slice(1, None, 2)
+            v[tuple(o)] = 0.5 * (u[tuple(a)] + u[tuple(b)])
+            u = v
+    assert u.shape == shape
+    out = oracle.decompose(u, nlevels=L)
+    idx = np.ix_(*[np.arange(0, n, stride) for n in shape])
+    rest = np.ones(shape, dtype=bool)
+    rest[idx] = False
+    assert np.all(out[rest] == 0.0)
+    want = oracle.decompose(coarse, nlevels=l0) if l0 > 0 else coarse
+    assert np.array_equal(out[idx], want)
+
+
+def test_constant_input():
+    """A constant field: coarsest values equal the constant, all coefficients 0."""
+    u = np.full((9, 17, 33), 2.5)
+    out = oracle.decompose(u)
+    stride = 1 << oracle.max_levels(u.shape)
+    idx = np.ix_(*[np.arange(0, n, stride) for n in u.shape])
+    assert np.all(out[idx] == 2.5)
+    rest = np.ones(u.shape, dtype=bool)
+    rest[idx] = False
+    assert np.all(out[rest] == 0.0)
+
+
+# ---------------------------------------------------------------- dense brute force
+
+@pytest.mark.parametrize("shape", [(33,), (17, 9), (9, 9, 9), (5, 9, 17)])
+@pytest.mark.parametrize("uniform", [True, False])
+@pytest.mark.parametrize("partial", [False, True])
+def test_matches_dense_projections(shape, uniform, partial):
+    """Whole decomposition equals the global-projection statement of Eq. 1:
+    level-l coefficients (I - Pi_{l-1}) Q_l u, coarsest values Q_0 u, with Q_l
+    from dense Gram systems (no recursion, no Thomas, no stencils)."""
+    rng = np.random.default_rng(11)
+    coords = ([oracle.uniform_coords(n) for n in shape] if uniform
+              else _rand_coords(rng, shape))
+    L = oracle.max_levels(shape)
+    if partial:
+        L = max(1, L - 1)
+    u = rng.standard_normal(shape)
+    got = oracle.decompose(u, nlevels=L, coords=coords)
+    want = dense.decompose(u, coords, L)
+    assert _relmax(got, want) < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(33,), (9, 17), (9, 9, 9)])
+def test_projection_orthogonality(shape):
+    """u - Q_l u is L2-orthogonal to V_l at every level (Section II-A-2)."""
+    rng = np.random.default_rng(5)
+    coords = _rand_coords(rng, shape)
+    L = oracle.max_levels(shape)
+    u = rng.standard_normal(shape)
+    G_L = dense._kron([dense.gram_1d(x) for x in coords])
+    for l in range(L - 1, -1, -1):
+        part = oracle.decompose(u, nlevels=L - l, coords=coords)
+        idx = [dense.level_index(len(x), L, l) for x in coords]
+        q = part[np.ix_(*idx)]
+        B = dense._kron([dense.hat_values(x, x[i]) for x, i in zip(coords, idx)])
+        resid = B.T @ (G_L @ (u.reshape(-1) - B @ q.reshape(-1)))
+        scale = np.abs(B.T @ (G_L @ u.reshape(-1))).max()
+        assert np.abs(resid).max() < 1e-12 * scale
+
+
+def test_separable_product_is_outer_product():
+    """For u = a(x) b(y) c(z), Q_l is a tensor product, so the N_l values of
+    the 3D decomposition are the outer product of the 1D ones."""
+    rng = np.random.default_rng(8)
+    shape = (9, 17, 33)
+    coords = _rand_coords(rng, shape)
+    fac = [rng.standard_normal(n) for n in shape]
+    u = np.einsum("i,j,k->ijk", *fac)
+    L = oracle.max_levels(shape)
+    for k in range(1, L + 1):
+        full = oracle.decompose(u, nlevels=k, coords=coords)
+        ones = [oracle.decompose(f, nlevels=k, coords=[c]) for f, c in zip(fac, coords)]
+        stride = 1 << k
+        idx = [np.arange(0, n, stride) for n in shape]
+        want = np.einsum("i,j,k->ijk", *[o[i] for o, i in zip(ones, idx)])
+        assert _relmax(full[np.ix_(*idx)], want) < 1e-12
+
+
+# ---------------------------------------------------------------- invariants
+
+def test_linearity():
+    rng = np.random.default_rng(2)
+    shape = (17, 9, 17)
+    coords = _rand_coords(rng, shape)
+    a, b = rng.standard_normal(shape), rng.standard_normal(shape)
+    lhs = oracle.decompose(2.5 * a - 0.75 * b, coords=coords)
+    rhs = 2.5 * oracle.decompose(a, coords=coords) - 0.75 * oracle.decompose(b, coords=coords)
+    assert _relmax(lhs, rhs) < 1e-13
+
+
+def test_coordinate_scaling_and_shift_invariance():
+    """Scaling or shifting one axis rescales M_l and M_{l-1} alike and leaves
+    interpolation weights unchanged, so the result is invariant."""
+    rng = np.random.default_rng(4)
+    shape = (9, 17, 33)
+    coords = _rand_coords(rng, shape)
+    u = rng.standard_normal(shape)
+    base = oracle.decompose(u, coords=coords)
+    moved = [coords[0] * 3.7 + 1.0, coords[1], coords[2] * 0.01]
+    assert _relmax(oracle.decompose(u, coords=moved), base) < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(65,), (33, 17), (17, 9, 33), (9, 9, 5)])
+@pytest.mark.parametrize("uniform", [True, False])
+def test_round_trip(shape, uniform):
+    """recompose(decompose(u)) == u to FP64 rounding (Section II-A: recomposition
+    runs the same stages in reverse)."""
+    rng = np.random.default_rng(6)
+    coords = ([oracle.uniform_coords(n) for n in shape] if uniform
+              else _rand_coords(rng, shape))
+    u = rng.standard_normal(shape)
+    for L in range(0, oracle.max_levels(shape) + 1):
+        back = oracle.recompose(oracle.decompose(u, nlevels=L, coords=coords),
+                                nlevels=L, coords=coords)
+        assert _relmax(back, u) < 1e-14 * max(1, L)
+
+
+# ---------------------------------------------------------------- adjoints
+
+def _dense_map(fn, shape, coords):
+    n = int(np.prod(shape))
+    D = np.zeros((n, n))
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        D[:, i] = fn(e.reshape(shape), coords=coords).reshape(-1)
+    return D
+
+
+@pytest.mark.parametrize("shape", [(17,), (9, 5), (5, 5, 9)])
+def test_adjoints_are_dense_transposes(shape):
+    rng = np.random.default_rng(9)
+    coords = _rand_coords(rng, shape)
+    D = _dense_map(oracle.decompose, shape, coords)
+    Dt = _dense_map(oracle.decompose_adjoint, shape, coords)
+    assert np.abs(D.T - Dt).max() < 1e-13 * np.abs(D).max()
+    R = _dense_map(oracle.recompose, shape, coords)
+    Rt = _dense_map(oracle.recompose_adjoint, shape, coords)
+    assert np.abs(R.T - Rt).max() < 1e-13 * np.abs(R).max()
+    assert np.abs(R @ D - np.eye(D.shape[0])).max() < 1e-13
+
+
+def test_adjoint_dot_products():
+    """|<Dx, y> - <x, D^T y>| <= 1e-12 ||Dx|| ||y|| on a 17^3 grid."""
+    rng = np.random.default_rng(10)
+    shape = (17, 17, 17)
+    coords = _rand_coords(rng, shape)
+    x, y = rng.standard_normal(shape), rng.standard_normal(shape)
+    for fwd, adj in ((oracle.decompose, oracle.decompose_adjoint),
+                     (oracle.recompose, oracle.recompose_adjoint)):
+        Dx = fwd(x, coords=coords)
+        lhs = np.vdot(Dx, y)
+        rhs = np.vdot(x, adj(y, coords=coords))
+        assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(Dx) * np.linalg.norm(y)
+    back = oracle.recompose_adjoint(oracle.decompose_adjoint(y, coords=coords), coords=coords)
+    assert _relmax(back, y) < 1e-13
+
+
+# ---------------------------------------------------------------- line operators
+
+def _line_matrix(fn, n_in, n_out, *args):
+    A = np.zeros((n_out, n_in))
+    for i in range(n_in):
+        e = np.zeros(n_in)
+        e[i] = 1.0
+        A[:, i] = fn(*args, e)
+    return A
+
+
+def test_mass_matrix_is_six_times_gram():
+    """The oracle's M is 6x the L2 Gram matrix of the hat functions (exact
+    Gauss quadrature), Section III-A-2."""
+    rng = np.random.default_rng(12)
+    x = _rand_coords(rng, (23,))[0]
+    M = _line_matrix(oracle.line_mass, 23, 23, x)
+    assert np.abs(M - 6.0 * dense.gram_1d(x)).max() < 1e-14
+
+
+def test_galerkin_identity_and_transfer():
+    """P^T M_l P = M_{l-1} (nested hat functions); R = P^T."""
+    rng = np.random.default_rng(13)
+    xf = _rand_coords(rng, (33,))[0]
+    xc = xf[::2]
+    P = _line_matrix(oracle.line_prolong, 17, 33, xf)
+    R = _line_matrix(oracle.line_restrict, 33, 17, xf)
+    Mf = _line_matrix(oracle.line_mass, 33, 33, xf)
+    Mc = _line_matrix(oracle.line_mass, 17, 17, xc)
+    assert np.abs(R - P.T).max() == 0.0
+    assert np.abs(P.T @ Mf @ P - Mc).max() < 1e-14 * np.abs(Mc).max()
+
+
+def test_prolongation_reproduces_linear_functions():
+    """P interpolates exactly: linear data on N_{l-1} stays linear on N_l."""
+    rng = np.random.default_rng(14)
+    xf = _rand_coords(rng, (41,))[0]
+    out = oracle.line_prolong(xf, 3.0 * xf[::2] - 1.25)
+    np.testing.assert_allclose(out, 3.0 * xf - 1.25, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(out, dense.hat_values(xf, xf[::2]) @ (3.0 * xf[::2] - 1.25),
+                               rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [2, 3, 17, 257])
+def test_thomas_matches_dense_solve(n):
+    rng = np.random.default_rng(15)
+    x = _rand_coords(rng, (n,))[0] if n > 2 else np.array([0.0, 0.7])
+    f = rng.standard_normal(n)
+    M = _line_matrix(oracle.line_mass, n, n, x)
+    z = oracle.line_mass_solve(x, f)
+    np.testing.assert_allclose(z, np.linalg.solve(M, f), rtol=1e-12, atol=1e-12)
