@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Throughput of the multilevel decomposition + recomposition on GB300.
+
+Workload: one 513^3 FP32 field (seeded sinusoid sum plus noise, 12 modes), the
+full 9-level decomposition followed by the full recomposition.  A step is one
+decompose + one recompose of the resident field.  The metric is algorithmic
+HBM bytes per second:
+
+  decompose level l:   2 M_l S            (read and write the level's nodes)
+  recompose level l:   (3 M_l - M_{l-1}) S (coefficients read twice, coarse
+                                            values read, level written)
+
+summed over l = L..1, divided by the time of the step (M_l = nodes of level
+l, S = bytes per element).  The field (540 MB) is larger than the 129 MB L2,
+so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank refactors its own field (independent partitions,
+weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SHAPE = (513, 513, 513)
+N_MODES = 12
+SEED = 2
+KIND_NAMES = {0: "restrict_dec", 1: "restrict_rec", 2: "solve", 3: "solve_fused",
+              4: "place_odd_rows", 5: "interp", 6: "place_even_rows"}
+
+
+def level_nodes(shape, L):
+    """M_l for l = L..0 (index 0 = finest)."""
+    out = []
+    for j in range(L + 1):
+        s = 1 << j
+        m = 1
+        for n in shape:
+            m *= (n - 1) // s + 1
+        out.append(m)
+    return out
+
+
+def algorithmic_bytes(shape, L, S):
+    M = level_nodes(shape, L)
+    dec = sum(2 * M[j] * S for j in range(L))
+    rec = sum((3 * M[j] - M[j + 1]) * S for j in range(L))
+    return dec, rec
+
+
+def kernel_bytes(kind, shape, S, SW):
+    """Compulsory bytes of one finest-level launch of a kernel kind."""
+    M = level_nodes(shape, 1)
+    Mf, Mc = M[0], M[1]
+    n = list(shape)
+    m = [(k - 1) // 2 + 1 for k in n]
+    even_rows_nodes = m[0] * m[1] * n[2]           # nodes on rows even in dims 0 and 1
+    return {
+        0: Mf * S + 2 * Mc * SW,                   # read level, write F and V
+        1: Mf * S + 2 * Mc * SW,                   # read level, write F and V
+        2: 2 * Mc * SW,                            # read + write F
+        3: 3 * Mc * SW,                            # read F, read + write V
+        4: 2 * (Mf - even_rows_nodes) * S,         # read + write the odd rows
+        5: 2 * Mf * S + Mc * SW,                   # read coefficients + V, write level
+        6: 2 * even_rows_nodes * S + Mc * SW,      # read + write even rows, read V
+    }[kind]
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2007_04457_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_name):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = kernel_source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel_name and parts[1] == cur:
+            return float(parts[2])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The oracle (plain FP64 CPU code) on the host cores, same metric."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2007_04457_gb300 import synth
+
+    n = 129
+    shape = (n, n, n)
+    L = 7
+    u = synth.sinusoid_field(shape, N_MODES, SEED, dtype=np.float32).astype(np.float64)
+    dec_b, rec_b = algorithmic_bytes(shape, L, 4)
+    for _ in range(args.warmup):
+        oracle.recompose(oracle.decompose(u))
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.recompose(oracle.decompose(u))
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = (dec_b + rec_b) * args.steps / total / 1e9
+    line = {
+        "impl": "reference", "metric": "decompose+recompose GB/s (algorithmic bytes) at 513^3 FP32",
+        "value": value, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "513^3 FP32 decompose+recompose, 9 levels",
+                   "sample": "129^3 sub-grid of the same generator per step, 7 levels"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "129^3, FP64 oracle, one decompose+recompose per step"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample():
+    """Oracle on a bounded sample (257^3 sub-grid, FP64, one thread)."""
+    import numpy as np
+
+    import oracle
+    from paper_2007_04457_gb300 import synth
+
+    n = 257
+    shape = (n, n, n)
+    u = synth.sinusoid_field(shape, N_MODES, SEED, dtype=np.float32).astype(np.float64)
+    dec_b, rec_b = algorithmic_bytes(shape, 8, 4)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.recompose(oracle.decompose(u))
+        reps += 1
+        if time.perf_counter() - t0 > 8.0 or reps >= 3:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": (dec_b + rec_b) * reps / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"257^3 sub-grid of the same generator, FP64 oracle, {reps} decompose+recompose"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    from paper_2007_04457_gb300 import mgard, synth
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    plan = mgard.Plan(SHAPE, dtype="f32")
+    L = plan.levels
+    S = 4
+    u = synth.sinusoid_field_torch(SHAPE, N_MODES, SEED + rank, dev, torch.float32)
+    ws = plan.workspace(dev)
+    stream = torch.cuda.current_stream(dev)
+    dec_b, rec_b = algorithmic_bytes(SHAPE, L, S)
+
+    def step():
+        plan.decompose(u, ws, stream)
+        plan.recompose(u, ws, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: whole steps, with event pairs around the finest-level kernels
+    mgard.mgard_profile_enable(plan.handle, 1)
+    mgard.mgard_profile_read(plan.handle)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms)
+    prof = [(KIND_NAMES[k], k, lv, c, t) for k, lv, c, t in mgard.mgard_profile_read(plan.handle)]
+    mgard.mgard_profile_enable(plan.handle, 0)
+
+    value = world * (dec_b + rec_b) * args.steps / (ms / 1e3) / 1e9
+    peak, peak_src = measured_peak()
+    top = max(prof, key=lambda r: r[4]) if prof else None
+    roof = None
+    if top is not None:
+        name, kind, lvl, c, t = top
+        per_launch_ms = t / c
+        kb = kernel_bytes(kind, SHAPE, S, S)
+        achieved = kb / (per_launch_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": f"{name} (finest level)", "achieved": achieved,
+                "peak": peak, "peak_source": f"{peak_src} hbm_gbs", "unit": "GB/s",
+                "frac": achieved / peak, "traffic": recorded_traffic(name),
+                "algorithmic_bytes_per_launch": kb, "ms_per_launch": per_launch_ms,
+                "share_of_step": t / ms}
+
+    finest_share = {f"{r[0]}": round(r[4] / ms, 4) for r in prof}
+
+    # FP64 alongside (same workload in double precision)
+    fp64 = None
+    if not args.no_fp64:
+        del u
+        torch.cuda.empty_cache()
+        plan64 = mgard.Plan(SHAPE, dtype="f64")
+        u64 = synth.sinusoid_field_torch(SHAPE, N_MODES, SEED + rank, dev, torch.float64)
+        ws64 = plan64.workspace(dev)
+        for _ in range(3):
+            plan64.decompose(u64, ws64, stream)
+            plan64.recompose(u64, ws64, stream)
+        torch.cuda.synchronize()
+        k64 = max(3, args.steps // 4)
+        e0.record(stream)
+        for _ in range(k64):
+            plan64.decompose(u64, ws64, stream)
+            plan64.recompose(u64, ws64, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = max_over_ranks(e0.elapsed_time(e1))
+        d64, r64 = algorithmic_bytes(SHAPE, L, 8)
+        fp64 = {"value": world * (d64 + r64) * k64 / (ms64 / 1e3) / 1e9, "unit": "GB/s",
+                "ms_per_step": ms64 / k64, "steps": k64}
+        del u64, ws64, plan64
+        torch.cuda.empty_cache()
+        u = synth.sinusoid_field_torch(SHAPE, N_MODES, SEED + rank, dev, torch.float32)
+
+    # end to end through the host-buffer entry points
+    e2e = None
+    if not args.no_e2e:
+        nbytes = u.numel() * S
+        h_in = torch.empty(SHAPE, dtype=torch.float32, pin_memory=True)
+        h_in.copy_(u.cpu())
+        h_mid = torch.empty_like(h_in).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        wsb = ws.numel()
+
+        def e2e_step():
+            mgard.mgard_decompose_host(plan.handle, h_in.data_ptr(), h_mid.data_ptr(), u.data_ptr(),
+                                       ws.data_ptr(), wsb, stream.cuda_stream)
+            mgard.mgard_recompose_host(plan.handle, h_mid.data_ptr(), h_out.data_ptr(), u.data_ptr(),
+                                       ws.data_ptr(), wsb, stream.cuda_stream)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        ke = max(3, args.steps // 4)
+        barrier()
+        e0.record(stream)
+        for _ in range(ke):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mse = max_over_ranks(e0.elapsed_time(e1))
+        e2e = {"value": world * (dec_b + rec_b) * ke / (mse / 1e3) / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes,
+               "ms_per_step": mse / ke, "steps": ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample()
+
+    launches = (plan.launches(False) + plan.launches(True)) * args.steps
+    if rank == 0:
+        line = {
+            "metric": "decompose+recompose GB/s (algorithmic bytes) at 513^3 FP32",
+            "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: 12-mode sinusoid sum + N(0,1e-3) noise, seeded",
+            "config": {"workload": "513^3 FP32 decompose+recompose, 9 levels, uniform grid",
+                       "shape": list(SHAPE), "levels": L,
+                       "l2": "inputs larger than L2 (540 MB field vs 129 MB L2), no flush",
+                       "parallelism": f"independent fields, {world} GPU(s)"},
+            "roofline": roof,
+            "finest_level_kernel_share": finest_share,
+            "fp64": fp64,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "gpu_launches": launches,
+            "kernel_source": kernel_source_hash(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

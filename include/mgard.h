@@ -1,0 +1,152 @@
+/*
+ * mgard.h -- C ABI of the GB300 (sm_103a) multilevel decomposition library.
+ *
+ * The library computes the multigrid-based hierarchical decomposition of a
+ * structured 1D-3D grid and its inverse (Chen et al., "Accelerating
+ * Multigrid-based Hierarchical Scientific Data Refactoring on GPUs",
+ * Section II-A, Eq. 1 and Eq. 2):
+ *
+ *   decomposition, level l = L .. 1:
+ *     coefficients  c = u - Pi_{l-1} u          on N_l \ N_{l-1}
+ *     load vector   f = R_l M_l vec(C_l)        C_l = c, zero on N_{l-1}
+ *     correction    M_{l-1} z = f               (tensor-product mass matrix)
+ *     update        u(N_{l-1}) += z
+ *   recomposition runs the same stages in reverse, level 1 .. L.
+ *
+ * Layout (Fig. 3): the field is a dense row-major array, dims[0] slowest.
+ * The transform is in place: after decomposition every node of
+ * N_l \ N_{l-1} holds its level-l coefficient and the nodes of N_0 hold the
+ * coarsest values.  N_l is the set of nodes whose indices are multiples of
+ * 2^(L-l) in every dimension.
+ *
+ * Shapes: 1 <= ndim <= 3; every dims[k] >= 2 with (dims[k]-1) divisible by
+ * 2^L.  Dimensions of size 1 are squeezed away.  nlevels = -1 selects the
+ * largest L allowed by the shape.
+ *
+ * Memory: every pointer named d_* is device memory owned by the caller; every
+ * pointer named h_* is host memory owned by the caller (pinned for
+ * asynchronous copies).  The plan owns its small device tables (interpolation
+ * weights, stencil and tridiagonal factors); nothing on the call path
+ * allocates.  Calls are asynchronous on the given stream (a cudaStream_t
+ * passed as void*, NULL = legacy default stream); the data and workspace must
+ * stay untouched until the stream reaches the call.  Functions never abort:
+ * they return a status, and mgard_last_error() gives a readable reason for
+ * the most recent failure on the calling thread.
+ */
+#ifndef MGARD_GB300_H
+#define MGARD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MGARD_API __attribute__((visibility("default")))
+#else
+#define MGARD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MGARD_OK = 0,
+    MGARD_ERR_INVALID_ARG = 1,       /* NULL pointer, bad enum, bad level count   */
+    MGARD_ERR_UNSUPPORTED_SHAPE = 2, /* dims not of the form k*2^L+1, > 3 dims    */
+    MGARD_ERR_WORKSPACE = 3,         /* workspace missing, misaligned or too small */
+    MGARD_ERR_CUDA = 4,              /* a CUDA runtime call or launch failed       */
+    MGARD_ERR_TIMEOUT = 5,           /* a bounded device-side wait ran out         */
+    MGARD_ERR_INTERNAL = 6
+} mgard_status;
+
+typedef enum {
+    MGARD_F32 = 0,       /* float storage, float arithmetic                        */
+    MGARD_F64 = 1,       /* double storage, double arithmetic                      */
+    MGARD_F32_MIXED = 2  /* float field; finest-level stencils in float; tridiagonal
+                            solves, the coarse-level arrays and the correction
+                            accumulation across levels in double                 */
+} mgard_dtype;
+
+typedef struct mgard_plan mgard_plan;
+
+/* Create a plan for one grid shape and precision.
+ *   ndim     number of dimensions, 1..3
+ *   dims     ndim node counts, slowest first
+ *   nlevels  number of levels L to process, or -1 for the largest allowed
+ *   coords   NULL for a uniform grid (x_i = i/(n-1)), else ndim host arrays,
+ *            coords[k] of length dims[k], strictly increasing (Section II-A:
+ *            non-uniformly spaced structured grids)
+ *   dtype    element type and precision scheme
+ *   out      receives the plan; NULL on failure
+ * The plan copies what it needs; coords may be freed afterwards.  Creating a
+ * plan allocates and fills its device tables synchronously on the current
+ * device; the plan is bound to that device. */
+MGARD_API mgard_status mgard_plan_create(int ndim, const int64_t *dims, int nlevels,
+                               const double *const *coords, mgard_dtype dtype,
+                               mgard_plan **out);
+
+/* Release a plan and its device tables (NULL is accepted). */
+MGARD_API mgard_status mgard_plan_destroy(mgard_plan *plan);
+
+/* Number of levels L the plan processes. */
+MGARD_API int mgard_plan_levels(const mgard_plan *plan);
+
+/* Bytes of device workspace one decompose/recompose call needs (256-byte
+ * aligned base required). */
+MGARD_API size_t mgard_workspace_bytes(const mgard_plan *plan);
+
+/* Kernel launches one mgard_decompose / mgard_recompose call issues. */
+MGARD_API int mgard_plan_launches(const mgard_plan *plan, int recompose);
+
+/* Multilevel decomposition in place (Section II-A, Eq. 1-2; Fig. 3 layout).
+ *   d_data   device array of prod(dims) elements of the plan's dtype
+ *            (float for MGARD_F32 and MGARD_F32_MIXED, double for MGARD_F64)
+ *   d_ws     device workspace of at least mgard_workspace_bytes(plan) bytes,
+ *            256-byte aligned; its contents on entry do not matter
+ *   stream   cudaStream_t as void* */
+MGARD_API mgard_status mgard_decompose(const mgard_plan *plan, void *d_data, void *d_ws,
+                             size_t ws_bytes, void *stream);
+
+/* Inverse of mgard_decompose, in place (Section II-A, recomposition runs the
+ * decomposition stages in reverse order).  Same arguments. */
+MGARD_API mgard_status mgard_recompose(const mgard_plan *plan, void *d_data, void *d_ws,
+                             size_t ws_bytes, void *stream);
+
+/* End-to-end forms with host buffers: copy h_in (host, prod(dims) elements,
+ * pinned for overlap) into d_data, transform it in place, copy the result
+ * into h_out (host, may equal h_in).  All three steps are queued on `stream`;
+ * the caller synchronizes the stream before reading h_out.  d_data and d_ws
+ * as for mgard_decompose. */
+MGARD_API mgard_status mgard_decompose_host(const mgard_plan *plan, const void *h_in, void *h_out,
+                                  void *d_data, void *d_ws, size_t ws_bytes, void *stream);
+MGARD_API mgard_status mgard_recompose_host(const mgard_plan *plan, const void *h_in, void *h_out,
+                                  void *d_data, void *d_ws, size_t ws_bytes, void *stream);
+
+/* Kernel timing (measurement support, not part of the method).  When
+ * enabled, the next calls on the plan record a CUDA event pair on the call's
+ * stream around every launch of the `levels` finest levels (0 = off).
+ * mgard_profile_read synchronizes on the recorded events and returns the
+ * accumulated time per kernel kind and level since the last read:
+ *   kinds[i]   0 coefficient+load-vector (decompose), 1 load-vector
+ *              (recompose), 2 solve sweep, 3 fused last solve sweep with
+ *              the correction update, 4 coarse placement, 5 interpolation
+ *   levels_out[i]  step index j (0 = finest level L)
+ *   launches[i], ms[i]  launch count and summed event time
+ * At most `cap` entries are written; the return value is the number of
+ * entries (or -1 on error).  Calls made while profiling must not overlap on
+ * different streams. */
+MGARD_API mgard_status mgard_profile_enable(mgard_plan *plan, int levels);
+MGARD_API int mgard_profile_read(mgard_plan *plan, int cap, int *kinds, int *levels_out,
+                                 int *launches, double *ms);
+
+/* Human-readable name of a status code (static string). */
+MGARD_API const char *mgard_status_string(mgard_status status);
+
+/* Reason for the most recent failure on the calling thread ("" if none). */
+MGARD_API const char *mgard_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGARD_GB300_H */

@@ -1,0 +1,664 @@
+// api.cu -- the C ABI of include/mgard.h: plan creation (validation, the
+// per-level interpolation / stencil / tridiagonal-factor tables), workspace
+// layout and the level loops of decomposition and recomposition
+// (Section II-A, Eq. 1-2; Section III-B, program structure).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mgard.h"
+#include "launch.cuh"
+
+using namespace mg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mgard_status fail(mgard_status st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+mgard_status cuda_fail(cudaError_t err, const char *what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(err);
+    return MGARD_ERR_CUDA;
+}
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+}  // namespace
+
+// One step of the hierarchy: level l = L - j (fine) -> l - 1 (coarse).
+struct mgard_level {
+    int64_t n[3];        // level-l node counts (inactive dims = 1)
+    int64_t m[3];        // level-(l-1) node counts
+    int64_t w_off[3];    // interpolation weight pairs (2 per fine node)
+    int64_t k_off[3];    // R*M stencil rows (5 per coarse node)
+    int64_t t_off[3];    // tridiagonal factors of M_{l-1} (3 per coarse node)
+    size_t v_off, f_off; // workspace offsets of V_j and F_j (bytes)
+    int rcfg;            // fused-restriction tile configuration
+    int zchunk, nzc, tiles_y, tiles_x;
+    int rgrid_dec, rgrid_rec;
+};
+
+struct mgard_plan {
+    int ndim;            // squeezed dimension count
+    int act;             // active-dimension mask (ACT_1D / ACT_2D / ACT_3D)
+    int64_t n[3];        // finest node counts, leading dims padded with 1
+    int L;
+    mgard_dtype dtype;
+    int device;
+    int num_sms;
+    size_t elem_user, elem_ws;
+    std::vector<mgard_level> lv;
+    double *tab64 = nullptr;
+    float *tab32 = nullptr;
+    size_t ws_bytes = 0;
+    int row_grid;
+    // kernel timing (measurement support): event pairs around the launches of
+    // the prof_levels finest levels
+    struct ProfRec {
+        int kind, level;
+        cudaEvent_t a, b;
+    };
+    mutable int prof_levels = 0;
+    mutable std::vector<ProfRec> prof_pending;
+    mutable std::vector<cudaEvent_t> prof_pool;
+};
+
+namespace {
+
+int64_t count(const int64_t *n) { return n[0] * n[1] * n[2]; }
+
+// Host construction of one dimension's tables at one level.
+//   x: coordinates of the level-l nodes (nf of them).
+void build_dim_tables(const std::vector<double> &x, std::vector<double> &tab, int64_t *w_off,
+                      int64_t *k_off, int64_t *t_off)
+{
+    const int64_t nf = (int64_t)x.size();
+    const int64_t nc = (nf - 1) / 2 + 1;
+    auto h = [&](int64_t i) -> double {  // spacing to the right of fine node i
+        return (i >= 0 && i < nf - 1) ? x[i + 1] - x[i] : 0.0;
+    };
+    // interpolation weights at odd fine nodes: left / right coarse neighbour
+    *w_off = (int64_t)tab.size();
+    std::vector<double> wl(nf, 0.0), wr(nf, 0.0);
+    for (int64_t j = 1; j < nf - 1; j += 2) {
+        const double span = x[j + 1] - x[j - 1];
+        wl[j] = (x[j + 1] - x[j]) / span;
+        wr[j] = (x[j] - x[j - 1]) / span;
+    }
+    for (int64_t j = 0; j < nf; ++j) {
+        tab.push_back(wl[j]);
+        tab.push_back(wr[j]);
+    }
+    // K = P^T M_l restricted to the band: row I covers fine nodes 2I-2 .. 2I+2.
+    // M_l (P1 mass matrix scaled by 6): diag 2(h_{i-1}+h_i), off-diagonal h_i.
+    auto mass = [&](int64_t r, int64_t c) -> double {
+        if (r < 0 || r >= nf || c < 0 || c >= nf) return 0.0;
+        if (r == c) return 2.0 * (h(r - 1) + h(r));
+        if (c == r + 1) return h(r);
+        if (c == r - 1) return h(c);
+        return 0.0;
+    };
+    *k_off = (int64_t)tab.size();
+    for (int64_t I = 0; I < nc; ++I) {
+        for (int t = 0; t < 5; ++t) {
+            const int64_t j = 2 * I - 2 + t;
+            double v = 0.0;
+            if (j >= 0 && j < nf) {
+                v += mass(2 * I, j);                                   // P[2I][I] = 1
+                if (2 * I - 1 >= 0) v += wr[2 * I - 1] * mass(2 * I - 1, j);  // P[2I-1][I]
+                if (2 * I + 1 < nf) v += wl[2 * I + 1] * mass(2 * I + 1, j);  // P[2I+1][I]
+            }
+            tab.push_back(v);
+        }
+    }
+    // LU factors of M_{l-1} on the coarse nodes x[0], x[2], ...
+    *t_off = (int64_t)tab.size();
+    std::vector<double> xc(nc);
+    for (int64_t i = 0; i < nc; ++i) xc[i] = x[2 * i];
+    auto hc = [&](int64_t i) -> double { return (i >= 0 && i < nc - 1) ? xc[i + 1] - xc[i] : 0.0; };
+    double piv_prev = 0.0;
+    for (int64_t i = 0; i < nc; ++i) {
+        const double d = 2.0 * (hc(i - 1) + hc(i));
+        double a = 0.0, piv = d;
+        if (i > 0) {
+            a = hc(i - 1) / piv_prev;       // multiplier of row i
+            piv = d - a * hc(i - 1);
+        }
+        const double inv = 1.0 / piv;
+        const double q = (i < nc - 1) ? hc(i) * inv : 0.0;
+        tab.push_back(a);
+        tab.push_back(inv);
+        tab.push_back(q);
+        piv_prev = piv;
+    }
+}
+
+template <typename T>
+const T *tab_ptr(const mgard_plan *P, int64_t off);
+template <>
+const float *tab_ptr<float>(const mgard_plan *P, int64_t off) { return P->tab32 + off; }
+template <>
+const double *tab_ptr<double>(const mgard_plan *P, int64_t off) { return P->tab64 + off; }
+
+int act_of(int ndim) { return ndim == 1 ? ACT_1D : (ndim == 2 ? ACT_2D : ACT_3D); }
+
+enum { KIND_RESTRICT_DEC = 0, KIND_RESTRICT_REC = 1, KIND_SOLVE = 2, KIND_SOLVE_FUSED = 3,
+       KIND_PLACE = 4, KIND_INTERP = 5, KIND_PLACE_EVEN = 6 };
+
+cudaEvent_t prof_event(const mgard_plan *P)
+{
+    if (!P->prof_pool.empty()) {
+        cudaEvent_t e = P->prof_pool.back();
+        P->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Launch `fn` on `st`, bracketed by an event pair when level j is profiled.
+template <typename Fn>
+cudaError_t timed(const mgard_plan *P, int kind, int j, cudaStream_t st, Fn &&fn)
+{
+    if (j >= P->prof_levels) return fn();
+    cudaEvent_t a = prof_event(P), b = prof_event(P);
+    if (!a || !b) return cudaErrorMemoryAllocation;
+    cudaError_t err = cudaEventRecord(a, st);
+    if (err == cudaSuccess) err = fn();
+    if (err == cudaSuccess) err = cudaEventRecord(b, st);
+    P->prof_pending.push_back({kind, j, a, b});
+    return err;
+}
+
+template <typename T, typename TW>
+cudaError_t run_restrict_level(const mgard_plan *P, int j, int mode, void *A, char *ws, cudaStream_t st)
+{
+    const mgard_level &L = P->lv[j];
+    RestrictParams p;
+    p.A = A;
+    p.F = ws + L.f_off;
+    p.V = ws + L.v_off;
+    p.n0 = L.n[0]; p.n1 = L.n[1]; p.n2 = L.n[2];
+    p.m0 = L.m[0]; p.m1 = L.m[1]; p.m2 = L.m[2];
+    p.w0 = tab_ptr<T>(P, L.w_off[0]); p.w1 = tab_ptr<T>(P, L.w_off[1]); p.w2 = tab_ptr<T>(P, L.w_off[2]);
+    p.k0 = tab_ptr<T>(P, L.k_off[0]); p.k1 = tab_ptr<T>(P, L.k_off[1]); p.k2 = tab_ptr<T>(P, L.k_off[2]);
+    p.tiles_y = L.tiles_y;
+    p.tiles_x = L.tiles_x;
+    p.zchunk = L.zchunk;
+    p.nzc = L.nzc;
+    p.nitems = L.tiles_y * L.tiles_x * L.nzc;
+    const int grid = (mode == MODE_DEC) ? L.rgrid_dec : L.rgrid_rec;
+    return timed(P, mode == MODE_DEC ? KIND_RESTRICT_DEC : KIND_RESTRICT_REC, j, st,
+                 [&] { return launch_restrict<T, TW>(P->act, mode, L.rcfg, p, grid, st); });
+}
+
+// Solves of M_{l-1} along every active dimension, fastest first; the last
+// (slowest) one applies V += z (sign +1) or V -= z (sign -1).
+template <typename TW>
+cudaError_t run_solves(const mgard_plan *P, int j, int sign, char *ws, cudaStream_t st)
+{
+    const mgard_level &L = P->lv[j];
+    const int nd = P->ndim;
+    for (int q = 0; q < nd; ++q) {
+        const int k = 2 - q;  // internal dim index, fastest first
+        SolveParams sp;
+        sp.F = ws + L.f_off;
+        sp.V = ws + L.v_off;
+        sp.fac = tab_ptr<TW>(P, L.t_off[k]);
+        sp.m = (int)L.m[k];
+        int64_t inner = 1;
+        for (int r = k + 1; r < 3; ++r) inner *= L.m[r];
+        sp.inner = inner;
+        sp.stride = inner;
+        sp.nlines = count(L.m) / L.m[k];
+        sp.chunk = solve_chunk(sp.m);
+        sp.nw = (sp.m + sp.chunk - 1) / sp.chunk;
+        sp.vmode = (q == nd - 1) ? (sign > 0 ? 1 : 2) : 0;
+        cudaError_t err = timed(P, sp.vmode ? KIND_SOLVE_FUSED : KIND_SOLVE, j, st,
+                                [&] { return launch_solve<TW>(sp, k == 2, st); });
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+PlaceParams place_params(const mgard_plan *P, int j, void *A, char *ws)
+{
+    const mgard_level &L = P->lv[j];
+    PlaceParams p;
+    p.A = A;
+    p.V = ws + L.v_off;
+    p.n0 = L.n[0]; p.n1 = L.n[1]; p.n2 = L.n[2];
+    p.m0 = L.m[0]; p.m1 = L.m[1]; p.m2 = L.m[2];
+    p.w0 = tab_ptr<T>(P, L.w_off[0]); p.w1 = tab_ptr<T>(P, L.w_off[1]); p.w2 = tab_ptr<T>(P, L.w_off[2]);
+    return p;
+}
+
+// Coefficients and final coarse values into the level array (decomposition).
+template <typename T, typename TW>
+cudaError_t run_place_level(const mgard_plan *P, int j, void *A, char *ws, cudaStream_t st)
+{
+    const mgard_level &L = P->lv[j];
+    const PlaceParams p = place_params<T>(P, j, A, ws);
+    cudaError_t err = cudaSuccess;
+    if (P->act != ACT_1D) {
+        const int64_t rows = L.n[0] * L.n[1];
+        const int grid = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)P->row_grid);
+        err = timed(P, KIND_PLACE, j, st, [&] { return launch_place<T, TW>(P->act, 0, p, grid, st); });
+        if (err != cudaSuccess) return err;
+    }
+    const int64_t rows = L.m[0] * L.m[1];
+    const int grid = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)P->row_grid);
+    return timed(P, KIND_PLACE_EVEN, j, st, [&] { return launch_place<T, TW>(P->act, 1, p, grid, st); });
+}
+
+template <typename T, typename TW>
+cudaError_t run_interp_level(const mgard_plan *P, int j, void *A, char *ws, cudaStream_t st)
+{
+    const mgard_level &L = P->lv[j];
+    const PlaceParams p = place_params<T>(P, j, A, ws);
+    const int64_t rows = L.n[0] * L.n[1];
+    const int grid = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)P->row_grid);
+    return timed(P, KIND_INTERP, j, st, [&] { return launch_interp<T, TW>(P->act, p, grid, st); });
+}
+
+// Decomposition, levels L..1 (Section II-A): level j = 0 works on the user
+// array (element type TU), deeper levels on the compact coarse arrays V_{j-1}
+// of the workspace (type TW).  Each level's restriction only reads its array;
+// after all levels, coarsest first, every level array receives its
+// coefficients and the final values of its coarse nodes.
+template <typename TU, typename TW>
+mgard_status exec_decompose(const mgard_plan *P, void *data, char *ws, cudaStream_t st)
+{
+    cudaError_t err;
+    for (int j = 0; j < P->L; ++j) {
+        void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
+        err = (j == 0) ? run_restrict_level<TU, TW>(P, j, MODE_DEC, A, ws, st)
+                       : run_restrict_level<TW, TW>(P, j, MODE_DEC, A, ws, st);
+        if (err != cudaSuccess) return cuda_fail(err, "decompose: coefficient/load-vector kernel");
+        err = run_solves<TW>(P, j, +1, ws, st);
+        if (err != cudaSuccess) return cuda_fail(err, "decompose: correction solve kernel");
+    }
+    for (int j = P->L - 1; j >= 0; --j) {
+        void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
+        err = (j == 0) ? run_place_level<TU, TW>(P, j, A, ws, st) : run_place_level<TW, TW>(P, j, A, ws, st);
+        if (err != cudaSuccess) return cuda_fail(err, "decompose: coefficient placement kernel");
+    }
+    return MGARD_OK;
+}
+
+// Recomposition, levels 1..L: first every level's load vector F_j and the
+// gathered coarse array V_j (both depend only on stored coefficients), then
+// coarsest first: correction solve with V_j -= z, then interpolation.
+template <typename TU, typename TW>
+mgard_status exec_recompose(const mgard_plan *P, void *data, char *ws, cudaStream_t st)
+{
+    cudaError_t err;
+    for (int j = 0; j < P->L; ++j) {
+        void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
+        err = (j == 0) ? run_restrict_level<TU, TW>(P, j, MODE_REC, A, ws, st)
+                       : run_restrict_level<TW, TW>(P, j, MODE_REC, A, ws, st);
+        if (err != cudaSuccess) return cuda_fail(err, "recompose: load-vector kernel");
+    }
+    for (int j = P->L - 1; j >= 0; --j) {
+        err = run_solves<TW>(P, j, -1, ws, st);
+        if (err != cudaSuccess) return cuda_fail(err, "recompose: correction solve kernel");
+        void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
+        err = (j == 0) ? run_interp_level<TU, TW>(P, j, A, ws, st) : run_interp_level<TW, TW>(P, j, A, ws, st);
+        if (err != cudaSuccess) return cuda_fail(err, "recompose: interpolation kernel");
+    }
+    return MGARD_OK;
+}
+
+template <typename TU, typename TW>
+cudaError_t configure_level(mgard_plan *P, mgard_level &L, bool finest)
+{
+    RestrictShape sh;
+    cudaError_t err = finest ? restrict_shape<TU, TW>(P->act, MODE_DEC, L.rcfg, &sh)
+                             : restrict_shape<TW, TW>(P->act, MODE_DEC, L.rcfg, &sh);
+    if (err != cudaSuccess) return err;
+    RestrictShape shr;
+    err = finest ? restrict_shape<TU, TW>(P->act, MODE_REC, L.rcfg, &shr)
+                 : restrict_shape<TW, TW>(P->act, MODE_REC, L.rcfg, &shr);
+    if (err != cudaSuccess) return err;
+    L.tiles_y = (int)((L.m[1] + sh.ty - 1) / sh.ty);
+    L.tiles_x = (int)((L.m[2] + sh.tx - 1) / sh.tx);
+    const int64_t tiles = (int64_t)L.tiles_y * L.tiles_x;
+    const int64_t slots = (int64_t)std::max(1, sh.blocks_per_sm) * P->num_sms;
+    if (P->act == ACT_3D) {
+        // enough items for about two per resident CTA, chunks of >= 4 planes
+        int64_t nzc = std::max<int64_t>(1, (2 * slots + tiles - 1) / tiles);
+        nzc = std::min<int64_t>(nzc, std::max<int64_t>(1, L.m[0] / 4));
+        L.zchunk = (int)((L.m[0] + nzc - 1) / nzc);
+        L.nzc = (int)((L.m[0] + L.zchunk - 1) / L.zchunk);
+    } else {
+        L.zchunk = 1;
+        L.nzc = 1;
+    }
+    const int64_t items = tiles * L.nzc;
+    L.rgrid_dec = (int)std::min<int64_t>(items, std::max(1, sh.blocks_per_sm) * (int64_t)P->num_sms);
+    L.rgrid_rec = (int)std::min<int64_t>(items, std::max(1, shr.blocks_per_sm) * (int64_t)P->num_sms);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mgard_status_string(mgard_status s)
+{
+    switch (s) {
+    case MGARD_OK: return "MGARD_OK";
+    case MGARD_ERR_INVALID_ARG: return "MGARD_ERR_INVALID_ARG";
+    case MGARD_ERR_UNSUPPORTED_SHAPE: return "MGARD_ERR_UNSUPPORTED_SHAPE";
+    case MGARD_ERR_WORKSPACE: return "MGARD_ERR_WORKSPACE";
+    case MGARD_ERR_CUDA: return "MGARD_ERR_CUDA";
+    case MGARD_ERR_TIMEOUT: return "MGARD_ERR_TIMEOUT";
+    case MGARD_ERR_INTERNAL: return "MGARD_ERR_INTERNAL";
+    }
+    return "MGARD_ERR_UNKNOWN";
+}
+
+const char *mgard_last_error(void) { return g_last_error.c_str(); }
+
+mgard_status mgard_plan_create(int ndim, const int64_t *dims, int nlevels, const double *const *coords,
+                               mgard_dtype dtype, mgard_plan **out)
+{
+    if (!out) return fail(MGARD_ERR_INVALID_ARG, "plan_create: out is NULL");
+    *out = nullptr;
+    if (!dims) return fail(MGARD_ERR_INVALID_ARG, "plan_create: dims is NULL");
+    if (ndim < 1 || ndim > 3) return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "plan_create: ndim must be 1..3");
+    if (dtype != MGARD_F32 && dtype != MGARD_F64 && dtype != MGARD_F32_MIXED)
+        return fail(MGARD_ERR_INVALID_ARG, "plan_create: unknown dtype");
+    if (nlevels < -1) return fail(MGARD_ERR_INVALID_ARG, "plan_create: nlevels must be >= -1");
+
+    // squeeze size-1 dimensions
+    std::vector<int64_t> n;
+    std::vector<std::vector<double>> x;
+    for (int k = 0; k < ndim; ++k) {
+        if (dims[k] < 1) return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "plan_create: dims must be >= 1");
+        if (dims[k] > (int64_t(1) << 31)) return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "plan_create: dimension too large");
+        if (dims[k] == 1) continue;
+        std::vector<double> xk(dims[k]);
+        if (coords && coords[k]) {
+            for (int64_t i = 0; i < dims[k]; ++i) xk[i] = coords[k][i];
+            for (int64_t i = 1; i < dims[k]; ++i)
+                if (!(xk[i] > xk[i - 1]) || !std::isfinite(xk[i]))
+                    return fail(MGARD_ERR_INVALID_ARG, "plan_create: coordinates must be finite and strictly increasing");
+        } else if (coords) {
+            return fail(MGARD_ERR_INVALID_ARG, "plan_create: coords given but coords[k] is NULL");
+        } else {
+            for (int64_t i = 0; i < dims[k]; ++i) xk[i] = (double)i / (double)(dims[k] - 1);
+        }
+        n.push_back(dims[k]);
+        x.push_back(std::move(xk));
+    }
+    if (n.empty()) return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "plan_create: no dimension larger than 1");
+    const int nd = (int)n.size();
+
+    int Lmax = 0;
+    for (;;) {
+        bool ok = true;
+        for (int64_t v : n) {
+            const int64_t step = int64_t(1) << (Lmax + 1);
+            if ((v - 1) % step != 0 || (v - 1) < step) ok = false;
+        }
+        if (!ok || Lmax >= 30) break;
+        ++Lmax;
+    }
+    const int L = (nlevels < 0) ? Lmax : nlevels;
+    if (L > Lmax)
+        return fail(MGARD_ERR_UNSUPPORTED_SHAPE,
+                    "plan_create: every (dims[k]-1) must be divisible by 2^nlevels (max levels here: " +
+                        std::to_string(Lmax) + ")");
+
+    mgard_plan *P = new (std::nothrow) mgard_plan();
+    if (!P) return fail(MGARD_ERR_INTERNAL, "plan_create: out of host memory");
+    P->ndim = nd;
+    P->act = act_of(nd);
+    P->n[0] = P->n[1] = 1;
+    for (int k = 0; k < nd; ++k) P->n[3 - nd + k] = n[k];
+    if (nd < 3) P->n[0] = 1;
+    if (nd < 2) P->n[1] = 1;
+    P->L = L;
+    P->dtype = dtype;
+    P->elem_user = (dtype == MGARD_F64) ? 8 : 4;
+    P->elem_ws = (dtype == MGARD_F32) ? 4 : 8;
+    cudaError_t err = cudaGetDevice(&P->device);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+    if (err != cudaSuccess) {
+        delete P;
+        return cuda_fail(err, "plan_create: device query");
+    }
+    P->row_grid = P->num_sms * 8;
+
+    // per-level geometry and tables
+    std::vector<double> tab;
+    tab.reserve(1024);
+    tab.push_back(0.0);  // offset 0 is a harmless dummy for inactive dims
+    for (int k = 0; k < 8; ++k) tab.push_back(0.0);
+    size_t ws = 0;
+    P->lv.resize(L);
+    for (int j = 0; j < L; ++j) {
+        mgard_level &lv = P->lv[j];
+        const int64_t stride = int64_t(1) << j;
+        for (int q = 0; q < 3; ++q) {
+            lv.n[q] = 1;
+            lv.m[q] = 1;
+            lv.w_off[q] = lv.k_off[q] = lv.t_off[q] = 0;
+        }
+        for (int k = 0; k < nd; ++k) {
+            const int q = 3 - nd + k;
+            const int64_t nf = (n[k] - 1) / stride + 1;
+            std::vector<double> xf(nf);
+            for (int64_t i = 0; i < nf; ++i) xf[i] = x[k][i * stride];
+            lv.n[q] = nf;
+            lv.m[q] = (nf - 1) / 2 + 1;
+            build_dim_tables(xf, tab, &lv.w_off[q], &lv.k_off[q], &lv.t_off[q]);
+        }
+        const size_t mbytes = (size_t)count(lv.m) * P->elem_ws;
+        lv.v_off = ws;
+        ws = align_up(ws + mbytes);
+        lv.f_off = ws;
+        ws = align_up(ws + mbytes);
+        lv.rcfg = 0;
+        if (P->act != ACT_1D && sizeof(double) == P->elem_ws && (j == 0 ? P->elem_user : P->elem_ws) == 8)
+            lv.rcfg = 1;  // 8-byte levels: 8 x 32 tiles keep three CTAs per SM
+        for (int k = 0; k < nd; ++k) {
+            const int q = 3 - nd + k;
+            if (solve_chunk((int)lv.m[q]) == 0) {
+                delete P;
+                return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "plan_create: a coarse line is longer than 2048 nodes");
+            }
+        }
+    }
+    P->ws_bytes = ws;
+
+    // device tables in double and float
+    std::vector<float> tab32(tab.begin(), tab.end());
+    err = cudaMalloc(&P->tab64, tab.size() * sizeof(double));
+    if (err == cudaSuccess) err = cudaMalloc(&P->tab32, tab32.size() * sizeof(float));
+    if (err == cudaSuccess) err = cudaMemcpy(P->tab64, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(P->tab32, tab32.data(), tab32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    for (int j = 0; j < L && err == cudaSuccess; ++j) {
+        mgard_level &lv = P->lv[j];
+        switch (dtype) {
+        case MGARD_F32: err = configure_level<float, float>(P, lv, j == 0); break;
+        case MGARD_F64: err = configure_level<double, double>(P, lv, j == 0); break;
+        default: err = configure_level<float, double>(P, lv, j == 0); break;
+        }
+    }
+    if (err != cudaSuccess) {
+        mgard_plan_destroy(P);
+        return cuda_fail(err, "plan_create: device tables");
+    }
+    *out = P;
+    return MGARD_OK;
+}
+
+mgard_status mgard_plan_destroy(mgard_plan *P)
+{
+    if (!P) return MGARD_OK;
+    if (P->tab64) cudaFree(P->tab64);
+    if (P->tab32) cudaFree(P->tab32);
+    for (auto &r : P->prof_pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : P->prof_pool) cudaEventDestroy(e);
+    delete P;
+    return MGARD_OK;
+}
+
+int mgard_plan_levels(const mgard_plan *P) { return P ? P->L : -1; }
+
+size_t mgard_workspace_bytes(const mgard_plan *P) { return P ? P->ws_bytes : 0; }
+
+int mgard_plan_launches(const mgard_plan *P, int recompose)
+{
+    if (!P) return -1;
+    // per level: one restriction + ndim solve sweeps + the element-wise
+    // kernel(s): interpolation (recompose) or one or two placement phases
+    const int tail = recompose ? 1 : (P->act == ACT_1D ? 1 : 2);
+    return P->L * (1 + P->ndim + tail);
+}
+
+static mgard_status check_call(const mgard_plan *P, void *data, void *ws, size_t ws_bytes)
+{
+    if (!P) return fail(MGARD_ERR_INVALID_ARG, "plan is NULL");
+    if (!data) return fail(MGARD_ERR_INVALID_ARG, "d_data is NULL");
+    if (P->ws_bytes > 0) {
+        if (!ws) return fail(MGARD_ERR_WORKSPACE, "d_ws is NULL");
+        if (ws_bytes < P->ws_bytes)
+            return fail(MGARD_ERR_WORKSPACE, "workspace too small: need " + std::to_string(P->ws_bytes) +
+                                                 " bytes, got " + std::to_string(ws_bytes));
+        if (reinterpret_cast<uintptr_t>(ws) % kAlign != 0)
+            return fail(MGARD_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+    }
+    if (reinterpret_cast<uintptr_t>(data) % P->elem_user != 0)
+        return fail(MGARD_ERR_INVALID_ARG, "d_data is not aligned to its element size");
+    int dev = -1;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaGetDevice");
+    if (dev != P->device) return fail(MGARD_ERR_INVALID_ARG, "the plan was created on another device");
+    return MGARD_OK;
+}
+
+mgard_status mgard_decompose(const mgard_plan *P, void *d_data, void *d_ws, size_t ws_bytes, void *stream)
+{
+    mgard_status s = check_call(P, d_data, d_ws, ws_bytes);
+    if (s != MGARD_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(d_ws);
+    switch (P->dtype) {
+    case MGARD_F32: return exec_decompose<float, float>(P, d_data, ws, st);
+    case MGARD_F64: return exec_decompose<double, double>(P, d_data, ws, st);
+    default: return exec_decompose<float, double>(P, d_data, ws, st);
+    }
+}
+
+mgard_status mgard_recompose(const mgard_plan *P, void *d_data, void *d_ws, size_t ws_bytes, void *stream)
+{
+    mgard_status s = check_call(P, d_data, d_ws, ws_bytes);
+    if (s != MGARD_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(d_ws);
+    switch (P->dtype) {
+    case MGARD_F32: return exec_recompose<float, float>(P, d_data, ws, st);
+    case MGARD_F64: return exec_recompose<double, double>(P, d_data, ws, st);
+    default: return exec_recompose<float, double>(P, d_data, ws, st);
+    }
+}
+
+static mgard_status host_call(bool DEC, const mgard_plan *P, const void *h_in, void *h_out, void *d_data,
+                              void *d_ws, size_t ws_bytes, void *stream)
+{
+    mgard_status s = check_call(P, d_data, d_ws, ws_bytes);
+    if (s != MGARD_OK) return s;
+    if (!h_in || !h_out) return fail(MGARD_ERR_INVALID_ARG, "host buffer is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)count(P->n) * P->elem_user;
+    cudaError_t err = cudaMemcpyAsync(d_data, h_in, bytes, cudaMemcpyHostToDevice, st);
+    if (err != cudaSuccess) return cuda_fail(err, "host-to-device copy");
+    s = DEC ? mgard_decompose(P, d_data, d_ws, ws_bytes, stream) : mgard_recompose(P, d_data, d_ws, ws_bytes, stream);
+    if (s != MGARD_OK) return s;
+    err = cudaMemcpyAsync(h_out, d_data, bytes, cudaMemcpyDeviceToHost, st);
+    if (err != cudaSuccess) return cuda_fail(err, "device-to-host copy");
+    return MGARD_OK;
+}
+
+mgard_status mgard_decompose_host(const mgard_plan *P, const void *h_in, void *h_out, void *d_data, void *d_ws,
+                                  size_t ws_bytes, void *stream)
+{
+    return host_call(true, P, h_in, h_out, d_data, d_ws, ws_bytes, stream);
+}
+
+mgard_status mgard_recompose_host(const mgard_plan *P, const void *h_in, void *h_out, void *d_data, void *d_ws,
+                                  size_t ws_bytes, void *stream)
+{
+    return host_call(false, P, h_in, h_out, d_data, d_ws, ws_bytes, stream);
+}
+
+mgard_status mgard_profile_enable(mgard_plan *P, int levels)
+{
+    if (!P || levels < 0) return fail(MGARD_ERR_INVALID_ARG, "profile_enable: bad arguments");
+    P->prof_levels = levels;
+    return MGARD_OK;
+}
+
+int mgard_profile_read(mgard_plan *P, int cap, int *kinds, int *levels_out, int *launches, double *ms)
+{
+    if (!P || cap < 0) return -1;
+    struct Acc {
+        int kind, level, count;
+        double ms;
+    };
+    std::vector<Acc> acc;
+    int rc = 0;
+    for (auto &r : P->prof_pending) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) rc = -1;
+        bool found = false;
+        for (auto &a : acc)
+            if (a.kind == r.kind && a.level == r.level) {
+                a.count++;
+                a.ms += t;
+                found = true;
+            }
+        if (!found) acc.push_back({r.kind, r.level, 1, (double)t});
+        P->prof_pool.push_back(r.a);
+        P->prof_pool.push_back(r.b);
+    }
+    P->prof_pending.clear();
+    if (rc != 0) {
+        g_last_error = "profile_read: event query failed";
+        return -1;
+    }
+    int n = 0;
+    for (auto &a : acc) {
+        if (n >= cap) break;
+        if (kinds) kinds[n] = a.kind;
+        if (levels_out) levels_out[n] = a.level;
+        if (launches) launches[n] = a.count;
+        if (ms) ms[n] = a.ms;
+        ++n;
+    }
+    return n;
+}
+
+}  // extern "C"

@@ -1,0 +1,50 @@
+// launch.cuh -- host-side launchers of the level kernels, instantiated per
+// element-type combination in inst_*.cu (compiled in parallel).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "params.h"
+
+namespace mg {
+
+// Tile shapes of the fused restriction kernel selectable per level.
+//   2D/3D: cfg 0 = 16 x 32 coarse nodes, cfg 1 = 8 x 32, cfg 2 = 4 x 64
+//   1D:    cfg 0 = 256 coarse nodes,     cfg 1 = 128,    cfg 2 = 512
+constexpr int kRestrictConfigs = 3;
+
+struct RestrictShape {
+    int ty, tx;          // coarse nodes per tile in dims 1 and 2
+    size_t smem;         // dynamic shared memory bytes
+    int blocks_per_sm;   // occupancy of the instantiation
+};
+
+template <typename T, typename TW>
+cudaError_t restrict_shape(int act, int mode, int cfg, RestrictShape *out);
+
+template <typename T, typename TW>
+cudaError_t launch_restrict(int act, int mode, int cfg, const RestrictParams &p, int grid,
+                            cudaStream_t st);
+
+// Chunk length for a line of m nodes: the smallest of 8/16/32/64 that keeps
+// the chunk count <= 32.  Returns 0 when m is too long.
+inline int solve_chunk(int m)
+{
+    for (int ch : {8, 16, 32, 64})
+        if ((m + ch - 1) / ch <= 32) return ch;
+    return 0;
+}
+
+// contiguous = lines along the fastest dimension (staged through shared
+// memory when it fits, otherwise read directly).
+template <typename TW>
+cudaError_t launch_solve(const SolveParams &p, bool contiguous, cudaStream_t st);
+
+// phase 0: rows odd in dim 0 or 1; phase 1: even rows (see k_place)
+template <typename T, typename TW>
+cudaError_t launch_place(int act, int phase, const PlaceParams &p, int grid, cudaStream_t st);
+
+template <typename T, typename TW>
+cudaError_t launch_interp(int act, const PlaceParams &p, int grid, cudaStream_t st);
+
+}  // namespace mg

@@ -1,0 +1,58 @@
+// params.h -- launch parameter blocks passed by value from the host level
+// loop to the kernels.  Internal to the library (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mg {
+
+// Active-dimension masks: bit 2 = dim 0 (slowest, "z"), bit 1 = dim 1 ("y"),
+// bit 0 = dim 2 (contiguous, "x").  1D grids use 1, 2D grids 3, 3D grids 7.
+enum : int { ACT_1D = 1, ACT_2D = 3, ACT_3D = 7 };
+
+enum : int { MODE_DEC = 0, MODE_REC = 1 };
+
+// Fused coefficient + load-vector pass over one level array (Section III-A:
+// the grid-processing coefficient step and the linear-processing
+// mass-transfer stencil, fused into a single tiled sweep).
+struct RestrictParams {
+    void *A;                 // level array, element type T (in/out)
+    void *F;                 // load vector on N_{l-1}, element type TW (out)
+    void *V;                 // values of A at N_{l-1}, element type TW (out)
+    int64_t n0, n1, n2;      // level-l node counts (inactive dims = 1)
+    int64_t m0, m1, m2;      // level-(l-1) node counts
+    const void *w0, *w1, *w2;  // interpolation weight pairs per fine node, type T
+    const void *k0, *k1, *k2;  // 5-point R*M stencil per coarse node, type T
+    int tiles_y, tiles_x;    // tile grid over (dim 1, dim 2) in coarse nodes
+    int zchunk, nzc;         // coarse planes per work item, number of chunks
+    int nitems;              // tiles_y * tiles_x * nzc
+};
+
+// Tridiagonal solves along one dimension of a compact coarse array, with the
+// LU factors of M_{l-1} precomputed per node: forward y_i = f_i - a_i y_{i-1},
+// backward z_i = inv_i y_i - q_i z_{i+1} (Section III-A-3, Thomas algorithm).
+struct SolveParams {
+    void *F;                 // right-hand sides, solved in place (type TW)
+    void *V;                 // coarse values updated by +-z when vmode != 0
+    const void *fac;         // 3 factors (a, inv, q) per node along the line
+    int64_t nlines;          // number of lines
+    int64_t inner;           // product of dims after the solved one
+    int64_t stride;          // element stride along the line (= inner)
+    int m;                   // line length
+    int nw;                  // warps per block (chunks per line)
+    int chunk;               // nodes per chunk
+    int vmode;               // 0: F <- z, 1: V += z, 2: V -= z
+};
+
+// Element-wise level kernels: placement of coefficients and coarse values
+// after a decomposition level (k_place), and the recomposition of a level
+// from its coefficients and the corrected coarse values (k_interp).
+struct PlaceParams {
+    void *A;                 // level array (type T)
+    const void *V;           // compact coarse array (type TW)
+    int64_t n0, n1, n2, m0, m1, m2;
+    const void *w0, *w1, *w2;  // interpolation weight pairs per fine node, type T
+};
+
+}  // namespace mg

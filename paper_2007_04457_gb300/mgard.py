@@ -1,0 +1,233 @@
+"""ctypes binding of the C ABI in ``include/mgard.h``.
+
+Argument marshalling only: every step of the decomposition runs in the CUDA
+library.  The module-level functions carry the C names and take raw
+integers (device pointers, byte counts, stream handles); ``Plan`` wraps them
+for torch tensors, using torch only for device memory and streams.
+
+Importing this module loads ``lib/libmgard_gb300.so`` and raises if it is
+missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+F32, F64, F32_MIXED = 0, 1, 2
+_DTYPE_CODES = {"f32": F32, "f64": F64, "f32_mixed": F32_MIXED}
+
+STATUS = {
+    0: "MGARD_OK",
+    1: "MGARD_ERR_INVALID_ARG",
+    2: "MGARD_ERR_UNSUPPORTED_SHAPE",
+    3: "MGARD_ERR_WORKSPACE",
+    4: "MGARD_ERR_CUDA",
+    5: "MGARD_ERR_TIMEOUT",
+    6: "MGARD_ERR_INTERNAL",
+}
+
+
+class MgardError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)}: {detail}")
+        self.status = status
+
+
+def _load() -> ctypes.CDLL:
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"CUDA library {path} is not built; run paper_2007_04457_gb300.build.build() "
+            "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    vp, sz, i64p = ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64)
+    dpp = ctypes.POINTER(ctypes.POINTER(ctypes.c_double))
+    sigs = {
+        "mgard_plan_create": ([ctypes.c_int, i64p, ctypes.c_int, dpp, ctypes.c_int,
+                               ctypes.POINTER(vp)], ctypes.c_int),
+        "mgard_plan_destroy": ([vp], ctypes.c_int),
+        "mgard_plan_levels": ([vp], ctypes.c_int),
+        "mgard_workspace_bytes": ([vp], sz),
+        "mgard_plan_launches": ([vp, ctypes.c_int], ctypes.c_int),
+        "mgard_decompose": ([vp, vp, vp, sz, vp], ctypes.c_int),
+        "mgard_recompose": ([vp, vp, vp, sz, vp], ctypes.c_int),
+        "mgard_decompose_host": ([vp, vp, vp, vp, vp, sz, vp], ctypes.c_int),
+        "mgard_recompose_host": ([vp, vp, vp, vp, vp, sz, vp], ctypes.c_int),
+        "mgard_profile_enable": ([vp, ctypes.c_int], ctypes.c_int),
+        "mgard_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "mgard_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "mgard_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+LIB = _load()
+LIB_PATH = _build.LIB
+
+
+def _check(status: int, what: str) -> None:
+    if status != 0:
+        raise MgardError(status, what, LIB.mgard_last_error().decode())
+
+
+# --------------------------------------------------------------- C-named calls
+
+def mgard_plan_create(ndim, dims, nlevels, coords, dtype) -> int:
+    """Returns the plan handle (an integer).  coords: None or ndim float64
+    numpy arrays."""
+    d = (ctypes.c_int64 * ndim)(*[int(v) for v in dims])
+    out = ctypes.c_void_p()
+    keep = []
+    cptr = None
+    if coords is not None:
+        import numpy as np
+        arrs = [np.ascontiguousarray(c, dtype=np.float64) for c in coords]
+        keep.extend(arrs)
+        cptr = (ctypes.POINTER(ctypes.c_double) * ndim)(
+            *[a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in arrs])
+    _check(LIB.mgard_plan_create(ndim, d, nlevels, cptr, dtype, ctypes.byref(out)),
+           "mgard_plan_create")
+    return out.value
+
+
+def mgard_plan_destroy(plan: int) -> None:
+    _check(LIB.mgard_plan_destroy(plan), "mgard_plan_destroy")
+
+
+def mgard_plan_levels(plan: int) -> int:
+    return LIB.mgard_plan_levels(plan)
+
+
+def mgard_workspace_bytes(plan: int) -> int:
+    return LIB.mgard_workspace_bytes(plan)
+
+
+def mgard_plan_launches(plan: int, recompose: int) -> int:
+    return LIB.mgard_plan_launches(plan, recompose)
+
+
+def mgard_decompose(plan: int, d_data: int, d_ws: int, ws_bytes: int, stream: int) -> None:
+    _check(LIB.mgard_decompose(plan, d_data, d_ws, ws_bytes, stream), "mgard_decompose")
+
+
+def mgard_recompose(plan: int, d_data: int, d_ws: int, ws_bytes: int, stream: int) -> None:
+    _check(LIB.mgard_recompose(plan, d_data, d_ws, ws_bytes, stream), "mgard_recompose")
+
+
+def mgard_decompose_host(plan: int, h_in: int, h_out: int, d_data: int, d_ws: int, ws_bytes: int,
+                         stream: int) -> None:
+    _check(LIB.mgard_decompose_host(plan, h_in, h_out, d_data, d_ws, ws_bytes, stream),
+           "mgard_decompose_host")
+
+
+def mgard_recompose_host(plan: int, h_in: int, h_out: int, d_data: int, d_ws: int, ws_bytes: int,
+                         stream: int) -> None:
+    _check(LIB.mgard_recompose_host(plan, h_in, h_out, d_data, d_ws, ws_bytes, stream),
+           "mgard_recompose_host")
+
+
+def mgard_profile_enable(plan: int, levels: int) -> None:
+    _check(LIB.mgard_profile_enable(plan, levels), "mgard_profile_enable")
+
+
+def mgard_profile_read(plan: int, cap: int = 64):
+    """List of (kind, level, launches, ms) since the last read."""
+    kinds = (ctypes.c_int * cap)()
+    levels = (ctypes.c_int * cap)()
+    launches = (ctypes.c_int * cap)()
+    ms = (ctypes.c_double * cap)()
+    n = LIB.mgard_profile_read(plan, cap, kinds, levels, launches, ms)
+    if n < 0:
+        raise MgardError(6, "mgard_profile_read", mgard_last_error())
+    return [(kinds[i], levels[i], launches[i], ms[i]) for i in range(n)]
+
+
+def mgard_status_string(status: int) -> str:
+    return LIB.mgard_status_string(status).decode()
+
+
+def mgard_last_error() -> str:
+    return LIB.mgard_last_error().decode()
+
+
+# --------------------------------------------------------------- torch wrapper
+
+def _torch():
+    import torch
+    return torch
+
+
+class Plan:
+    """A plan for one shape / precision, bound to the current CUDA device.
+
+    shape:   node counts, slowest first (1 to 3 dims after squeezing 1s)
+    nlevels: number of levels, -1 for the maximum the shape allows
+    coords:  None (uniform) or one increasing float64 array per dimension
+    dtype:   "f32", "f64" or "f32_mixed"
+    """
+
+    def __init__(self, shape, nlevels: int = -1, coords=None, dtype: str = "f32"):
+        if dtype not in _DTYPE_CODES:
+            raise ValueError(f"dtype must be one of {sorted(_DTYPE_CODES)}")
+        self.shape = tuple(int(n) for n in shape)
+        self.dtype = dtype
+        self.handle = mgard_plan_create(len(self.shape), self.shape, nlevels, coords,
+                                        _DTYPE_CODES[dtype])
+        self.levels = mgard_plan_levels(self.handle)
+        self.workspace_bytes = mgard_workspace_bytes(self.handle)
+        self._ws = None
+
+    @property
+    def torch_dtype(self):
+        torch = _torch()
+        return torch.float64 if self.dtype == "f64" else torch.float32
+
+    def launches(self, recompose: bool = False) -> int:
+        return mgard_plan_launches(self.handle, int(recompose))
+
+    def workspace(self, device=None):
+        """A cached device workspace of the required size (torch allocator)."""
+        torch = _torch()
+        if self._ws is None or (device is not None and self._ws.device != torch.device(device)):
+            self._ws = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8,
+                                   device=device or "cuda")
+        return self._ws
+
+    def _args(self, data, workspace, stream):
+        torch = _torch()
+        if not data.is_cuda or not data.is_contiguous() or data.dtype != self.torch_dtype:
+            raise ValueError(f"data must be a contiguous CUDA {self.torch_dtype} tensor")
+        if tuple(n for n in data.shape if n != 1) != tuple(n for n in self.shape if n != 1):
+            raise ValueError(f"data shape {tuple(data.shape)} does not match plan {self.shape}")
+        ws = workspace if workspace is not None else self.workspace(data.device)
+        s = stream if stream is not None else torch.cuda.current_stream(data.device)
+        return data.data_ptr(), ws.data_ptr(), ws.numel() * ws.element_size(), s.cuda_stream
+
+    def decompose(self, data, workspace=None, stream=None):
+        """In-place decomposition of a CUDA tensor; returns it."""
+        mgard_decompose(self.handle, *self._args(data, workspace, stream))
+        return data
+
+    def recompose(self, data, workspace=None, stream=None):
+        """In-place recomposition of a CUDA tensor; returns it."""
+        mgard_recompose(self.handle, *self._args(data, workspace, stream))
+        return data
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mgard_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
