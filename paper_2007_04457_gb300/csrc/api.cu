@@ -228,6 +228,7 @@ cudaError_t run_solves(const mgard_plan *P, int j, int sign, char *ws, cudaStrea
         sp.nlines = count(L.m) / L.m[k];
         sp.chunk = solve_chunk(sp.m);
         sp.nw = (sp.m + sp.chunk - 1) / sp.chunk;
+        sp.lpb = 32;
         sp.vmode = (q == nd - 1) ? (sign > 0 ? 1 : 2) : 0;
         cudaError_t err = timed(P, sp.vmode ? KIND_SOLVE_FUSED : KIND_SOLVE, j, st,
                                 [&] { return launch_solve<TW>(sp, k == 2, st); });
@@ -483,7 +484,7 @@ mgard_status mgard_plan_create(int ndim, const int64_t *dims, int nlevels, const
             const int q = 3 - nd + k;
             if (solve_chunk((int)lv.m[q]) == 0) {
                 delete P;
-                return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "plan_create: a coarse line is longer than 2048 nodes");
+                return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "plan_create: a coarse line is longer than 4096 nodes");
             }
         }
     }

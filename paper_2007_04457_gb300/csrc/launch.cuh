@@ -26,12 +26,15 @@ template <typename T, typename TW>
 cudaError_t launch_restrict(int act, int mode, int cfg, const RestrictParams &p, int grid,
                             cudaStream_t st);
 
-// Chunk length for a line of m nodes: the smallest of 8/16/32/64 that keeps
-// the chunk count <= 32.  Returns 0 when m is too long.
+// Chunk length for a line of m nodes.  Lines of up to 288 nodes use register
+// chunks of 16 (at most 18 warps per block); longer lines use 32
+// shared-memory chunks of ceil(m/32).  Returns 0 when m exceeds kMaxLine.
+constexpr int kMaxLine = 4096;
+constexpr int kRegLine = 288;
 inline int solve_chunk(int m)
 {
-    for (int ch : {8, 16, 32, 64})
-        if ((m + ch - 1) / ch <= 32) return ch;
+    if (m <= kRegLine) return 16;
+    if (m <= kMaxLine) return (m + 31) / 32;
     return 0;
 }
 

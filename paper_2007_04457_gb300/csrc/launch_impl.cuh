@@ -90,21 +90,39 @@ cudaError_t launch_restrict(int act, int mode, int cfg, const RestrictParams &p,
 }
 
 template <typename TW>
-cudaError_t launch_solve(const SolveParams &p, bool contiguous, cudaStream_t st)
+cudaError_t launch_solve(const SolveParams &p_in, bool contiguous, cudaStream_t st)
 {
+    SolveParams p = p_in;
     if (p.nlines <= 0) return cudaSuccess;
+    if (p.m > kRegLine) {
+        // shared-memory chunks: as many lines per block as fit in 200 KB
+        const size_t carry = sizeof(TW) * 2 * 32 * 32;
+        const size_t per_line = sizeof(TW) * (size_t)(p.m | 1);
+        int lpb = 32;
+        while (lpb > 1 && carry + per_line * lpb > 200 * 1024) lpb /= 2;
+        if (carry + per_line * lpb > 200 * 1024) return cudaErrorInvalidValue;
+        p.lpb = lpb;
+        p.nw = 32;
+        p.chunk = (p.m + 31) / 32;
+        const size_t smem = carry + per_line * lpb;
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(k_solve_smem<TW>),
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            if (err != cudaSuccess) return err;
+            attr_set = true;
+        }
+        const unsigned grid = (unsigned)((p.nlines + lpb - 1) / lpb);
+        k_solve_smem<TW><<<grid, dim3(32, 32), smem, st>>>(p);
+        return cudaGetLastError();
+    }
     const dim3 block(32, p.nw);
     const unsigned grid = (unsigned)((p.nlines + 31) / 32);
     const size_t smem = sizeof(TW) * (2 * 32 * 32 + 32 * (size_t)(p.m | 1));
-    const bool staged = contiguous && smem <= 200 * 1024;
+    const bool staged = contiguous;
     void (*fn)(SolveParams) = nullptr;
-    switch (p.chunk) {
-    case 8: fn = staged ? k_solve_contig<TW, 8> : k_solve_strided<TW, 8>; break;
-    case 16: fn = staged ? k_solve_contig<TW, 16> : k_solve_strided<TW, 16>; break;
-    case 32: fn = staged ? k_solve_contig<TW, 32> : k_solve_strided<TW, 32>; break;
-    case 64: fn = staged ? k_solve_contig<TW, 64> : k_solve_strided<TW, 64>; break;
-    default: return cudaErrorInvalidValue;
-    }
+    if (p.chunk != 16) return cudaErrorInvalidValue;
+    fn = staged ? k_solve_contig<TW, 16> : k_solve_strided<TW, 16>;
     if (staged) {
         if (smem > 48 * 1024) {
             cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),

@@ -43,6 +43,7 @@ struct SolveParams {
     int nw;                  // warps per block (chunks per line)
     int chunk;               // nodes per chunk
     int vmode;               // 0: F <- z, 1: V += z, 2: V -= z
+    int lpb;                 // lines per block (shared-memory variant)
 };
 
 // Element-wise level kernels: placement of coefficients and coarse values

@@ -61,6 +61,8 @@ CASES = [
     ((17, 65, 33), "f64", 2, True),
     ((65, 129, 65), "f32_mixed", -1, False),
     ((33, 17, 65), "f32_mixed", -1, True),
+    ((1025, 9), "f32", -1, False),      # long strided lines: shared-memory solve
+    ((9, 1025), "f64", -1, True),       # long contiguous lines: shared-memory solve
     ((3, 3, 3), "f32", -1, False),
     ((3, 5), "f64", -1, False),
     ((3,), "f32", -1, False),
