@@ -112,6 +112,20 @@ MGARD_API mgard_status mgard_decompose(const mgard_plan *plan, void *d_data, voi
 MGARD_API mgard_status mgard_recompose(const mgard_plan *plan, void *d_data, void *d_ws,
                              size_t ws_bytes, void *stream);
 
+/* Launch-shape tuning of one level (step j = 0 is the finest level L).  The
+ * result of a call does not depend on these settings beyond floating-point
+ * rounding of the solve order, which they do not change: only tile shapes
+ * and kernel variants are affected.
+ *   param 0  restriction tile: 0 = 8 x 64, 1 = 4 x 64, 2 = 16 x 64 coarse nodes
+ *   param 1  correction-solve variant: 0 = automatic, 1 = register chunks
+ *            (lines of at most 288 nodes), 2 = shared-memory chunks
+ *   param 2  coarse planes per restriction work item (0 = automatic)
+ * Returns MGARD_ERR_INVALID_ARG for an unknown parameter or value. */
+MGARD_API mgard_status mgard_plan_tune(mgard_plan *plan, int level, int param, int value);
+
+/* Current value of a tuning parameter of level j (-1 on error). */
+MGARD_API int mgard_plan_get_tune(const mgard_plan *plan, int level, int param);
+
 /* End-to-end forms with host buffers: copy h_in (host, prod(dims) elements,
  * pinned for overlap) into d_data, transform it in place, copy the result
  * into h_out (host, may equal h_in).  All three steps are queued on `stream`;

@@ -48,6 +48,8 @@ struct mgard_level {
     int64_t t_off[3];    // tridiagonal factors of M_{l-1} (3 per coarse node)
     size_t v_off, f_off; // workspace offsets of V_j and F_j (bytes)
     int rcfg;            // fused-restriction tile configuration
+    int svar;            // solve variant: 0 auto, 1 register chunks, 2 shared-memory chunks
+    int zreq;            // requested coarse planes per restriction item (0 = automatic)
     int zchunk, nzc, tiles_y, tiles_x;
     int rgrid_dec, rgrid_rec;
 };
@@ -230,8 +232,9 @@ cudaError_t run_solves(const mgard_plan *P, int j, int sign, char *ws, cudaStrea
         sp.nw = (sp.m + sp.chunk - 1) / sp.chunk;
         sp.lpb = 32;
         sp.vmode = (q == nd - 1) ? (sign > 0 ? 1 : 2) : 0;
+        const bool use_smem = (L.svar == 2) || sp.m > kRegLine;
         cudaError_t err = timed(P, sp.vmode ? KIND_SOLVE_FUSED : KIND_SOLVE, j, st,
-                                [&] { return launch_solve<TW>(sp, k == 2, st); });
+                                [&] { return launch_solve<TW>(sp, k == 2, use_smem, st); });
         if (err != cudaSuccess) return err;
     }
     return cudaSuccess;
@@ -337,16 +340,20 @@ cudaError_t configure_level(mgard_plan *P, mgard_level &L, bool finest)
     err = finest ? restrict_shape<TU, TW>(P->act, MODE_REC, L.rcfg, &shr)
                  : restrict_shape<TW, TW>(P->act, MODE_REC, L.rcfg, &shr);
     if (err != cudaSuccess) return err;
-    L.tiles_y = (int)((L.m[1] + sh.ty - 1) / sh.ty);
-    L.tiles_x = (int)((L.m[2] + sh.tx - 1) / sh.tx);
+    // tiles of ty x tx coarse nodes; the last tile of a dimension also takes
+    // the final node, so there are ceil((m-1)/t) tiles
+    L.tiles_y = (P->act == ACT_1D) ? 1 : (int)std::max<int64_t>(1, (L.m[1] - 1 + sh.ty - 1) / sh.ty);
+    L.tiles_x = (int)std::max<int64_t>(1, (L.m[2] - 1 + sh.tx - 1) / sh.tx);
     const int64_t tiles = (int64_t)L.tiles_y * L.tiles_x;
     const int64_t slots = (int64_t)std::max(1, sh.blocks_per_sm) * P->num_sms;
     if (P->act == ACT_3D) {
-        // enough items for about two per resident CTA, chunks of >= 4 planes
+        // enough items for about two per resident CTA, chunks of >= 4 planes;
+        // the last chunk takes the final plane
         int64_t nzc = std::max<int64_t>(1, (2 * slots + tiles - 1) / tiles);
-        nzc = std::min<int64_t>(nzc, std::max<int64_t>(1, L.m[0] / 4));
-        L.zchunk = (int)((L.m[0] + nzc - 1) / nzc);
-        L.nzc = (int)((L.m[0] + L.zchunk - 1) / L.zchunk);
+        nzc = std::min<int64_t>(nzc, std::max<int64_t>(1, (L.m[0] - 1) / 4));
+        L.zchunk = (int)std::max<int64_t>(1, (L.m[0] - 1 + nzc - 1) / nzc);
+        if (L.zreq > 0) L.zchunk = L.zreq;
+        L.nzc = (int)std::max<int64_t>(1, (L.m[0] - 1 + L.zchunk - 1) / L.zchunk);
     } else {
         L.zchunk = 1;
         L.nzc = 1;
@@ -478,8 +485,10 @@ mgard_status mgard_plan_create(int ndim, const int64_t *dims, int nlevels, const
         lv.f_off = ws;
         ws = align_up(ws + mbytes);
         lv.rcfg = 0;
-        if (P->act != ACT_1D && sizeof(double) == P->elem_ws && (j == 0 ? P->elem_user : P->elem_ws) == 8)
-            lv.rcfg = 1;  // 8-byte levels: 8 x 32 tiles keep three CTAs per SM
+        lv.svar = 0;
+        lv.zreq = 0;
+        if (P->act != ACT_1D && (j == 0 ? P->elem_user : P->elem_ws) == 8)
+            lv.rcfg = 1;  // 8-byte levels: 4 x 64 tiles keep two CTAs per SM
         for (int k = 0; k < nd; ++k) {
             const int q = 3 - nd + k;
             if (solve_chunk((int)lv.m[q]) == 0) {
@@ -583,6 +592,51 @@ mgard_status mgard_recompose(const mgard_plan *P, void *d_data, void *d_ws, size
     case MGARD_F32: return exec_recompose<float, float>(P, d_data, ws, st);
     case MGARD_F64: return exec_recompose<double, double>(P, d_data, ws, st);
     default: return exec_recompose<float, double>(P, d_data, ws, st);
+    }
+}
+
+static cudaError_t reconfigure(mgard_plan *P, int j)
+{
+    switch (P->dtype) {
+    case MGARD_F32: return configure_level<float, float>(P, P->lv[j], j == 0);
+    case MGARD_F64: return configure_level<double, double>(P, P->lv[j], j == 0);
+    default: return configure_level<float, double>(P, P->lv[j], j == 0);
+    }
+}
+
+mgard_status mgard_plan_tune(mgard_plan *P, int level, int param, int value)
+{
+    if (!P || level < 0 || level >= P->L) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: bad plan or level");
+    mgard_level &L = P->lv[level];
+    switch (param) {
+    case 0:
+        if (value < 0 || value >= kRestrictConfigs) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: tile config");
+        L.rcfg = value;
+        break;
+    case 1:
+        if (value < 0 || value > 2) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: solve variant");
+        L.svar = value;
+        return MGARD_OK;
+    case 2:
+        if (value < 0) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: chunk planes");
+        L.zreq = value;
+        break;
+    default: return fail(MGARD_ERR_INVALID_ARG, "plan_tune: unknown parameter");
+    }
+    cudaError_t err = reconfigure(P, level);
+    if (err != cudaSuccess) return cuda_fail(err, "plan_tune");
+    return MGARD_OK;
+}
+
+int mgard_plan_get_tune(const mgard_plan *P, int level, int param)
+{
+    if (!P || level < 0 || level >= P->L) return -1;
+    const mgard_level &L = P->lv[level];
+    switch (param) {
+    case 0: return L.rcfg;
+    case 1: return L.svar;
+    case 2: return L.zchunk;
+    default: return -1;
     }
 }
 

@@ -24,6 +24,31 @@ __device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem, bool valid
     }
 }
 
+// L2 policy that marks lines for early eviction (streamed data read once).
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+    return pol;
+}
+
+// cp_async_elem with an L2 cache policy.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem_hint(T *smem, const T *gmem, bool valid, uint64_t pol)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    const int nbytes = valid ? static_cast<int>(sizeof(T)) : 0;
+    if constexpr (sizeof(T) == 4) {
+        asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2, %3;\n" ::"r"(s), "l"(gmem),
+                     "r"(nbytes), "l"(pol)
+                     : "memory");
+    } else {
+        asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2, %3;\n" ::"r"(s), "l"(gmem),
+                     "r"(nbytes), "l"(pol)
+                     : "memory");
+    }
+}
+
 __device__ __forceinline__ void cp_async_commit()
 {
     asm volatile("cp.async.commit_group;\n" ::: "memory");

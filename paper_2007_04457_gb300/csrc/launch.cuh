@@ -8,9 +8,9 @@
 
 namespace mg {
 
-// Tile shapes of the fused restriction kernel selectable per level.
-//   2D/3D: cfg 0 = 16 x 32 coarse nodes, cfg 1 = 8 x 32, cfg 2 = 4 x 64
-//   1D:    cfg 0 = 256 coarse nodes,     cfg 1 = 128,    cfg 2 = 512
+// Tile shapes of the fused restriction kernel selectable per level (coarse
+// nodes in dims 1 x 2; a last tile absorbs the final node of a dimension):
+//   2D/3D: cfg 0 = 8 x 64, cfg 1 = 4 x 64, cfg 2 = 16 x 64;  1D: 64
 constexpr int kRestrictConfigs = 3;
 
 struct RestrictShape {
@@ -41,7 +41,7 @@ inline int solve_chunk(int m)
 // contiguous = lines along the fastest dimension (staged through shared
 // memory when it fits, otherwise read directly).
 template <typename TW>
-cudaError_t launch_solve(const SolveParams &p, bool contiguous, cudaStream_t st);
+cudaError_t launch_solve(const SolveParams &p, bool contiguous, bool use_smem, cudaStream_t st);
 
 // phase 0: rows odd in dim 0 or 1; phase 1: even rows (see k_place)
 template <typename T, typename TW>

@@ -17,27 +17,23 @@ struct RestrictEntry {
     size_t smem;
 };
 
-template <typename T, typename TW, int ACT, int MODE, int TY, int TX>
+template <typename T, typename TW, int ACT, int MODE, int TY>
 RestrictEntry restrict_entry()
 {
-    using G = RestrictGeom<ACT, TY, TX>;
-    return {k_restrict<T, TW, ACT, MODE, TY, TX>, G::TY, TX, sizeof(T) * (size_t)G::TOTAL};
+    using G = RestrictGeom<T, ACT, MODE, TY>;
+    return {k_restrict<T, TW, ACT, MODE, TY>, G::TY, kRestrictTX, sizeof(T) * (size_t)G::TOTAL};
 }
 
 template <typename T, typename TW, int ACT, int MODE>
 RestrictEntry restrict_pick_cfg(int cfg)
 {
     if constexpr (ACT == ACT_1D) {
-        switch (cfg) {
-        case 1: return restrict_entry<T, TW, ACT, MODE, 1, 128>();
-        case 2: return restrict_entry<T, TW, ACT, MODE, 1, 512>();
-        default: return restrict_entry<T, TW, ACT, MODE, 1, 256>();
-        }
+        return restrict_entry<T, TW, ACT, MODE, 1>();
     } else {
         switch (cfg) {
-        case 1: return restrict_entry<T, TW, ACT, MODE, 8, 32>();
-        case 2: return restrict_entry<T, TW, ACT, MODE, 4, 64>();
-        default: return restrict_entry<T, TW, ACT, MODE, 16, 32>();
+        case 1: return restrict_entry<T, TW, ACT, MODE, 4>();
+        case 2: return restrict_entry<T, TW, ACT, MODE, 16>();
+        default: return restrict_entry<T, TW, ACT, MODE, 8>();
         }
     }
 }
@@ -90,11 +86,11 @@ cudaError_t launch_restrict(int act, int mode, int cfg, const RestrictParams &p,
 }
 
 template <typename TW>
-cudaError_t launch_solve(const SolveParams &p_in, bool contiguous, cudaStream_t st)
+cudaError_t launch_solve(const SolveParams &p_in, bool contiguous, bool use_smem, cudaStream_t st)
 {
     SolveParams p = p_in;
     if (p.nlines <= 0) return cudaSuccess;
-    if (p.m > kRegLine) {
+    if (use_smem || p.m > kRegLine) {
         // shared-memory chunks: as many lines per block as fit in 200 KB
         const size_t carry = sizeof(TW) * 2 * 32 * 32;
         const size_t per_line = sizeof(TW) * (size_t)(p.m | 1);
@@ -171,6 +167,6 @@ cudaError_t launch_interp(int act, const PlaceParams &p, int grid, cudaStream_t 
     template cudaError_t launch_interp<T, TW>(int, const PlaceParams &, int, cudaStream_t);
 
 #define MG_INSTANTIATE_SOLVE(TW) \
-    template cudaError_t launch_solve<TW>(const SolveParams &, bool, cudaStream_t);
+    template cudaError_t launch_solve<TW>(const SolveParams &, bool, bool, cudaStream_t);
 
 }  // namespace mg

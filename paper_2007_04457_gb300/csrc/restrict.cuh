@@ -15,13 +15,21 @@
 // (k_place), with the same explicitly rounded interpolation, so the stored
 // coefficients are bit-identical to the C used here.
 //
-// Work item = (tile of TY x TX coarse nodes in dims 1,2) x (chunk of coarse
-// planes in dim 0).  The CTA streams the fine planes of its chunk through
-// shared memory (cp.async, one step ahead): each step handles the odd plane
-// 2Z-1 and the even plane 2Z, so the z-direction of both the interpolation
-// and the stencil reduces to rolling register accumulators.  A slab covers
-// fine rows [2Y0-2, 2Y0+2TY] and columns [2X0-2, 2X0+2TX] (a 2-node halo on
-// the low side and 1 node on the high side, the reach of the K stencil).
+// Work item = tile of TY x 64 coarse nodes in dims (1, 2) (the last tile of a
+// dimension absorbs the final node, so it may hold TY+1 x 65) x a chunk of
+// coarse planes in dim 0.  The CTA streams the fine planes of its chunk
+// through shared memory with cp.async, one step ahead; each step handles the
+// odd plane 2Z-1 and the even plane 2Z, so the dim-0 parts of both the
+// interpolation and the stencil reduce to rolling register accumulators.
+//
+// Thread mapping inside a plane: warp w takes slab rows w, w+8, ...; lane L
+// takes the four fine columns 4L..4L+3 of the tile (coarse columns 2L and
+// 2L+1), so the interpolation parities are uniform within a warp, the row
+// loads are 128-bit shared-memory loads, and the 5-point dim-2 stencil takes
+// its two left and one right neighbour values from the adjacent lanes by
+// shuffles.  Lane 0 also covers the two fine columns left of the tile and
+// lane 31 the one on its right (and the 65th coarse column of a last tile).
+// The dim-1 stencil then reads the dim-2-restricted rows from shared memory.
 #pragma once
 
 #include "common.cuh"
@@ -30,52 +38,102 @@
 namespace mg {
 
 constexpr int kRestrictThreads = 256;
+constexpr int kRestrictTX = 64;  // coarse columns per tile (+1 in a last tile)
 
-template <int ACT, int TY_, int TX>
+template <typename T, int ACT, int MODE, int TY_>
 struct RestrictGeom {
     static constexpr bool HZ = (ACT & 4) != 0;
     static constexpr bool HY = (ACT & 2) != 0;
+    static constexpr bool DEC = (MODE == MODE_DEC);
     static constexpr int TY = HY ? TY_ : 1;
-    static constexpr int RY = HY ? 2 * TY + 3 : 1;  // slab rows
-    static constexpr int CX = 2 * TX + 3;           // slab columns
-    static constexpr int PL = RY * CX;              // elements per slab
-    static constexpr int ROFF = HY ? 2 : 0;         // slab row of fine row 2*Y0
-    static constexpr int COFF = 2;                  // slab column of fine col 2*X0
+    static constexpr int RYM = HY ? 2 * TY + 5 : 1;   // slab rows, sized for a TY+1 last tile
+    static constexpr int SP = 136;                    // slab pitch: fine cols 2X0-4 .. 2X0+131
+    static constexpr int HP = 68;                     // pitch of the dim-2-restricted rows
     static constexpr int NT = kRestrictThreads;
-    static constexpr int PPT = (TY * TX + NT - 1) / NT;  // owned coarse nodes per thread
+    static constexpr int NWARP = NT / 32;
+    static constexpr int OUTS = (HY ? TY + 1 : 1) * HP;    // output slots per plane pair
+    static constexpr int PPT = (OUTS + NT - 1) / NT;       // output slots per thread
 
     // shared memory layout, in elements of T
-    static constexpr int OFF_SLAB = 0;                        // 4 slabs (2 steps x odd/even)
-    static constexpr int OFF_I = 4 * PL;                      // 2 interpolant planes (DEC)
-    static constexpr int OFF_H = OFF_I + 2 * PL;              // 2 x-restricted planes RY x TX
-    static constexpr int OFF_TAB = OFF_H + 2 * RY * TX;       // weights and stencils
-    static constexpr int TAB = 2 * CX + 2 * RY + 5 * TX + 5 * TY;
-    static constexpr int TOTAL = OFF_TAB + TAB;
+    static constexpr int OFF_SLAB = 0;                                      // 4 slabs
+    static constexpr int OFF_I = OFF_SLAB + 4 * RYM * SP;                   // 2 interpolant planes
+    static constexpr int OFF_H = OFF_I + ((DEC && HZ) ? 2 * RYM * SP : 0);  // 2 restricted planes
+    static constexpr int OFF_WY = OFF_H + 2 * RYM * HP;                     // dim-1 weights
+    static constexpr int OFF_KY = OFF_WY + 2 * RYM;                         // dim-1 stencil rows
+    static constexpr int TOTAL = OFF_KY + 5 * (TY + 1);
 };
 
-template <typename T, typename TW, int ACT, int MODE, int TY_, int TX>
+template <typename T>
+__device__ __forceinline__ void ld4(const T *p, T (&v)[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const double2 a = *reinterpret_cast<const double2 *>(p);
+        const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void st4(T *p, const T (&v)[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_dn(T v)
+{
+    return __shfl_down_sync(0xffffffffu, v, 1);
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_upw(T v)
+{
+    return __shfl_up_sync(0xffffffffu, v, 1);
+}
+
+// 5-point dim-2 stencil of the two coarse columns of a lane from the lane's
+// four C values, its left neighbour's last two (cl2, cl3) and its right
+// neighbour's first (crr).
+template <typename T>
+__device__ __forceinline__ void stencil2(const T (&ka)[5], const T (&kb)[5], T cl2, T cl3, const T (&c)[4],
+                                         T crr, T &ha, T &hb)
+{
+    ha = fma_rn(ka[0], cl2, mul_rn(ka[1], cl3));
+    ha = fma_rn(ka[2], c[0], ha);
+    ha = fma_rn(ka[3], c[1], ha);
+    ha = fma_rn(ka[4], c[2], ha);
+    hb = fma_rn(kb[0], c[0], mul_rn(kb[1], c[1]));
+    hb = fma_rn(kb[2], c[2], hb);
+    hb = fma_rn(kb[3], c[3], hb);
+    hb = fma_rn(kb[4], crr, hb);
+}
+
+template <typename T, typename TW, int ACT, int MODE, int TY_>
 __global__ void __launch_bounds__(kRestrictThreads)
 k_restrict(RestrictParams p)
 {
-    using G = RestrictGeom<ACT, TY_, TX>;
-    constexpr bool HZ = G::HZ, HY = G::HY;
-    constexpr int TY = G::TY, RY = G::RY, CX = G::CX, PL = G::PL;
-    constexpr int NT = G::NT, PPT = G::PPT;
-    constexpr bool DEC = (MODE == MODE_DEC);
+    using G = RestrictGeom<T, ACT, MODE, TY_>;
+    constexpr bool HZ = G::HZ, HY = G::HY, DEC = G::DEC;
+    constexpr int TY = G::TY, RYM = G::RYM, SP = G::SP, HP = G::HP;
+    constexpr int NT = G::NT, NWARP = G::NWARP, PPT = G::PPT;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     T *slab = sm + G::OFF_SLAB;
     T *Ib = sm + G::OFF_I;
-    T *Hx = sm + G::OFF_H;
-    T *wxl = sm + G::OFF_TAB;
-    T *wxr = wxl + CX;
-    T *wyl = wxr + CX;
-    T *wyr = wyl + RY;
-    T *kx = wyr + RY;
-    T *ky = kx + 5 * TX;
+    T *Hb = sm + G::OFF_H;
+    T *swy = sm + G::OFF_WY;
+    T *sky = sm + G::OFF_KY;
 
-    T *A = static_cast<T *>(p.A);
+    const T *A = static_cast<const T *>(p.A);
     TW *F = static_cast<TW *>(p.F);
     TW *V = static_cast<TW *>(p.V);
     const T *w0 = static_cast<const T *>(p.w0);
@@ -86,65 +144,92 @@ k_restrict(RestrictParams p)
     const T *k2 = static_cast<const T *>(p.k2);
 
     const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    constexpr int NWARP = NT / 32;
+    const int L = tid & 31, warp = tid >> 5;
     const int64_t n1 = p.n1, n2 = p.n2, m0 = p.m0, m1 = p.m1, m2 = p.m2;
     const int ntiles = p.tiles_y * p.tiles_x;
+    const uint64_t pol = policy_evict_first();  // the level array is streamed once
 
     for (int item = blockIdx.x; item < p.nitems; item += gridDim.x) {
         const int tile = item % ntiles;
         const int zc = item / ntiles;
-        const int64_t Y0 = HY ? (int64_t)(tile / p.tiles_x) * TY : 0;
-        const int64_t X0 = (int64_t)(tile % p.tiles_x) * TX;
-        const int TYo = HY ? (int)min64(TY, m1 - Y0) : 1;
-        const int TXo = (int)min64(TX, m2 - X0);
-        const int64_t gy0 = HY ? 2 * Y0 - 2 : 0;
-        const int64_t gx0 = 2 * X0 - 2;
+        const int ty = HY ? tile / p.tiles_x : 0;
+        const int tx = tile % p.tiles_x;
+        const int64_t Y0 = (int64_t)ty * TY;
+        const int64_t X0 = (int64_t)tx * kRestrictTX;
+        const int TYo = HY ? (ty == p.tiles_y - 1 ? (int)(m1 - Y0) : TY) : 1;
+        const int TXo = (tx == p.tiles_x - 1) ? (int)(m2 - X0) : kRestrictTX;
+        const int RY = HY ? 2 * TYo + 3 : 1;
+        const int64_t gy0 = HY ? 2 * Y0 - 2 : 0;   // fine row of slab row 0
+        const int64_t gx0 = 2 * X0 - 4;            // fine column of slab column 0
         const int64_t Zs = HZ ? (int64_t)zc * p.zchunk : 0;
-        const int64_t Ze = HZ ? min64(m0, Zs + p.zchunk) : 1;
+        const int64_t Ze = HZ ? (zc == p.nzc - 1 ? m0 : Zs + p.zchunk) : 1;
         const int64_t Zfirst = (HZ && Zs > 0) ? Zs - 1 : Zs;
         const int64_t Zlast = HZ ? min64(Ze, m0 - 1) : 0;
 
-        __syncthreads();  // the previous item is done with shared memory
-
-        // per-tile weights and stencil rows
-        for (int c = tid; c < CX; c += NT) {
-            const int64_t gx = gx0 + c;
-            const bool odd = (gx > 0) && (gx < n2 - 1) && (gx & 1);
-            wxl[c] = odd ? w2[2 * gx] : T(0);
-            wxr[c] = odd ? w2[2 * gx + 1] : T(0);
+        // per-lane tables: dim-2 weights of the odd columns 4L+1, 4L+3 (and
+        // lane 0's halo column -1), stencil rows of coarse columns 2L, 2L+1
+        // (and lane 31's column 64 of a 65-wide tile)
+        auto wxl_at = [&](int64_t gx) -> T {
+            return (gx > 0 && gx < n2 - 1 && (gx & 1)) ? w2[2 * gx] : T(0);
+        };
+        auto wxr_at = [&](int64_t gx) -> T {
+            return (gx > 0 && gx < n2 - 1 && (gx & 1)) ? w2[2 * gx + 1] : T(0);
+        };
+        const int64_t gxl = 2 * X0 + 4 * L;  // fine column of the lane's first node
+        const T wa1 = wxl_at(gxl + 1), wb1 = wxr_at(gxl + 1);
+        const T wa3 = wxl_at(gxl + 3), wb3 = wxr_at(gxl + 3);
+        const T wah = wxl_at(2 * X0 - 1), wbh = wxr_at(2 * X0 - 1);
+        T ka[5], kb[5], kc[5];
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            ka[t] = (2 * L < TXo) ? k2[5 * (X0 + 2 * L) + t] : T(0);
+            kb[t] = (2 * L + 1 < TXo) ? k2[5 * (X0 + 2 * L + 1) + t] : T(0);
+            kc[t] = (L == 31 && TXo > 64) ? k2[5 * (X0 + 64) + t] : T(0);
         }
+        // column validity of the lane's load slots L + 32k
+        unsigned colmask = 0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int s = L + 32 * k;
+            const int64_t gx = gx0 + s;
+            if (s < SP && gx >= 0 && gx < n2) colmask |= 1u << k;
+        }
+
+        __syncthreads();  // the previous item is done with shared memory
         if constexpr (HY) {
             for (int r = tid; r < RY; r += NT) {
                 const int64_t gy = gy0 + r;
                 const bool odd = (gy > 0) && (gy < n1 - 1) && (gy & 1);
-                wyl[r] = odd ? w1[2 * gy] : T(0);
-                wyr[r] = odd ? w1[2 * gy + 1] : T(0);
+                swy[2 * r] = odd ? w1[2 * gy] : T(0);
+                swy[2 * r + 1] = odd ? w1[2 * gy + 1] : T(0);
             }
-            for (int e = tid; e < 5 * TY; e += NT) {
+            for (int e = tid; e < 5 * (TY + 1); e += NT) {
                 const int Y = e / 5;
-                ky[e] = (Y < TYo) ? k1[5 * (Y0 + Y) + (e % 5)] : T(0);
+                sky[e] = (Y < TYo) ? k1[5 * (Y0 + Y) + (e % 5)] : T(0);
             }
-        }
-        for (int e = tid; e < 5 * TX; e += NT) {
-            const int X = e / 5;
-            kx[e] = (X < TXo) ? k2[5 * (X0 + X) + (e % 5)] : T(0);
         }
 
-        // Issue the loads of the fine planes of step Z into slab pair s.
+        // Loads of the fine planes of step Z into slab pair s.
         auto issue = [&](int64_t Z, int s) {
             const bool odd_plane = HZ && Z >= 1 && Z >= Zs;
+#pragma unroll
             for (int q = 0; q < 2; ++q) {
                 if (q == 0 && !odd_plane) continue;
                 const int64_t z = HZ ? (q == 0 ? 2 * Z - 1 : 2 * Z) : 0;
-                T *dst = slab + (2 * s + q) * PL;
+                T *dst = slab + (2 * s + q) * (RYM * SP);
                 const T *plane = A + z * n1 * n2;
-                for (int e = tid; e < PL; e += NT) {
-                    const int r = e / CX, c = e - (e / CX) * CX;
-                    const int64_t gy = gy0 + r, gx = gx0 + c;
-                    const bool ok = (gy >= 0) && (gy < n1) && (gx >= 0) && (gx < n2);
-                    const T *src = ok ? plane + gy * n2 + gx : A;
-                    cp_async_elem(dst + e, src, ok);
+                for (int r = warp; r < RY; r += NWARP) {
+                    const int64_t gy = gy0 + r;
+                    const bool rok = (gy >= 0) && (gy < n1);
+                    const T *src = plane + (rok ? gy : 0) * n2 + gx0;
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        const int s2 = L + 32 * k;
+                        if (s2 < SP) {
+                            const bool ok = rok && ((colmask >> k) & 1u);
+                            cp_async_elem_hint(dst + r * SP + s2, ok ? src + s2 : A, ok, pol);
+                        }
+                    }
                 }
             }
             cp_async_commit();
@@ -162,80 +247,145 @@ k_restrict(RestrictParams p)
             const int s = (int)((Z - Zfirst) & 1);
             const bool has_odd = HZ && Z >= 1 && Z >= Zs;
             const bool own_even = (Z >= Zs) && (Z < Ze);
-            T *So = slab + (2 * s) * PL;
-            T *Se = slab + (2 * s + 1) * PL;
-            T *Icur = Ib + s * PL;
-            T *Iprev = Ib + (1 - s) * PL;
+            const T *So = slab + (2 * s) * (RYM * SP);
+            const T *Se = slab + (2 * s + 1) * (RYM * SP);
+            T *Icur = Ib + s * (RYM * SP);
+            const T *Iprev = Ib + (1 - s) * (RYM * SP);
+            T *He = Hb + RYM * HP;
+            T *Ho = Hb;
+            T wzl = T(0), wzr = T(0);
+            if (has_odd) {
+                wzl = w0[2 * (2 * Z - 1)];
+                wzr = w0[2 * (2 * Z - 1) + 1];
+            }
 
             cp_async_wait<1>();
             __syncthreads();
 
-            if constexpr (DEC) {
-                // interpolant of the even plane from its even-even nodes
-                for (int e = tid; e < PL; e += NT) {
-                    const int r = e / CX, c = e - (e / CX) * CX;
-                    const bool ro = HY && (r & 1), co = (c & 1);
-                    T iv;
-                    if (!ro && !co) {
-                        iv = Se[e];
-                    } else if (!ro) {
-                        iv = lerp2(wxl[c], Se[e - 1], wxr[c], Se[e + 1]);
-                    } else if (!co) {
-                        iv = lerp2(wyl[r], Se[e - CX], wyr[r], Se[e + CX]);
+            // ---- passes over the rows of the two planes (warp-private rows)
+            for (int r = warp; r < RY; r += NWARP) {
+                const bool ro = HY && (r & 1);
+                const int rb = r * SP + 4 * L + 4;  // slab index of the lane's first column
+                T u[4], C[4], chl2, chl1, ch128;    // halo C: cols -2, -1 (lane 0), 128 (lane 31)
+                ld4(Se + rb, u);
+                const T uh128 = Se[r * SP + 132];
+                const T uhm2 = Se[r * SP + 2], uhm1 = Se[r * SP + 3];
+                // even plane
+                if constexpr (DEC) {
+                    T I[4], Ih2, Ih1, Ih128;
+                    if (!ro) {
+                        const T un = (L == 31) ? uh128 : shfl_dn(u[0]);
+                        I[0] = u[0];
+                        I[1] = lerp2(wa1, u[0], wb1, u[2]);
+                        I[2] = u[2];
+                        I[3] = lerp2(wa3, u[2], wb3, un);
+                        Ih2 = uhm2;
+                        Ih1 = lerp2(wah, uhm2, wbh, u[0]);
+                        Ih128 = uh128;
+                        C[0] = T(0);
+                        C[1] = sub_rn(u[1], I[1]);
+                        C[2] = T(0);
+                        C[3] = sub_rn(u[3], I[3]);
+                        chl2 = T(0);
+                        chl1 = sub_rn(uhm1, Ih1);
+                        ch128 = T(0);
                     } else {
-                        iv = lerp2(wyl[r], lerp2(wxl[c], Se[e - CX - 1], wxr[c], Se[e - CX + 1]), wyr[r],
-                                   lerp2(wxl[c], Se[e + CX - 1], wxr[c], Se[e + CX + 1]));
+                        const T wyl = swy[2 * r], wyr = swy[2 * r + 1];
+                        T um[4], up[4];
+                        ld4(Se + rb - SP, um);
+                        ld4(Se + rb + SP, up);
+                        const T umh = Se[(r - 1) * SP + 132], uph = Se[(r + 1) * SP + 132];
+                        const T umn = (L == 31) ? umh : shfl_dn(um[0]);
+                        const T upn = (L == 31) ? uph : shfl_dn(up[0]);
+                        const T xm1 = lerp2(wa1, um[0], wb1, um[2]), xm3 = lerp2(wa3, um[2], wb3, umn);
+                        const T xp1 = lerp2(wa1, up[0], wb1, up[2]), xp3 = lerp2(wa3, up[2], wb3, upn);
+                        I[0] = lerp2(wyl, um[0], wyr, up[0]);
+                        I[1] = lerp2(wyl, xm1, wyr, xp1);
+                        I[2] = lerp2(wyl, um[2], wyr, up[2]);
+                        I[3] = lerp2(wyl, xm3, wyr, xp3);
+                        const T umh2 = Se[(r - 1) * SP + 2], uph2 = Se[(r + 1) * SP + 2];
+                        const T xmh1 = lerp2(wah, umh2, wbh, um[0]), xph1 = lerp2(wah, uph2, wbh, up[0]);
+                        Ih2 = lerp2(wyl, umh2, wyr, uph2);
+                        Ih1 = lerp2(wyl, xmh1, wyr, xph1);
+                        Ih128 = lerp2(wyl, umh, wyr, uph);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) C[k] = sub_rn(u[k], I[k]);
+                        chl2 = sub_rn(uhm2, Ih2);
+                        chl1 = sub_rn(uhm1, Ih1);
+                        ch128 = sub_rn(uh128, Ih128);
                     }
-                    Icur[e] = iv;
-                }
-                __syncthreads();
-                // coefficients in place; the even-even nodes of the even plane keep u
-                T wzl = T(0), wzr = T(0);
-                if (has_odd) {
-                    wzl = w0[2 * (2 * Z - 1)];
-                    wzr = w0[2 * (2 * Z - 1) + 1];
-                }
-                for (int e = tid; e < PL; e += NT) {
-                    const int r = e / CX, c = e - (e / CX) * CX;
-                    const bool ee = !(HY && (r & 1)) && !(c & 1);
-                    if (!ee) Se[e] = sub_rn(Se[e], Icur[e]);
-                    if (has_odd) So[e] = sub_rn(So[e], lerp2(wzl, Iprev[e], wzr, Icur[e]));
-                }
-                __syncthreads();
-            }
-
-            // coarse values of the owned coarse nodes
-            if (own_even) {
-                TW *vrow = V + (HZ ? Z * m1 * m2 : 0);
-                for (int Y = warp; Y < TYo; Y += NWARP) {
-                    const int r = G::ROFF + 2 * Y;
-                    for (int X = lane; X < TXo; X += 32)
-                        vrow[(Y0 + Y) * m2 + X0 + X] = static_cast<TW>(Se[r * CX + G::COFF + 2 * X]);
-                }
-            }
-
-            // x-direction stencil of both planes: Hx[r][X] = sum_t kx[X][t] C[r][2X+t]
-            T *Ho = Hx;
-            T *He = Hx + RY * TX;
-            for (int e = tid; e < RY * TX; e += NT) {
-                const int r = e / TX, X = e - (e / TX) * TX;
-                const T *ce = Se + r * CX + 2 * X;
-                const T *kk = kx + 5 * X;
-                T he;
-                if (!(HY && (r & 1))) {
-                    he = kk[1] * ce[1] + kk[3] * ce[3];  // even row of the even plane: C = 0 at even columns
+                    if constexpr (HZ) {
+                        st4(Icur + rb, I);
+                        if (L == 0) {
+                            Icur[r * SP + 2] = Ih2;
+                            Icur[r * SP + 3] = Ih1;
+                        }
+                        if (L == 31) Icur[r * SP + 132] = Ih128;
+                    }
                 } else {
-                    he = kk[0] * ce[0] + kk[1] * ce[1] + kk[2] * ce[2] + kk[3] * ce[3] + kk[4] * ce[4];
+                    C[0] = ro ? u[0] : T(0);
+                    C[1] = u[1];
+                    C[2] = ro ? u[2] : T(0);
+                    C[3] = u[3];
+                    chl2 = ro ? uhm2 : T(0);
+                    chl1 = uhm1;
+                    ch128 = ro ? uh128 : T(0);
                 }
-                He[e] = he;
+                // coarse values of the owned coarse nodes (even row of an owned even plane)
+                if (own_even && !ro) {
+                    const int Yl = HY ? (r - 2) / 2 : 0;
+                    if (r >= (HY ? 2 : 0) && Yl < TYo) {
+                        TW *vrow = V + ((HZ ? Z : 0) * m1 + Y0 + Yl) * m2 + X0;
+                        if (2 * L < TXo) vrow[2 * L] = static_cast<TW>(u[0]);
+                        if (2 * L + 1 < TXo) vrow[2 * L + 1] = static_cast<TW>(u[2]);
+                        if (L == 31 && TXo > 64) vrow[64] = static_cast<TW>(uh128);
+                    }
+                }
+                // dim-2 stencil of the even plane
+                {
+                    T cl2 = shfl_upw(C[2]), cl3 = shfl_upw(C[3]);
+                    const T cr0 = shfl_dn(C[0]);
+                    if (L == 0) { cl2 = chl2; cl3 = chl1; }
+                    const T crr = (L == 31) ? ch128 : cr0;
+                    T ha, hb;
+                    stencil2(ka, kb, cl2, cl3, C, crr, ha, hb);
+                    T *hrow = He + r * HP;
+                    hrow[2 * L] = ha;
+                    hrow[2 * L + 1] = hb;
+                    if (L == 31) hrow[64] = fma_rn(kc[2], ch128, fma_rn(kc[0], C[2], mul_rn(kc[1], C[3])));
+                }
+                // odd plane: every node is a coefficient node
                 if (has_odd) {
-                    const T *co = So + r * CX + 2 * X;
-                    Ho[e] = kk[0] * co[0] + kk[1] * co[1] + kk[2] * co[2] + kk[3] * co[3] + kk[4] * co[4];
+                    T v[4];
+                    ld4(So + rb, v);
+                    T ohm2 = So[r * SP + 2], ohm1 = So[r * SP + 3], oh128 = So[r * SP + 132];
+                    if constexpr (DEC) {
+                        T ip[4], ic[4];
+                        ld4(Iprev + rb, ip);
+                        ld4(Icur + rb, ic);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) v[k] = sub_rn(v[k], lerp2(wzl, ip[k], wzr, ic[k]));
+                        ohm2 = sub_rn(ohm2, lerp2(wzl, Iprev[r * SP + 2], wzr, Icur[r * SP + 2]));
+                        ohm1 = sub_rn(ohm1, lerp2(wzl, Iprev[r * SP + 3], wzr, Icur[r * SP + 3]));
+                        oh128 = sub_rn(oh128, lerp2(wzl, Iprev[r * SP + 132], wzr, Icur[r * SP + 132]));
+                    }
+                    T cl2 = shfl_upw(v[2]), cl3 = shfl_upw(v[3]);
+                    const T cr0 = shfl_dn(v[0]);
+                    if (L == 0) { cl2 = ohm2; cl3 = ohm1; }
+                    const T crr = (L == 31) ? oh128 : cr0;
+                    T ha, hb;
+                    stencil2(ka, kb, cl2, cl3, v, crr, ha, hb);
+                    T *hrow = Ho + r * HP;
+                    hrow[2 * L] = ha;
+                    hrow[2 * L + 1] = hb;
+                    if (L == 31) hrow[64] = fma_rn(kc[2], oh128, fma_rn(kc[0], v[2], mul_rn(kc[1], v[3])));
                 }
             }
-            __syncthreads();
+            __syncthreads();  // restricted rows complete; the slabs of this step are free
+            if (Z + 2 <= Zlast) issue(Z + 2, s);
+            else cp_async_commit();
 
-            // y-direction stencil and z accumulation of the owned coarse nodes
+            // ---- dim-1 stencil and dim-0 accumulation of the owned coarse nodes
             T kzP[5], kzC[5], kzN[5];
             if constexpr (HZ) {
 #pragma unroll
@@ -248,39 +398,43 @@ k_restrict(RestrictParams p)
 #pragma unroll
             for (int i = 0; i < PPT; ++i) {
                 const int pos = tid + i * NT;
-                if (pos >= TY * TX) break;
-                const int Y = pos / TX, X = pos - (pos / TX) * TX;
+                if (pos >= G::OUTS) break;
+                const int Y = pos / HP, X = pos - (pos / HP) * HP;
+                if (Y >= TYo || X >= TXo) continue;
                 T ge, go = T(0);
                 if constexpr (HY) {
-                    const T *kk = ky + 5 * Y;
-                    const T *he = He + (2 * Y) * TX + X;
-                    ge = kk[0] * he[0] + kk[1] * he[TX] + kk[2] * he[2 * TX] + kk[3] * he[3 * TX] +
-                         kk[4] * he[4 * TX];
+                    const T *kk = sky + 5 * Y;
+                    const T *he = He + (2 * Y) * HP + X;
+                    ge = fma_rn(kk[0], he[0], mul_rn(kk[1], he[HP]));
+                    ge = fma_rn(kk[2], he[2 * HP], ge);
+                    ge = fma_rn(kk[3], he[3 * HP], ge);
+                    ge = fma_rn(kk[4], he[4 * HP], ge);
                     if (has_odd) {
-                        const T *ho = Ho + (2 * Y) * TX + X;
-                        go = kk[0] * ho[0] + kk[1] * ho[TX] + kk[2] * ho[2 * TX] + kk[3] * ho[3 * TX] +
-                             kk[4] * ho[4 * TX];
+                        const T *ho = Ho + (2 * Y) * HP + X;
+                        go = fma_rn(kk[0], ho[0], mul_rn(kk[1], ho[HP]));
+                        go = fma_rn(kk[2], ho[2 * HP], go);
+                        go = fma_rn(kk[3], ho[3 * HP], go);
+                        go = fma_rn(kk[4], ho[4 * HP], go);
                     }
                 } else {
                     ge = He[X];
                 }
                 if constexpr (HZ) {
-                    accP[i] += kzP[3] * go + kzP[4] * ge;
-                    accC[i] += kzC[1] * go + kzC[2] * ge;
-                    accN[i] += kzN[0] * ge;
+                    accP[i] = fma_rn(kzP[3], go, fma_rn(kzP[4], ge, accP[i]));
+                    accC[i] = fma_rn(kzC[1], go, fma_rn(kzC[2], ge, accC[i]));
+                    accN[i] = fma_rn(kzN[0], ge, accN[i]);
                 } else {
                     accC[i] = ge;
                 }
             }
-
             if constexpr (HZ) {
                 // F(Z-1) is complete once the planes up to 2Z are in
                 if (Z - 1 >= Zs && Z - 1 < Ze) {
 #pragma unroll
                     for (int i = 0; i < PPT; ++i) {
                         const int pos = tid + i * NT;
-                        if (pos >= TY * TX) break;
-                        const int Y = pos / TX, X = pos - (pos / TX) * TX;
+                        if (pos >= G::OUTS) break;
+                        const int Y = pos / HP, X = pos - (pos / HP) * HP;
                         if (Y < TYo && X < TXo)
                             F[((Z - 1) * m1 + Y0 + Y) * m2 + X0 + X] = static_cast<TW>(accP[i]);
                     }
@@ -292,10 +446,6 @@ k_restrict(RestrictParams p)
                     accN[i] = T(0);
                 }
             }
-
-            __syncthreads();  // slabs of this step may now be refilled
-            if (Z + 2 <= Zlast) issue(Z + 2, s);
-            else cp_async_commit();
         }
 
         // the last coarse plane of the grid has no contributions beyond it
@@ -304,8 +454,8 @@ k_restrict(RestrictParams p)
 #pragma unroll
             for (int i = 0; i < PPT; ++i) {
                 const int pos = tid + i * NT;
-                if (pos >= TY * TX) break;
-                const int Y = pos / TX, X = pos - (pos / TX) * TX;
+                if (pos >= G::OUTS) break;
+                const int Y = pos / HP, X = pos - (pos / HP) * HP;
                 if (Y < TYo && X < TXo)
                     F[(Zend * m1 + Y0 + Y) * m2 + X0 + X] = static_cast<TW>(HZ ? accP[i] : accC[i]);
             }

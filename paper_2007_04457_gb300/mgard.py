@@ -59,6 +59,8 @@ def _load() -> ctypes.CDLL:
         "mgard_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "mgard_plan_tune": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "mgard_plan_get_tune": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "mgard_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "mgard_last_error": ([], ctypes.c_char_p),
     }
@@ -148,6 +150,14 @@ def mgard_profile_read(plan: int, cap: int = 64):
     if n < 0:
         raise MgardError(6, "mgard_profile_read", mgard_last_error())
     return [(kinds[i], levels[i], launches[i], ms[i]) for i in range(n)]
+
+
+def mgard_plan_tune(plan: int, level: int, param: int, value: int) -> None:
+    _check(LIB.mgard_plan_tune(plan, level, param, value), "mgard_plan_tune")
+
+
+def mgard_plan_get_tune(plan: int, level: int, param: int) -> int:
+    return LIB.mgard_plan_get_tune(plan, level, param)
 
 
 def mgard_status_string(status: int) -> str:
