@@ -22,6 +22,10 @@
 // odd plane 2Z-1 and the even plane 2Z, so the dim-0 parts of both the
 // interpolation and the stencil reduce to rolling register accumulators.
 //
+// Every warp shuffle below runs in all 32 lanes (full mask) and the lanes
+// that need a halo value select it afterwards; a shuffle under a lane
+// condition would leave the warp waiting for the lanes that skipped it.
+//
 // Thread mapping inside a plane: warp w takes slab rows w, w+8, ...; lane L
 // takes the four fine columns 4L..4L+3 of the tile (coarse columns 2L and
 // 2L+1), so the interpolation parities are uniform within a warp, the row
@@ -274,7 +278,8 @@ k_restrict(RestrictParams p)
                 if constexpr (DEC) {
                     T I[4], Ih2, Ih1, Ih128;
                     if (!ro) {
-                        const T un = (L == 31) ? uh128 : shfl_dn(u[0]);
+                        const T sn = shfl_dn(u[0]);  // every lane shuffles, then selects
+                        const T un = (L == 31) ? uh128 : sn;
                         I[0] = u[0];
                         I[1] = lerp2(wa1, u[0], wb1, u[2]);
                         I[2] = u[2];
@@ -295,8 +300,9 @@ k_restrict(RestrictParams p)
                         ld4(Se + rb - SP, um);
                         ld4(Se + rb + SP, up);
                         const T umh = Se[(r - 1) * SP + 132], uph = Se[(r + 1) * SP + 132];
-                        const T umn = (L == 31) ? umh : shfl_dn(um[0]);
-                        const T upn = (L == 31) ? uph : shfl_dn(up[0]);
+                        const T smn = shfl_dn(um[0]), spn = shfl_dn(up[0]);
+                        const T umn = (L == 31) ? umh : smn;
+                        const T upn = (L == 31) ? uph : spn;
                         const T xm1 = lerp2(wa1, um[0], wb1, um[2]), xm3 = lerp2(wa3, um[2], wb3, umn);
                         const T xp1 = lerp2(wa1, up[0], wb1, up[2]), xp3 = lerp2(wa3, up[2], wb3, upn);
                         I[0] = lerp2(wyl, um[0], wyr, up[0]);
