@@ -12,7 +12,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/mgard.h"
+#include "mgard.h"
 #include "launch.cuh"
 
 using namespace mg;
