@@ -358,7 +358,11 @@ cudaError_t configure_level(mgard_plan *P, mgard_level &L, bool finest)
         L.zchunk = 1;
         L.nzc = 1;
     }
-    const int64_t items = tiles * L.nzc;
+    if (P->act == ACT_1D) {
+        // per-coarse-node kernel: items are blocks of sh.tx coarse nodes
+        L.tiles_x = (int)std::max<int64_t>(1, (L.m[2] + sh.tx - 1) / sh.tx);
+    }
+    const int64_t items = (P->act == ACT_1D) ? L.tiles_x : tiles * L.nzc;
     L.rgrid_dec = (int)std::min<int64_t>(items, std::max(1, sh.blocks_per_sm) * (int64_t)P->num_sms);
     L.rgrid_rec = (int)std::min<int64_t>(items, std::max(1, shr.blocks_per_sm) * (int64_t)P->num_sms);
     return cudaSuccess;

@@ -28,7 +28,7 @@ template <typename T, typename TW, int ACT, int MODE>
 RestrictEntry restrict_pick_cfg(int cfg)
 {
     if constexpr (ACT == ACT_1D) {
-        return restrict_entry<T, TW, ACT, MODE, 1>();
+        return {k_restrict1d<T, TW, MODE>, 1, 256, 0};
     } else {
         switch (cfg) {
         case 1: return restrict_entry<T, TW, ACT, MODE, 4>();
@@ -53,9 +53,11 @@ bool restrict_pick(int act, int mode, int cfg, RestrictEntry *e)
 
 inline cudaError_t prepare(void (*fn)(RestrictParams), size_t smem, int *bps)
 {
-    cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
+    if (smem > 0) {
+        cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+    }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, kRestrictThreads, smem);
 }
 

@@ -470,4 +470,32 @@ k_restrict(RestrictParams p)
     }
 }
 
+// One-dimensional grids: one thread per coarse node I.  Only the odd fine
+// nodes 2I-1 and 2I+1 carry coefficients, so F[I] = K[I][1] C(2I-1) +
+// K[I][3] C(2I+1), evaluated in the rounding order of the tiled kernel, and
+// V[I] = A[2I].  The tiled kernel above is not instantiated for 1D.
+template <typename T, typename TW, int MODE>
+__global__ void __launch_bounds__(256) k_restrict1d(RestrictParams p)
+{
+    const T *__restrict__ A = static_cast<const T *>(p.A);
+    TW *__restrict__ F = static_cast<TW *>(p.F);
+    TW *__restrict__ V = static_cast<TW *>(p.V);
+    const T *__restrict__ w2 = static_cast<const T *>(p.w2);
+    const T *__restrict__ k2 = static_cast<const T *>(p.k2);
+    const int64_t n2 = p.n2, m2 = p.m2;
+    auto coef = [&](int64_t j) -> T {  // C at the odd fine node j (0 outside the grid)
+        if (j < 1 || j > n2 - 2) return T(0);
+        if constexpr (MODE == MODE_DEC)
+            return sub_rn(A[j], lerp2(w2[2 * j], A[j - 1], w2[2 * j + 1], A[j + 1]));
+        else
+            return A[j];
+    };
+    for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < m2;
+         I += (int64_t)gridDim.x * blockDim.x) {
+        const T cl = coef(2 * I - 1), cr = coef(2 * I + 1);
+        F[I] = static_cast<TW>(fma_rn(k2[5 * I + 3], cr, mul_rn(k2[5 * I + 1], cl)));
+        V[I] = static_cast<TW>(A[2 * I]);
+    }
+}
+
 }  // namespace mg
