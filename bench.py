@@ -36,7 +36,7 @@ SHAPE = (513, 513, 513)
 N_MODES = 12
 SEED = 2
 KIND_NAMES = {0: "restrict_dec", 1: "restrict_rec", 2: "solve", 3: "solve_fused",
-              4: "place_odd_rows", 5: "interp", 6: "place_even_rows"}
+              4: "coef", 5: "interp", 6: "scatter"}
 
 
 def level_nodes(shape, L):
@@ -62,17 +62,14 @@ def kernel_bytes(kind, shape, S, SW):
     """Compulsory bytes of one finest-level launch of a kernel kind."""
     M = level_nodes(shape, 1)
     Mf, Mc = M[0], M[1]
-    n = list(shape)
-    m = [(k - 1) // 2 + 1 for k in n]
-    even_rows_nodes = m[0] * m[1] * n[2]           # nodes on rows even in dims 0 and 1
     return {
         0: Mf * S + 2 * Mc * SW,                   # read level, write F and V
         1: Mf * S + 2 * Mc * SW,                   # read level, write F and V
         2: 2 * Mc * SW,                            # read + write F
         3: 3 * Mc * SW,                            # read F, read + write V
-        4: 2 * (Mf - even_rows_nodes) * S,         # read + write the odd rows
+        4: 2 * Mf * S,                             # read + write the level
         5: 2 * Mf * S + Mc * SW,                   # read coefficients + V, write level
-        6: 2 * even_rows_nodes * S + Mc * SW,      # read + write even rows, read V
+        6: Mc * SW + Mc * S,                       # read V, write the coarse nodes
     }[kind]
 
 

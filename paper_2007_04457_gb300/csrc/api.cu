@@ -48,7 +48,7 @@ struct mgard_level {
     int64_t t_off[3];    // tridiagonal factors of M_{l-1} (3 per coarse node)
     size_t v_off, f_off; // workspace offsets of V_j and F_j (bytes)
     int rcfg;            // fused-restriction tile configuration
-    int svar;            // solve variant: 0 auto, 1 register chunks, 2 shared-memory chunks
+    int svar;            // warps per line in the solve kernel (0 = automatic)
     int zreq;            // requested coarse planes per restriction item (0 = automatic)
     int zchunk, nzc, tiles_y, tiles_x;
     int rgrid_dec, rgrid_rec;
@@ -228,13 +228,12 @@ cudaError_t run_solves(const mgard_plan *P, int j, int sign, char *ws, cudaStrea
         sp.inner = inner;
         sp.stride = inner;
         sp.nlines = count(L.m) / L.m[k];
-        sp.chunk = solve_chunk(sp.m);
-        sp.nw = (sp.m + sp.chunk - 1) / sp.chunk;
+        sp.chunk = 0;
+        sp.nw = 0;
         sp.lpb = 32;
         sp.vmode = (q == nd - 1) ? (sign > 0 ? 1 : 2) : 0;
-        const bool use_smem = (L.svar == 2) || sp.m > kRegLine;
         cudaError_t err = timed(P, sp.vmode ? KIND_SOLVE_FUSED : KIND_SOLVE, j, st,
-                                [&] { return launch_solve<TW>(sp, k == 2, use_smem, st); });
+                                [&] { return launch_solve<TW>(sp, L.svar, st); });
         if (err != cudaSuccess) return err;
     }
     return cudaSuccess;
@@ -257,28 +256,17 @@ PlaceParams place_params(const mgard_plan *P, int j, void *A, char *ws)
 template <typename T, typename TW>
 cudaError_t run_place_level(const mgard_plan *P, int j, void *A, char *ws, cudaStream_t st)
 {
-    const mgard_level &L = P->lv[j];
     const PlaceParams p = place_params<T>(P, j, A, ws);
-    cudaError_t err = cudaSuccess;
-    if (P->act != ACT_1D) {
-        const int64_t rows = L.n[0] * L.n[1];
-        const int grid = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)P->row_grid);
-        err = timed(P, KIND_PLACE, j, st, [&] { return launch_place<T, TW>(P->act, 0, p, grid, st); });
-        if (err != cudaSuccess) return err;
-    }
-    const int64_t rows = L.m[0] * L.m[1];
-    const int grid = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)P->row_grid);
-    return timed(P, KIND_PLACE_EVEN, j, st, [&] { return launch_place<T, TW>(P->act, 1, p, grid, st); });
+    cudaError_t err = timed(P, KIND_PLACE, j, st, [&] { return launch_coef<T, TW>(P->act, p, st); });
+    if (err != cudaSuccess) return err;
+    return timed(P, KIND_PLACE_EVEN, j, st, [&] { return launch_scatter<T, TW>(P->act, p, st); });
 }
 
 template <typename T, typename TW>
 cudaError_t run_interp_level(const mgard_plan *P, int j, void *A, char *ws, cudaStream_t st)
 {
-    const mgard_level &L = P->lv[j];
     const PlaceParams p = place_params<T>(P, j, A, ws);
-    const int64_t rows = L.n[0] * L.n[1];
-    const int grid = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)P->row_grid);
-    return timed(P, KIND_INTERP, j, st, [&] { return launch_interp<T, TW>(P->act, p, grid, st); });
+    return timed(P, KIND_INTERP, j, st, [&] { return launch_interp<T, TW>(P->act, p, st); });
 }
 
 // Decomposition, levels L..1 (Section II-A): level j = 0 works on the user
@@ -495,7 +483,7 @@ mgard_status mgard_plan_create(int ndim, const int64_t *dims, int nlevels, const
             lv.rcfg = 1;  // 8-byte levels: 4 x 64 tiles keep two CTAs per SM
         for (int k = 0; k < nd; ++k) {
             const int q = 3 - nd + k;
-            if (solve_chunk((int)lv.m[q]) == 0) {
+            if (lv.m[q] > kMaxLine) {
                 delete P;
                 return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "plan_create: a coarse line is longer than 4096 nodes");
             }
@@ -547,8 +535,8 @@ int mgard_plan_launches(const mgard_plan *P, int recompose)
 {
     if (!P) return -1;
     // per level: one restriction + ndim solve sweeps + the element-wise
-    // kernel(s): interpolation (recompose) or one or two placement phases
-    const int tail = recompose ? 1 : (P->act == ACT_1D ? 1 : 2);
+    // kernel(s): interpolation (recompose) or coefficients + coarse placement
+    const int tail = recompose ? 1 : 2;
     return P->L * (1 + P->ndim + tail);
 }
 
@@ -618,7 +606,7 @@ mgard_status mgard_plan_tune(mgard_plan *P, int level, int param, int value)
         L.rcfg = value;
         break;
     case 1:
-        if (value < 0 || value > 2) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: solve variant");
+        if (value < 0 || value > 32) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: solve warps");
         L.svar = value;
         return MGARD_OK;
     case 2:

@@ -26,28 +26,24 @@ template <typename T, typename TW>
 cudaError_t launch_restrict(int act, int mode, int cfg, const RestrictParams &p, int grid,
                             cudaStream_t st);
 
-// Chunk length for a line of m nodes.  Lines of up to 288 nodes use register
-// chunks of 16 (at most 18 warps per block); longer lines use 32
-// shared-memory chunks of ceil(m/32).  Returns 0 when m exceeds kMaxLine.
+// Longest coarse line the solve kernel takes (a panel of one line must fit in
+// shared memory).
 constexpr int kMaxLine = 4096;
-constexpr int kRegLine = 288;
-inline int solve_chunk(int m)
-{
-    if (m <= kRegLine) return 16;
-    if (m <= kMaxLine) return (m + 31) / 32;
-    return 0;
-}
 
-// contiguous = lines along the fastest dimension (staged through shared
-// memory when it fits, otherwise read directly).
+// Solves along dimension k of a compact array; nw_req = warps (chunks) per
+// line, 0 = automatic (about 8 nodes per chunk, at most 32 warps).
 template <typename TW>
-cudaError_t launch_solve(const SolveParams &p, bool contiguous, bool use_smem, cudaStream_t st);
+cudaError_t launch_solve(const SolveParams &p, int nw_req, cudaStream_t st);
 
-// phase 0: rows odd in dim 0 or 1; phase 1: even rows (see k_place)
+// Element-wise kernels (one thread per node): coefficients of a decomposed
+// level, placement of its final coarse values, and recomposition of a level.
 template <typename T, typename TW>
-cudaError_t launch_place(int act, int phase, const PlaceParams &p, int grid, cudaStream_t st);
+cudaError_t launch_coef(int act, const PlaceParams &p, cudaStream_t st);
 
 template <typename T, typename TW>
-cudaError_t launch_interp(int act, const PlaceParams &p, int grid, cudaStream_t st);
+cudaError_t launch_scatter(int act, const PlaceParams &p, cudaStream_t st);
+
+template <typename T, typename TW>
+cudaError_t launch_interp(int act, const PlaceParams &p, cudaStream_t st);
 
 }  // namespace mg

@@ -2,6 +2,8 @@
 // Included only by the inst_*.cu translation units.
 #pragma once
 
+#include <algorithm>
+
 #include "interp.cuh"
 #include "launch.cuh"
 #include "restrict.cuh"
@@ -88,74 +90,84 @@ cudaError_t launch_restrict(int act, int mode, int cfg, const RestrictParams &p,
 }
 
 template <typename TW>
-cudaError_t launch_solve(const SolveParams &p_in, bool contiguous, bool use_smem, cudaStream_t st)
+cudaError_t launch_solve(const SolveParams &p_in, int nw_req, cudaStream_t st)
 {
     SolveParams p = p_in;
     if (p.nlines <= 0) return cudaSuccess;
-    if (use_smem || p.m > kRegLine) {
-        // shared-memory chunks: as many lines per block as fit in 200 KB
-        const size_t carry = sizeof(TW) * 2 * 32 * 32;
-        const size_t per_line = sizeof(TW) * (size_t)(p.m | 1);
-        int lpb = 32;
-        while (lpb > 1 && carry + per_line * lpb > 200 * 1024) lpb /= 2;
-        if (carry + per_line * lpb > 200 * 1024) return cudaErrorInvalidValue;
-        p.lpb = lpb;
-        p.nw = 32;
-        p.chunk = (p.m + 31) / 32;
-        const size_t smem = carry + per_line * lpb;
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(k_solve_smem<TW>),
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            if (err != cudaSuccess) return err;
-            attr_set = true;
-        }
-        const unsigned grid = (unsigned)((p.nlines + lpb - 1) / lpb);
-        k_solve_smem<TW><<<grid, dim3(32, 32), smem, st>>>(p);
-        return cudaGetLastError();
+    int nw = nw_req > 0 ? nw_req : std::min(32, std::max(1, (p.m + 7) / 8));
+    nw = std::max(1, std::min(nw, std::min(32, p.m)));
+    p.nw = nw;
+    p.chunk = (p.m + nw - 1) / nw;
+    constexpr size_t kCap = 200 * 1024;
+    int lpb = 32;
+    while (lpb > 1 && solve_panel_elems(p.m, lpb) * sizeof(TW) > kCap) lpb /= 2;
+    const size_t smem = solve_panel_elems(p.m, lpb) * sizeof(TW);
+    if (smem > kCap) return cudaErrorInvalidValue;
+    p.lpb = lpb;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(k_solve_panel<TW>),
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCap);
+        if (err != cudaSuccess) return err;
+        attr_set = true;
     }
-    const dim3 block(32, p.nw);
-    const unsigned grid = (unsigned)((p.nlines + 31) / 32);
-    const size_t smem = sizeof(TW) * (2 * 32 * 32 + 32 * (size_t)(p.m | 1));
-    const bool staged = contiguous;
-    void (*fn)(SolveParams) = nullptr;
-    if (p.chunk != 16) return cudaErrorInvalidValue;
-    fn = staged ? k_solve_contig<TW, 16> : k_solve_strided<TW, 16>;
-    if (staged) {
-        if (smem > 48 * 1024) {
-            cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   200 * 1024);
-            if (err != cudaSuccess) return err;
-        }
-        fn<<<grid, block, smem, st>>>(p);
-    } else {
-        fn<<<grid, block, 0, st>>>(p);
-    }
+    const int64_t panels = (p.nlines + lpb - 1) / lpb;
+    k_solve_panel<TW><<<(unsigned)std::min<int64_t>(panels, 1 << 30), dim3(32, nw), smem, st>>>(p);
     return cudaGetLastError();
 }
 
-template <typename T, typename TW>
-cudaError_t launch_place(int act, int phase, const PlaceParams &p, int grid, cudaStream_t st)
+namespace detail {
+
+// Block of a multiple of 32 threads (<= 256) that splits n evenly into chunks.
+inline void node_grid(int64_t nx, int64_t ny, int64_t nz, dim3 *grid, dim3 *block)
 {
-    switch (act * 2 + phase) {
-    case ACT_1D * 2 + 1: k_place<T, TW, ACT_1D, 1><<<grid, kRowThreads, 0, st>>>(p); break;
-    case ACT_2D * 2 + 0: k_place<T, TW, ACT_2D, 0><<<grid, kRowThreads, 0, st>>>(p); break;
-    case ACT_2D * 2 + 1: k_place<T, TW, ACT_2D, 1><<<grid, kRowThreads, 0, st>>>(p); break;
-    case ACT_3D * 2 + 0: k_place<T, TW, ACT_3D, 0><<<grid, kRowThreads, 0, st>>>(p); break;
-    case ACT_3D * 2 + 1: k_place<T, TW, ACT_3D, 1><<<grid, kRowThreads, 0, st>>>(p); break;
+    const int64_t chunks = (nx + 255) / 256;
+    int64_t bx = (nx + chunks - 1) / chunks;
+    bx = (bx + 31) / 32 * 32;
+    *block = dim3((unsigned)bx);
+    *grid = dim3((unsigned)((nx + bx - 1) / bx), (unsigned)std::min<int64_t>(ny, 65535),
+                 (unsigned)std::min<int64_t>(nz, 65535));
+}
+
+}  // namespace detail
+
+template <typename T, typename TW>
+cudaError_t launch_coef(int act, const PlaceParams &p, cudaStream_t st)
+{
+    dim3 g, b;
+    detail::node_grid(p.n2, p.n1, p.n0, &g, &b);
+    switch (act) {
+    case ACT_1D: k_coef<T, TW, ACT_1D><<<g, b, 0, st>>>(p); break;
+    case ACT_2D: k_coef<T, TW, ACT_2D><<<g, b, 0, st>>>(p); break;
+    case ACT_3D: k_coef<T, TW, ACT_3D><<<g, b, 0, st>>>(p); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
 template <typename T, typename TW>
-cudaError_t launch_interp(int act, const PlaceParams &p, int grid, cudaStream_t st)
+cudaError_t launch_scatter(int act, const PlaceParams &p, cudaStream_t st)
 {
+    dim3 g, b;
+    detail::node_grid(p.m2, p.m1, p.m0, &g, &b);
     switch (act) {
-    case ACT_1D: k_interp<T, TW, ACT_1D><<<grid, kRowThreads, 0, st>>>(p); break;
-    case ACT_2D: k_interp<T, TW, ACT_2D><<<grid, kRowThreads, 0, st>>>(p); break;
-    case ACT_3D: k_interp<T, TW, ACT_3D><<<grid, kRowThreads, 0, st>>>(p); break;
+    case ACT_1D: k_scatter<T, TW, ACT_1D><<<g, b, 0, st>>>(p); break;
+    case ACT_2D: k_scatter<T, TW, ACT_2D><<<g, b, 0, st>>>(p); break;
+    case ACT_3D: k_scatter<T, TW, ACT_3D><<<g, b, 0, st>>>(p); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, typename TW>
+cudaError_t launch_interp(int act, const PlaceParams &p, cudaStream_t st)
+{
+    dim3 g, b;
+    detail::node_grid(p.n2, p.n1, p.n0, &g, &b);
+    switch (act) {
+    case ACT_1D: k_interp<T, TW, ACT_1D><<<g, b, 0, st>>>(p); break;
+    case ACT_2D: k_interp<T, TW, ACT_2D><<<g, b, 0, st>>>(p); break;
+    case ACT_3D: k_interp<T, TW, ACT_3D><<<g, b, 0, st>>>(p); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -165,10 +177,11 @@ cudaError_t launch_interp(int act, const PlaceParams &p, int grid, cudaStream_t 
     template cudaError_t restrict_shape<T, TW>(int, int, int, RestrictShape *);                  \
     template cudaError_t launch_restrict<T, TW>(int, int, int, const RestrictParams &, int,     \
                                                 cudaStream_t);                                   \
-    template cudaError_t launch_place<T, TW>(int, int, const PlaceParams &, int, cudaStream_t); \
-    template cudaError_t launch_interp<T, TW>(int, const PlaceParams &, int, cudaStream_t);
+    template cudaError_t launch_coef<T, TW>(int, const PlaceParams &, cudaStream_t);            \
+    template cudaError_t launch_scatter<T, TW>(int, const PlaceParams &, cudaStream_t);         \
+    template cudaError_t launch_interp<T, TW>(int, const PlaceParams &, cudaStream_t);
 
 #define MG_INSTANTIATE_SOLVE(TW) \
-    template cudaError_t launch_solve<TW>(const SolveParams &, bool, bool, cudaStream_t);
+    template cudaError_t launch_solve<TW>(const SolveParams &, int, cudaStream_t);
 
 }  // namespace mg

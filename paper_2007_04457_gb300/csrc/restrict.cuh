@@ -120,8 +120,16 @@ __device__ __forceinline__ void stencil2(const T (&ka)[5], const T (&kb)[5], T c
     hb = fma_rn(kb[4], crr, hb);
 }
 
+// Resident blocks per SM the register allocation is sized for: 4 for the
+// small FP32 tiles (49 KB of shared memory), 2 otherwise.
+template <typename T, int TY_>
+constexpr int restrict_min_blocks()
+{
+    return (sizeof(T) == 4 && TY_ <= 4) ? 4 : 2;
+}
+
 template <typename T, typename TW, int ACT, int MODE, int TY_>
-__global__ void __launch_bounds__(kRestrictThreads)
+__global__ void __launch_bounds__(kRestrictThreads, (restrict_min_blocks<T, TY_>()))
 k_restrict(RestrictParams p)
 {
     using G = RestrictGeom<T, ACT, MODE, TY_>;
