@@ -118,7 +118,7 @@ MGARD_API mgard_status mgard_recompose(const mgard_plan *plan, void *d_data, voi
  * and kernel variants are affected.
  *   param 0  restriction tile: 0 = 8 x 64, 1 = 4 x 64, 2 = 16 x 64 coarse nodes
  *   param 1  warps (chunks) per line in the correction solves, 1..32, or
- *            0 = automatic (about 8 nodes per chunk)
+ *            0 = automatic (about 16 nodes per chunk)
  *   param 2  coarse planes per restriction work item (0 = automatic)
  * Returns MGARD_ERR_INVALID_ARG for an unknown parameter or value. */
 MGARD_API mgard_status mgard_plan_tune(mgard_plan *plan, int level, int param, int value);

@@ -600,6 +600,7 @@ mgard_status mgard_plan_tune(mgard_plan *P, int level, int param, int value)
 {
     if (!P || level < 0 || level >= P->L) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: bad plan or level");
     mgard_level &L = P->lv[level];
+    const mgard_level saved = L;
     switch (param) {
     case 0:
         if (value < 0 || value >= kRestrictConfigs) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: tile config");
@@ -616,7 +617,11 @@ mgard_status mgard_plan_tune(mgard_plan *P, int level, int param, int value)
     default: return fail(MGARD_ERR_INVALID_ARG, "plan_tune: unknown parameter");
     }
     cudaError_t err = reconfigure(P, level);
-    if (err != cudaSuccess) return cuda_fail(err, "plan_tune");
+    if (err != cudaSuccess) {
+        L = saved;  // keep the previous, working configuration
+        cudaGetLastError();
+        return cuda_fail(err, "plan_tune: configuration not supported on this device");
+    }
     return MGARD_OK;
 }
 

@@ -1,6 +1,6 @@
-// interp.cuh -- the element-wise level kernels: one thread per fine node on
-// a (x-chunk, row, plane) grid, so every kernel runs at full occupancy with
-// independent loads in flight; the interpolation corners are re-read from L1.
+// interp.cuh -- the element-wise level kernels, on a (x-chunk, row, plane)
+// grid of small threads so every kernel runs at full occupancy with many
+// independent loads in flight; interpolation corners are re-read from L1.
 //
 // k_coef (decomposition, after the coarser levels are done): every node of
 //   N_l \ N_{l-1} receives its coefficient u - Pi_{l-1} u, recomputed from the
@@ -40,6 +40,9 @@ __device__ __forceinline__ NodeIter node_iter()
     return it;
 }
 
+// Each thread of k_coef / k_interp handles the 4 consecutive nodes
+// x0 .. x0+3 (x0 = 4t) of one row, so the even corner columns x0, x0+2,
+// x0+4 of every row it interpolates from are loaded once for four nodes.
 template <typename T, typename TW, int ACT>
 __global__ void __launch_bounds__(kRowThreads) k_coef(PlaceParams p)
 {
@@ -50,36 +53,57 @@ __global__ void __launch_bounds__(kRowThreads) k_coef(PlaceParams p)
     const T *__restrict__ w2 = static_cast<const T *>(p.w2);
     const int64_t n0 = p.n0, n1 = p.n1, n2 = p.n2;
     const NodeIter it = node_iter();
-    const int64_t x = it.x;
-    if (x >= n2) return;
-    const bool ox = (x & 1);
-    const T wxa = ox ? w2[2 * x] : T(0), wxb = ox ? w2[2 * x + 1] : T(0);
-    const int64_t xl = ox ? x - 1 : x, xr = ox ? x + 1 : x;
+    const int64_t x0 = 4 * it.x;
+    if (x0 >= n2) return;
+    const int nk = (int)min64(4, n2 - x0);
+    const bool has2 = x0 + 2 < n2, has4 = x0 + 4 < n2;
+    const T wa1 = (x0 + 1 < n2 - 1) ? w2[2 * (x0 + 1)] : T(0), wb1 = (x0 + 1 < n2 - 1) ? w2[2 * (x0 + 1) + 1] : T(0);
+    const T wa3 = (x0 + 3 < n2 - 1) ? w2[2 * (x0 + 3)] : T(0), wb3 = (x0 + 3 < n2 - 1) ? w2[2 * (x0 + 3) + 1] : T(0);
+    // x-interpolant of row r at the four nodes, from its even columns
+    auto X4 = [&](const T *r, T (&o)[4]) {
+        const T e0 = r[x0], e2 = has2 ? r[x0 + 2] : T(0), e4 = has4 ? r[x0 + 4] : T(0);
+        o[0] = e0;
+        o[1] = lerp2(wa1, e0, wb1, e2);
+        o[2] = e2;
+        o[3] = lerp2(wa3, e2, wb3, e4);
+    };
     for (int64_t z = it.z0; z < n0; z += it.zstep) {
         const bool oz = HZ && (z & 1);
         const T wza = oz ? w0[2 * z] : T(0), wzb = oz ? w0[2 * z + 1] : T(0);
         const int64_t za = oz ? z - 1 : z, zb = oz ? z + 1 : z;
         for (int64_t y = it.y0; y < n1; y += it.ystep) {
             const bool oy = HY && (y & 1);
-            T *a = A + (z * n1 + y) * n2 + x;
-            const T u = *a;
-            if (!ox && !oy && !oz) {
-                __stcg(a, u);  // coarse node: rewritten unchanged (opaque store keeps the
-                continue;      // sector whole); its final value comes from k_scatter
-            }
             const T wya = oy ? w1[2 * y] : T(0), wyb = oy ? w1[2 * y + 1] : T(0);
             const int64_t ya = oy ? y - 1 : y, yb = oy ? y + 1 : y;
-            auto X = [&](int64_t zz, int64_t yy) -> T {
-                const T *r = A + (zz * n1 + yy) * n2;
-                return ox ? lerp2(wxa, r[xl], wxb, r[xr]) : r[x];
-            };
-            const T ia = oy ? lerp2(wya, X(za, ya), wyb, X(za, yb)) : X(za, ya);
-            T iv = ia;
-            if (oz) {
-                const T ib = oy ? lerp2(wya, X(zb, ya), wyb, X(zb, yb)) : X(zb, ya);
-                iv = lerp2(wza, ia, wzb, ib);
+            T *arow = A + (z * n1 + y) * n2;
+            T u[4], I[4], t[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) u[k] = (k < nk) ? arow[x0 + k] : T(0);
+            X4(A + (za * n1 + ya) * n2, I);
+            if (oy) {
+                X4(A + (za * n1 + yb) * n2, t);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) I[k] = lerp2(wya, I[k], wyb, t[k]);
             }
-            *a = sub_rn(u, iv);
+            if (oz) {
+                T b[4];
+                X4(A + (zb * n1 + ya) * n2, b);
+                if (oy) {
+                    X4(A + (zb * n1 + yb) * n2, t);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) b[k] = lerp2(wya, b[k], wyb, t[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) I[k] = lerp2(wza, I[k], wzb, b[k]);
+            }
+            const bool eo = !oy && !oz;  // even row: even columns are coarse nodes
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (k < nk) {
+                    const T out = (eo && !(k & 1)) ? u[k] : sub_rn(u[k], I[k]);
+                    __stcg(arow + x0 + k, out);  // opaque store: coarse nodes are rewritten unchanged
+                }
+            }
         }
     }
 }
@@ -113,11 +137,22 @@ __global__ void __launch_bounds__(kRowThreads) k_interp(PlaceParams p)
     const T *__restrict__ w2 = static_cast<const T *>(p.w2);
     const int64_t n0 = p.n0, n1 = p.n1, n2 = p.n2, m1 = p.m1, m2 = p.m2;
     const NodeIter it = node_iter();
-    const int64_t x = it.x;
-    if (x >= n2) return;
-    const bool ox = (x & 1);
-    const int64_t Xa = x >> 1, Xb = ox ? Xa + 1 : Xa;
-    const T wxa = ox ? w2[2 * x] : T(0), wxb = ox ? w2[2 * x + 1] : T(0);
+    const int64_t x0 = 4 * it.x;
+    if (x0 >= n2) return;
+    const int nk = (int)min64(4, n2 - x0);
+    const int64_t X0 = x0 >> 1;
+    const bool has1 = X0 + 1 < m2, has2 = X0 + 2 < m2;
+    const T wa1 = (x0 + 1 < n2 - 1) ? w2[2 * (x0 + 1)] : T(0), wb1 = (x0 + 1 < n2 - 1) ? w2[2 * (x0 + 1) + 1] : T(0);
+    const T wa3 = (x0 + 3 < n2 - 1) ? w2[2 * (x0 + 3)] : T(0), wb3 = (x0 + 3 < n2 - 1) ? w2[2 * (x0 + 3) + 1] : T(0);
+    auto X4 = [&](const TW *r, T (&o)[4]) {
+        const T v0 = static_cast<T>(r[X0]);
+        const T v1 = has1 ? static_cast<T>(r[X0 + 1]) : T(0);
+        const T v2 = has2 ? static_cast<T>(r[X0 + 2]) : T(0);
+        o[0] = v0;
+        o[1] = lerp2(wa1, v0, wb1, v1);
+        o[2] = v1;
+        o[3] = lerp2(wa3, v1, wb3, v2);
+    };
     for (int64_t z = it.z0; z < n0; z += it.zstep) {
         const bool oz = HZ && (z & 1);
         const int64_t Za = HZ ? (z >> 1) : 0, Zb = Za + (oz ? 1 : 0);
@@ -125,24 +160,32 @@ __global__ void __launch_bounds__(kRowThreads) k_interp(PlaceParams p)
         for (int64_t y = it.y0; y < n1; y += it.ystep) {
             const bool oy = HY && (y & 1);
             const int64_t Ya = HY ? (y >> 1) : 0, Yb = Ya + (oy ? 1 : 0);
-            T *a = A + (z * n1 + y) * n2 + x;
-            auto X = [&](int64_t ZZ, int64_t YY) -> T {
-                const TW *r = V + (ZZ * m1 + YY) * m2;
-                return ox ? lerp2(wxa, static_cast<T>(r[Xa]), wxb, static_cast<T>(r[Xb])) : static_cast<T>(r[Xa]);
-            };
-            if (!ox && !oy && !oz) {
-                *a = X(Za, Ya);
-                continue;
-            }
-            const T c = *a;
             const T wya = oy ? w1[2 * y] : T(0), wyb = oy ? w1[2 * y + 1] : T(0);
-            const T ia = oy ? lerp2(wya, X(Za, Ya), wyb, X(Za, Yb)) : X(Za, Ya);
-            T iv = ia;
-            if (oz) {
-                const T ib = oy ? lerp2(wya, X(Zb, Ya), wyb, X(Zb, Yb)) : X(Zb, Ya);
-                iv = lerp2(wza, ia, wzb, ib);
+            T *arow = A + (z * n1 + y) * n2;
+            T c[4], I[4], t[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) c[k] = (k < nk) ? arow[x0 + k] : T(0);
+            X4(V + (Za * m1 + Ya) * m2, I);
+            if (oy) {
+                X4(V + (Za * m1 + Yb) * m2, t);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) I[k] = lerp2(wya, I[k], wyb, t[k]);
             }
-            *a = add_rn(c, iv);
+            if (oz) {
+                T b[4];
+                X4(V + (Zb * m1 + Ya) * m2, b);
+                if (oy) {
+                    X4(V + (Zb * m1 + Yb) * m2, t);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) b[k] = lerp2(wya, b[k], wyb, t[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) I[k] = lerp2(wza, I[k], wzb, b[k]);
+            }
+            const bool eo = !oy && !oz;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k < nk) arow[x0 + k] = (eo && !(k & 1)) ? I[k] : add_rn(c[k], I[k]);
         }
     }
 }

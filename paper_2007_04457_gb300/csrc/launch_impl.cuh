@@ -94,7 +94,7 @@ cudaError_t launch_solve(const SolveParams &p_in, int nw_req, cudaStream_t st)
 {
     SolveParams p = p_in;
     if (p.nlines <= 0) return cudaSuccess;
-    int nw = nw_req > 0 ? nw_req : std::min(32, std::max(1, (p.m + 7) / 8));
+    int nw = nw_req > 0 ? nw_req : std::min(32, std::max(1, (p.m + 15) / 16));
     nw = std::max(1, std::min(nw, std::min(32, p.m)));
     p.nw = nw;
     p.chunk = (p.m + nw - 1) / nw;
@@ -135,7 +135,7 @@ template <typename T, typename TW>
 cudaError_t launch_coef(int act, const PlaceParams &p, cudaStream_t st)
 {
     dim3 g, b;
-    detail::node_grid(p.n2, p.n1, p.n0, &g, &b);
+    detail::node_grid((p.n2 + 3) / 4, p.n1, p.n0, &g, &b);  // 4 nodes per thread
     switch (act) {
     case ACT_1D: k_coef<T, TW, ACT_1D><<<g, b, 0, st>>>(p); break;
     case ACT_2D: k_coef<T, TW, ACT_2D><<<g, b, 0, st>>>(p); break;
@@ -163,7 +163,7 @@ template <typename T, typename TW>
 cudaError_t launch_interp(int act, const PlaceParams &p, cudaStream_t st)
 {
     dim3 g, b;
-    detail::node_grid(p.n2, p.n1, p.n0, &g, &b);
+    detail::node_grid((p.n2 + 3) / 4, p.n1, p.n0, &g, &b);  // 4 nodes per thread
     switch (act) {
     case ACT_1D: k_interp<T, TW, ACT_1D><<<g, b, 0, st>>>(p); break;
     case ACT_2D: k_interp<T, TW, ACT_2D><<<g, b, 0, st>>>(p); break;
