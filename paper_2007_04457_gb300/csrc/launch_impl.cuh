@@ -104,15 +104,18 @@ cudaError_t launch_solve(const SolveParams &p_in, int nw_req, cudaStream_t st)
     const size_t smem = solve_panel_elems(p.m, lpb) * sizeof(TW);
     if (smem > kCap) return cudaErrorInvalidValue;
     p.lpb = lpb;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(k_solve_panel<TW>),
+    const bool reg = (p.chunk <= 16) && (nw <= kSolveRegWarps);
+    void (*fn)(SolveParams) = reg ? k_solve_panel<TW, 16> : k_solve_panel<TW, 0>;
+    static bool attr_set[2] = {false, false};
+    const int which = reg ? 0 : 1;
+    if (!attr_set[which]) {
+        cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCap);
         if (err != cudaSuccess) return err;
-        attr_set = true;
+        attr_set[which] = true;
     }
     const int64_t panels = (p.nlines + lpb - 1) / lpb;
-    k_solve_panel<TW><<<(unsigned)std::min<int64_t>(panels, 1 << 30), dim3(32, nw), smem, st>>>(p);
+    fn<<<(unsigned)std::min<int64_t>(panels, 1 << 30), dim3(32, nw), smem, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -131,11 +134,22 @@ inline void node_grid(int64_t nx, int64_t ny, int64_t nz, dim3 *grid, dim3 *bloc
 
 }  // namespace detail
 
+namespace detail {
+// one warp per 128-node row segment, 8 warps per block
+inline void segment_grid(const PlaceParams &p, dim3 *grid, dim3 *block)
+{
+    const int64_t segs = (p.n2 + kSeg - 1) / kSeg;
+    const int64_t warps = p.n0 * p.n1 * segs;
+    *block = dim3(kRowThreads);
+    *grid = dim3((unsigned)((warps + kRowThreads / 32 - 1) / (kRowThreads / 32)));
+}
+}  // namespace detail
+
 template <typename T, typename TW>
 cudaError_t launch_coef(int act, const PlaceParams &p, cudaStream_t st)
 {
     dim3 g, b;
-    detail::node_grid((p.n2 + 3) / 4, p.n1, p.n0, &g, &b);  // 4 nodes per thread
+    detail::segment_grid(p, &g, &b);
     switch (act) {
     case ACT_1D: k_coef<T, TW, ACT_1D><<<g, b, 0, st>>>(p); break;
     case ACT_2D: k_coef<T, TW, ACT_2D><<<g, b, 0, st>>>(p); break;
@@ -163,7 +177,7 @@ template <typename T, typename TW>
 cudaError_t launch_interp(int act, const PlaceParams &p, cudaStream_t st)
 {
     dim3 g, b;
-    detail::node_grid((p.n2 + 3) / 4, p.n1, p.n0, &g, &b);  // 4 nodes per thread
+    detail::segment_grid(p, &g, &b);
     switch (act) {
     case ACT_1D: k_interp<T, TW, ACT_1D><<<g, b, 0, st>>>(p); break;
     case ACT_2D: k_interp<T, TW, ACT_2D><<<g, b, 0, st>>>(p); break;

@@ -66,14 +66,78 @@ __device__ __forceinline__ void chunk_solve_smem(TW *row, const TW *fac, int s, 
     }
 }
 
+// The same on a chunk held in registers (CH >= len): one shared-memory read
+// and one write per node instead of four passes over shared memory.
+template <typename TW, int CH>
+__device__ __forceinline__ void chunk_solve_reg(TW *row, const TW *fac, int s, int len, int w, int nw,
+                                                TW *carry_a, TW *carry_b, int lane)
+{
+    TW r[CH];
+#pragma unroll
+    for (int j = 0; j < CH; ++j) r[j] = (j < len) ? row[s + j] : TW(0);
+    TW y = TW(0), pr = TW(1);
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+        if (j < len) {
+            const TW a = fac[3 * (s + j)];
+            y = r[j] - a * y;
+            pr = -a * pr;
+        }
+    }
+    carry_a[w * 32 + lane] = y;
+    carry_b[w * 32 + lane] = pr;
+    __syncthreads();
+    TW c = TW(0);
+    for (int k = 0; k < w; ++k) c = carry_a[k * 32 + lane] + carry_b[k * 32 + lane] * c;
+    __syncthreads();
+    y = c;
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+        if (j < len) {
+            y = r[j] - fac[3 * (s + j)] * y;
+            r[j] = y;
+        }
+    }
+    TW z = TW(0);
+    pr = TW(1);
+#pragma unroll
+    for (int j = CH - 1; j >= 0; --j) {
+        if (j < len) {
+            const TW inv = fac[3 * (s + j) + 1], q = fac[3 * (s + j) + 2];
+            z = inv * r[j] - q * z;
+            pr = -q * pr;
+        }
+    }
+    carry_a[w * 32 + lane] = z;
+    carry_b[w * 32 + lane] = pr;
+    __syncthreads();
+    c = TW(0);
+    for (int k = nw - 1; k > w; --k) c = carry_a[k * 32 + lane] + carry_b[k * 32 + lane] * c;
+    z = c;
+#pragma unroll
+    for (int j = CH - 1; j >= 0; --j) {
+        if (j < len) {
+            z = fac[3 * (s + j) + 1] * r[j] - fac[3 * (s + j) + 2] * z;
+            r[j] = z;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < CH; ++j)
+        if (j < len) row[s + j] = r[j];
+}
+
 // Shared memory of k_solve_panel, in elements of TW.
 inline size_t solve_panel_elems(int m, int lpb)
 {
     return 2 * 32 * 32 + 3 * (size_t)m + 1 + (size_t)lpb * (size_t)(m | 1);
 }
 
-template <typename TW>
-__global__ void __launch_bounds__(1024, 2) k_solve_panel(SolveParams p)
+// CH > 0: chunks of at most CH nodes held in registers (at most 18 warps per
+// block); CH = 0: chunks of any length solved in shared memory.
+constexpr int kSolveRegWarps = 18;
+
+template <typename TW, int CH>
+__global__ void __launch_bounds__(CH > 0 ? 32 * kSolveRegWarps : 1024, 2) k_solve_panel(SolveParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TW *carry_a = reinterpret_cast<TW *>(smem_raw);
@@ -118,7 +182,10 @@ __global__ void __launch_bounds__(1024, 2) k_solve_panel(SolveParams p)
         cp_async_wait<0>();
         __syncthreads();
 
-        chunk_solve_smem<TW>(tile + lane * pitch, sfac, s, len, w, nw, carry_a, carry_b, lane);
+        if constexpr (CH > 0)
+            chunk_solve_reg<TW, CH>(tile + lane * pitch, sfac, s, len, w, nw, carry_a, carry_b, lane);
+        else
+            chunk_solve_smem<TW>(tile + lane * pitch, sfac, s, len, w, nw, carry_a, carry_b, lane);
         __syncthreads();
 
         // write back
