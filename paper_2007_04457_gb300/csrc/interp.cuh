@@ -40,27 +40,9 @@ __device__ __forceinline__ NodeIter node_iter()
     return it;
 }
 
-// k_coef / k_interp: a warp takes a 128-node segment of one row; lane L
-// handles the nodes base + L + 32k (k < 4), so every load is one coalesced
-// 128-byte access.  An odd node's even neighbours x-1 and x+1 come from the
-// adjacent lanes by shuffle (lane 31 takes x+1 from lane 0 of the next
-// group, or loads it after the last group).
-constexpr int kSegChunks = 4;
-constexpr int kSeg = 32 * kSegChunks;
-
-template <typename T>
-__device__ __forceinline__ void odd_neighbours(const T (&e)[kSegChunks], T extra, int lane, T (&left)[kSegChunks],
-                                               T (&right)[kSegChunks])
-{
-#pragma unroll
-    for (int k = 0; k < kSegChunks; ++k) {
-        left[k] = __shfl_up_sync(0xffffffffu, e[k], 1);
-        const T dn = __shfl_down_sync(0xffffffffu, e[k], 1);
-        const T nx = (k + 1 < kSegChunks) ? __shfl_sync(0xffffffffu, e[(k + 1) % kSegChunks], 0) : extra;
-        right[k] = (lane == 31) ? nx : dn;
-    }
-}
-
+// Each thread of k_coef / k_interp handles the 4 consecutive nodes
+// x0 .. x0+3 (x0 = 4t) of one row, so the even corner columns x0, x0+2,
+// x0+4 of every row it interpolates from are loaded once for four nodes.
 template <typename T, typename TW, int ACT>
 __global__ void __launch_bounds__(kRowThreads) k_coef(PlaceParams p)
 {
@@ -70,64 +52,60 @@ __global__ void __launch_bounds__(kRowThreads) k_coef(PlaceParams p)
     const T *__restrict__ w1 = static_cast<const T *>(p.w1);
     const T *__restrict__ w2 = static_cast<const T *>(p.w2);
     const int64_t n0 = p.n0, n1 = p.n1, n2 = p.n2;
-    const int lane = threadIdx.x & 31;
-    const int64_t segs = (n2 + kSeg - 1) / kSeg;
-    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    if (wid >= n0 * n1 * segs) return;  // whole warps only
-    const int64_t row = wid / segs, base = (wid - row * segs) * kSeg;
-    const int64_t z = row / n1, y = row - (row / n1) * n1;
-    const bool ox = lane & 1;
-    const bool oz = HZ && (z & 1), oy = HY && (y & 1);
-    const T wza = oz ? w0[2 * z] : T(0), wzb = oz ? w0[2 * z + 1] : T(0);
-    const T wya = oy ? w1[2 * y] : T(0), wyb = oy ? w1[2 * y + 1] : T(0);
-    const int64_t za = oz ? z - 1 : z, zb = oz ? z + 1 : z;
-    const int64_t ya = oy ? y - 1 : y, yb = oy ? y + 1 : y;
-    T wa[kSegChunks], wb[kSegChunks];
-    bool valid[kSegChunks];
-#pragma unroll
-    for (int k = 0; k < kSegChunks; ++k) {
-        const int64_t x = base + lane + 32 * k;
-        valid[k] = x < n2;
-        const bool wok = ox && x < n2 - 1;
-        wa[k] = wok ? w2[2 * x] : T(0);
-        wb[k] = wok ? w2[2 * x + 1] : T(0);
-    }
-    const bool has_extra = base + kSeg < n2;
-    // x-interpolant of row r at the lane's nodes (even nodes: the value itself)
-    auto Xrow = [&](const T *r, T (&o)[kSegChunks]) {
-        T e[kSegChunks], l[kSegChunks], rr[kSegChunks];
-#pragma unroll
-        for (int k = 0; k < kSegChunks; ++k) e[k] = valid[k] ? r[base + lane + 32 * k] : T(0);
-        const T extra = has_extra ? r[base + kSeg] : T(0);
-        odd_neighbours(e, extra, lane, l, rr);
-#pragma unroll
-        for (int k = 0; k < kSegChunks; ++k) o[k] = ox ? lerp2(wa[k], l[k], wb[k], rr[k]) : e[k];
+    const NodeIter it = node_iter();
+    const int64_t x0 = 4 * it.x;
+    if (x0 >= n2) return;
+    const int nk = (int)min64(4, n2 - x0);
+    const bool has2 = x0 + 2 < n2, has4 = x0 + 4 < n2;
+    const T wa1 = (x0 + 1 < n2 - 1) ? w2[2 * (x0 + 1)] : T(0), wb1 = (x0 + 1 < n2 - 1) ? w2[2 * (x0 + 1) + 1] : T(0);
+    const T wa3 = (x0 + 3 < n2 - 1) ? w2[2 * (x0 + 3)] : T(0), wb3 = (x0 + 3 < n2 - 1) ? w2[2 * (x0 + 3) + 1] : T(0);
+    // x-interpolant of row r at the four nodes, from its even columns
+    auto X4 = [&](const T *r, T (&o)[4]) {
+        const T e0 = r[x0], e2 = has2 ? r[x0 + 2] : T(0), e4 = has4 ? r[x0 + 4] : T(0);
+        o[0] = e0;
+        o[1] = lerp2(wa1, e0, wb1, e2);
+        o[2] = e2;
+        o[3] = lerp2(wa3, e2, wb3, e4);
     };
-    T *arow = A + row * n2;
-    T u[kSegChunks], I[kSegChunks], t[kSegChunks];
+    for (int64_t z = it.z0; z < n0; z += it.zstep) {
+        const bool oz = HZ && (z & 1);
+        const T wza = oz ? w0[2 * z] : T(0), wzb = oz ? w0[2 * z + 1] : T(0);
+        const int64_t za = oz ? z - 1 : z, zb = oz ? z + 1 : z;
+        for (int64_t y = it.y0; y < n1; y += it.ystep) {
+            const bool oy = HY && (y & 1);
+            const T wya = oy ? w1[2 * y] : T(0), wyb = oy ? w1[2 * y + 1] : T(0);
+            const int64_t ya = oy ? y - 1 : y, yb = oy ? y + 1 : y;
+            T *arow = A + (z * n1 + y) * n2;
+            T u[4], I[4], t[4];
 #pragma unroll
-    for (int k = 0; k < kSegChunks; ++k) u[k] = valid[k] ? arow[base + lane + 32 * k] : T(0);
-    Xrow(A + (za * n1 + ya) * n2, I);
-    if (oy) {
-        Xrow(A + (za * n1 + yb) * n2, t);
+            for (int k = 0; k < 4; ++k) u[k] = (k < nk) ? arow[x0 + k] : T(0);
+            X4(A + (za * n1 + ya) * n2, I);
+            if (oy) {
+                X4(A + (za * n1 + yb) * n2, t);
 #pragma unroll
-        for (int k = 0; k < kSegChunks; ++k) I[k] = lerp2(wya, I[k], wyb, t[k]);
-    }
-    if (oz) {
-        T b[kSegChunks];
-        Xrow(A + (zb * n1 + ya) * n2, b);
-        if (oy) {
-            Xrow(A + (zb * n1 + yb) * n2, t);
+                for (int k = 0; k < 4; ++k) I[k] = lerp2(wya, I[k], wyb, t[k]);
+            }
+            if (oz) {
+                T b[4];
+                X4(A + (zb * n1 + ya) * n2, b);
+                if (oy) {
+                    X4(A + (zb * n1 + yb) * n2, t);
 #pragma unroll
-            for (int k = 0; k < kSegChunks; ++k) b[k] = lerp2(wya, b[k], wyb, t[k]);
+                    for (int k = 0; k < 4; ++k) b[k] = lerp2(wya, b[k], wyb, t[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) I[k] = lerp2(wza, I[k], wzb, b[k]);
+            }
+            const bool eo = !oy && !oz;  // even row: even columns are coarse nodes
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (k < nk) {
+                    const T out = (eo && !(k & 1)) ? u[k] : sub_rn(u[k], I[k]);
+                    __stcg(arow + x0 + k, out);  // opaque store: coarse nodes are rewritten unchanged
+                }
+            }
         }
-#pragma unroll
-        for (int k = 0; k < kSegChunks; ++k) I[k] = lerp2(wza, I[k], wzb, b[k]);
     }
-    const bool coarse = !oy && !oz && !ox;  // even node of an even row: rewritten unchanged
-#pragma unroll
-    for (int k = 0; k < kSegChunks; ++k)
-        if (valid[k]) __stcg(arow + base + lane + 32 * k, coarse ? u[k] : sub_rn(u[k], I[k]));
 }
 
 template <typename T, typename TW, int ACT>
@@ -158,66 +136,58 @@ __global__ void __launch_bounds__(kRowThreads) k_interp(PlaceParams p)
     const T *__restrict__ w1 = static_cast<const T *>(p.w1);
     const T *__restrict__ w2 = static_cast<const T *>(p.w2);
     const int64_t n0 = p.n0, n1 = p.n1, n2 = p.n2, m1 = p.m1, m2 = p.m2;
-    const int lane = threadIdx.x & 31;
-    const int64_t segs = (n2 + kSeg - 1) / kSeg;
-    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    if (wid >= n0 * n1 * segs) return;  // whole warps only
-    const int64_t row = wid / segs, base = (wid - row * segs) * kSeg;
-    const int64_t z = row / n1, y = row - (row / n1) * n1;
-    const bool ox = lane & 1;
-    const bool oz = HZ && (z & 1), oy = HY && (y & 1);
-    const int64_t Za = HZ ? (z >> 1) : 0, Zb = Za + (oz ? 1 : 0);
-    const int64_t Ya = HY ? (y >> 1) : 0, Yb = Ya + (oy ? 1 : 0);
-    const T wza = oz ? w0[2 * z] : T(0), wzb = oz ? w0[2 * z + 1] : T(0);
-    const T wya = oy ? w1[2 * y] : T(0), wyb = oy ? w1[2 * y + 1] : T(0);
-    T wa[kSegChunks], wb[kSegChunks];
-    bool valid[kSegChunks];
-#pragma unroll
-    for (int k = 0; k < kSegChunks; ++k) {
-        const int64_t x = base + lane + 32 * k;
-        valid[k] = x < n2;
-        const bool wok = ox && x < n2 - 1;
-        wa[k] = wok ? w2[2 * x] : T(0);
-        wb[k] = wok ? w2[2 * x + 1] : T(0);
-    }
-    const bool has_extra = base + kSeg < n2;
-    // x-interpolant of coarse row r at the lane's fine nodes: node x reads
-    // V[x/2]; an odd node takes V[x/2 + 1] from the next lane
-    auto Xrow = [&](const TW *r, T (&o)[kSegChunks]) {
-        T e[kSegChunks], l[kSegChunks], rr[kSegChunks];
-#pragma unroll
-        for (int k = 0; k < kSegChunks; ++k) e[k] = valid[k] ? static_cast<T>(r[(base + lane + 32 * k) >> 1]) : T(0);
-        const T extra = has_extra ? static_cast<T>(r[(base + kSeg) >> 1]) : T(0);
-        odd_neighbours(e, extra, lane, l, rr);
-#pragma unroll
-        for (int k = 0; k < kSegChunks; ++k) o[k] = ox ? lerp2(wa[k], e[k], wb[k], rr[k]) : e[k];
-        (void)l;
+    const NodeIter it = node_iter();
+    const int64_t x0 = 4 * it.x;
+    if (x0 >= n2) return;
+    const int nk = (int)min64(4, n2 - x0);
+    const int64_t X0 = x0 >> 1;
+    const bool has1 = X0 + 1 < m2, has2 = X0 + 2 < m2;
+    const T wa1 = (x0 + 1 < n2 - 1) ? w2[2 * (x0 + 1)] : T(0), wb1 = (x0 + 1 < n2 - 1) ? w2[2 * (x0 + 1) + 1] : T(0);
+    const T wa3 = (x0 + 3 < n2 - 1) ? w2[2 * (x0 + 3)] : T(0), wb3 = (x0 + 3 < n2 - 1) ? w2[2 * (x0 + 3) + 1] : T(0);
+    auto X4 = [&](const TW *r, T (&o)[4]) {
+        const T v0 = static_cast<T>(r[X0]);
+        const T v1 = has1 ? static_cast<T>(r[X0 + 1]) : T(0);
+        const T v2 = has2 ? static_cast<T>(r[X0 + 2]) : T(0);
+        o[0] = v0;
+        o[1] = lerp2(wa1, v0, wb1, v1);
+        o[2] = v1;
+        o[3] = lerp2(wa3, v1, wb3, v2);
     };
-    T *arow = A + row * n2;
-    T c[kSegChunks], I[kSegChunks], t[kSegChunks];
+    for (int64_t z = it.z0; z < n0; z += it.zstep) {
+        const bool oz = HZ && (z & 1);
+        const int64_t Za = HZ ? (z >> 1) : 0, Zb = Za + (oz ? 1 : 0);
+        const T wza = oz ? w0[2 * z] : T(0), wzb = oz ? w0[2 * z + 1] : T(0);
+        for (int64_t y = it.y0; y < n1; y += it.ystep) {
+            const bool oy = HY && (y & 1);
+            const int64_t Ya = HY ? (y >> 1) : 0, Yb = Ya + (oy ? 1 : 0);
+            const T wya = oy ? w1[2 * y] : T(0), wyb = oy ? w1[2 * y + 1] : T(0);
+            T *arow = A + (z * n1 + y) * n2;
+            T c[4], I[4], t[4];
 #pragma unroll
-    for (int k = 0; k < kSegChunks; ++k) c[k] = valid[k] ? arow[base + lane + 32 * k] : T(0);
-    Xrow(V + (Za * m1 + Ya) * m2, I);
-    if (oy) {
-        Xrow(V + (Za * m1 + Yb) * m2, t);
+            for (int k = 0; k < 4; ++k) c[k] = (k < nk) ? arow[x0 + k] : T(0);
+            X4(V + (Za * m1 + Ya) * m2, I);
+            if (oy) {
+                X4(V + (Za * m1 + Yb) * m2, t);
 #pragma unroll
-        for (int k = 0; k < kSegChunks; ++k) I[k] = lerp2(wya, I[k], wyb, t[k]);
-    }
-    if (oz) {
-        T b[kSegChunks];
-        Xrow(V + (Zb * m1 + Ya) * m2, b);
-        if (oy) {
-            Xrow(V + (Zb * m1 + Yb) * m2, t);
+                for (int k = 0; k < 4; ++k) I[k] = lerp2(wya, I[k], wyb, t[k]);
+            }
+            if (oz) {
+                T b[4];
+                X4(V + (Zb * m1 + Ya) * m2, b);
+                if (oy) {
+                    X4(V + (Zb * m1 + Yb) * m2, t);
 #pragma unroll
-            for (int k = 0; k < kSegChunks; ++k) b[k] = lerp2(wya, b[k], wyb, t[k]);
+                    for (int k = 0; k < 4; ++k) b[k] = lerp2(wya, b[k], wyb, t[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) I[k] = lerp2(wza, I[k], wzb, b[k]);
+            }
+            const bool eo = !oy && !oz;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k < nk) arow[x0 + k] = (eo && !(k & 1)) ? I[k] : add_rn(c[k], I[k]);
         }
-#pragma unroll
-        for (int k = 0; k < kSegChunks; ++k) I[k] = lerp2(wza, I[k], wzb, b[k]);
     }
-    const bool coarse = !oy && !oz && !ox;
-#pragma unroll
-    for (int k = 0; k < kSegChunks; ++k)
-        if (valid[k]) arow[base + lane + 32 * k] = coarse ? I[k] : add_rn(c[k], I[k]);
 }
 
 }  // namespace mg

@@ -134,22 +134,11 @@ inline void node_grid(int64_t nx, int64_t ny, int64_t nz, dim3 *grid, dim3 *bloc
 
 }  // namespace detail
 
-namespace detail {
-// one warp per 128-node row segment, 8 warps per block
-inline void segment_grid(const PlaceParams &p, dim3 *grid, dim3 *block)
-{
-    const int64_t segs = (p.n2 + kSeg - 1) / kSeg;
-    const int64_t warps = p.n0 * p.n1 * segs;
-    *block = dim3(kRowThreads);
-    *grid = dim3((unsigned)((warps + kRowThreads / 32 - 1) / (kRowThreads / 32)));
-}
-}  // namespace detail
-
 template <typename T, typename TW>
 cudaError_t launch_coef(int act, const PlaceParams &p, cudaStream_t st)
 {
     dim3 g, b;
-    detail::segment_grid(p, &g, &b);
+    detail::node_grid((p.n2 + 3) / 4, p.n1, p.n0, &g, &b);  // 4 nodes per thread
     switch (act) {
     case ACT_1D: k_coef<T, TW, ACT_1D><<<g, b, 0, st>>>(p); break;
     case ACT_2D: k_coef<T, TW, ACT_2D><<<g, b, 0, st>>>(p); break;
@@ -177,7 +166,7 @@ template <typename T, typename TW>
 cudaError_t launch_interp(int act, const PlaceParams &p, cudaStream_t st)
 {
     dim3 g, b;
-    detail::segment_grid(p, &g, &b);
+    detail::node_grid((p.n2 + 3) / 4, p.n1, p.n0, &g, &b);  // 4 nodes per thread
     switch (act) {
     case ACT_1D: k_interp<T, TW, ACT_1D><<<g, b, 0, st>>>(p); break;
     case ACT_2D: k_interp<T, TW, ACT_2D><<<g, b, 0, st>>>(p); break;
