@@ -153,6 +153,21 @@ MGARD_API mgard_status mgard_profile_enable(mgard_plan *plan, int levels);
 MGARD_API int mgard_profile_read(mgard_plan *plan, int cap, int *kinds, int *levels_out,
                                  int *launches, double *ms);
 
+/* Transposes of the two linear maps, in place, same arguments as
+ * mgard_decompose: d_data holds a cotangent of the map's output and receives
+ * the cotangent of its input (back-propagation through the map).  Per level,
+ * with K = R M_l the restriction stencil and M_l P = K^T (M symmetric):
+ *   decomposition^T  w = c_bar + [K^T M_{l-1}^{-1} e_bar]_odd,
+ *                    e_bar <- e_bar - Pi^T w        (coarsest level first)
+ *   recomposition^T  e_tot = e_bar + Pi^T o_bar,
+ *                    o_bar <- o_bar - [K^T M_{l-1}^{-1} e_tot]_odd
+ *                                                   (finest level first)
+ * (transposes of Section II-A, Eq. 1-2). */
+MGARD_API mgard_status mgard_decompose_adjoint(const mgard_plan *plan, void *d_data, void *d_ws,
+                                     size_t ws_bytes, void *stream);
+MGARD_API mgard_status mgard_recompose_adjoint(const mgard_plan *plan, void *d_data, void *d_ws,
+                                     size_t ws_bytes, void *stream);
+
 /* Human-readable name of a status code (static string). */
 MGARD_API const char *mgard_status_string(mgard_status status);
 

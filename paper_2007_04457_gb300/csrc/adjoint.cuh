@@ -1,0 +1,164 @@
+// adjoint.cuh -- kernels of the transposed level maps (decomposition and
+// recomposition are linear; their transposes back-propagate gradients).
+//
+// With o = nodes of N_l \ N_{l-1}, e = nodes of N_{l-1}, K = P^T M_l (the
+// 5-point restriction stencil of the forward maps; M_l P = K^T because M_l
+// is symmetric) and Pi^T the transposed interpolation:
+//   decomposition step  o' = o - Pi e,  e' = e + M_{l-1}^{-1} K (o - Pi e)
+//   its transpose       w = o_bar' + [K^T M_{l-1}^{-1} e_bar']_o,
+//                       o_bar = w,  e_bar = e_bar' - Pi^T w
+//   recomposition step  e_new = e - M_{l-1}^{-1} K o,  o_new = o + Pi e_new
+//   its transpose       e_tot = e_bar_new + Pi^T o_bar_new,
+//                       o_bar = o_bar_new - [K^T M_{l-1}^{-1} e_tot]_o,
+//                       e_bar = e_tot
+// (Section II-A, Eq. 1-2, transposed; M_{l-1} is symmetric).
+//
+// k_gather:  compact V <- the N_{l-1} nodes of the level array.
+// k_adj_odd: A(o) <- A(o) + s (K^T z)(o) for every node of N_l \ N_{l-1}.
+// k_adj_even: A(e) <- B(e) + s (Pi^T A|_o)(e) for every node of N_{l-1}, B
+//   either A itself or the compact V; reads only nodes of N_l \ N_{l-1} and
+//   writes only nodes of N_{l-1}, so threads never race.
+#pragma once
+
+#include "common.cuh"
+#include "params.h"
+
+namespace mg {
+
+constexpr int kAdjThreads = 256;
+
+template <typename T, typename TW, int ACT>
+__global__ void __launch_bounds__(kAdjThreads) k_gather(PlaceParams p)
+{
+    constexpr bool HZ = (ACT & 4) != 0, HY = (ACT & 2) != 0;
+    const T *__restrict__ A = static_cast<const T *>(p.A);
+    TW *__restrict__ V = const_cast<TW *>(static_cast<const TW *>(p.V));
+    const int64_t X = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (X >= p.m2) return;
+    for (int64_t Z = blockIdx.z; Z < p.m0; Z += gridDim.z) {
+        const int64_t z = HZ ? 2 * Z : 0;
+        for (int64_t Y = blockIdx.y; Y < p.m1; Y += gridDim.y) {
+            const int64_t y = HY ? 2 * Y : 0;
+            V[(Z * p.m1 + Y) * p.m2 + X] = static_cast<TW>(A[(z * p.n1 + y) * p.n2 + 2 * X]);
+        }
+    }
+}
+
+// Coarse neighbours of fine index j along one dimension with their K^T
+// weights: even j = 2I: I-1 (t=4), I (t=2), I+1 (t=0); odd j = 2I+1:
+// I (t=3), I+1 (t=1).  Returns the count (<= 3).
+template <typename TW>
+__device__ __forceinline__ int kt_support(int64_t j, int64_t m, const TW *k, int64_t (&I)[3], TW (&w)[3])
+{
+    int c = 0;
+    if (!(j & 1)) {
+        const int64_t I0 = j >> 1;
+        if (I0 - 1 >= 0) { I[c] = I0 - 1; w[c] = k[5 * (I0 - 1) + 4]; ++c; }
+        I[c] = I0; w[c] = k[5 * I0 + 2]; ++c;
+        if (I0 + 1 < m) { I[c] = I0 + 1; w[c] = k[5 * (I0 + 1)]; ++c; }
+    } else {
+        const int64_t I0 = j >> 1;
+        I[c] = I0; w[c] = k[5 * I0 + 3]; ++c;
+        if (I0 + 1 < m) { I[c] = I0 + 1; w[c] = k[5 * (I0 + 1) + 1]; ++c; }
+    }
+    return c;
+}
+
+template <typename T, typename TW, int ACT>
+__global__ void __launch_bounds__(kAdjThreads) k_adj_odd(AdjParams p)
+{
+    constexpr bool HZ = (ACT & 4) != 0, HY = (ACT & 2) != 0;
+    T *__restrict__ A = static_cast<T *>(p.A);
+    const TW *__restrict__ Z = static_cast<const TW *>(p.Z);
+    const TW *k0 = static_cast<const TW *>(p.k0);
+    const TW *k1 = static_cast<const TW *>(p.k1);
+    const TW *k2 = static_cast<const TW *>(p.k2);
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.n2) return;
+    int64_t Ix[3];
+    TW wx[3];
+    const int cx = kt_support(x, p.m2, k2, Ix, wx);
+    for (int64_t z = blockIdx.z; z < p.n0; z += gridDim.z) {
+        int64_t Iz[3] = {0, 0, 0};
+        TW wz[3] = {TW(1), TW(0), TW(0)};
+        const int cz = HZ ? kt_support(z, p.m0, k0, Iz, wz) : 1;
+        for (int64_t y = blockIdx.y; y < p.n1; y += gridDim.y) {
+            const bool odd = (x & 1) || (HY && (y & 1)) || (HZ && (z & 1));
+            if (!odd) continue;
+            int64_t Iy[3] = {0, 0, 0};
+            TW wy[3] = {TW(1), TW(0), TW(0)};
+            const int cy = HY ? kt_support(y, p.m1, k1, Iy, wy) : 1;
+            TW g = TW(0);
+            for (int a = 0; a < cz; ++a) {
+                TW gy = TW(0);
+                for (int b = 0; b < cy; ++b) {
+                    const TW *zr = Z + (Iz[a] * p.m1 + Iy[b]) * p.m2;
+                    TW gx = TW(0);
+                    for (int c = 0; c < cx; ++c) gx += wx[c] * zr[Ix[c]];
+                    gy += wy[b] * gx;
+                }
+                g += wz[a] * gy;
+            }
+            T *pa = A + (z * p.n1 + y) * p.n2 + x;
+            const TW a = static_cast<TW>(*pa);
+            *pa = static_cast<T>(p.sign > 0 ? a + g : a - g);
+        }
+    }
+}
+
+// Interpolation weights of the fine neighbours of coarse index E along one
+// dimension: j = 2E-1 (E is its right corner: weight wr), j = 2E (weight 1,
+// an even node in this dimension), j = 2E+1 (E is its left corner: wl).
+template <typename TW, typename T>
+__device__ __forceinline__ int pt_support(int64_t E, int64_t n, const T *w, int64_t (&j)[3], TW (&wt)[3])
+{
+    int c = 0;
+    const int64_t f = 2 * E;
+    if (f - 1 >= 1) { j[c] = f - 1; wt[c] = static_cast<TW>(w[2 * (f - 1) + 1]); ++c; }
+    j[c] = f; wt[c] = TW(1); ++c;
+    if (f + 1 <= n - 2) { j[c] = f + 1; wt[c] = static_cast<TW>(w[2 * (f + 1)]); ++c; }
+    return c;
+}
+
+template <typename T, typename TW, int ACT>
+__global__ void __launch_bounds__(kAdjThreads) k_adj_even(AdjParams p)
+{
+    constexpr bool HZ = (ACT & 4) != 0, HY = (ACT & 2) != 0;
+    T *__restrict__ A = static_cast<T *>(p.A);
+    const TW *__restrict__ B = static_cast<const TW *>(p.Z);  // compact base, or null: A itself
+    const T *w0 = static_cast<const T *>(p.w0);
+    const T *w1 = static_cast<const T *>(p.w1);
+    const T *w2 = static_cast<const T *>(p.w2);
+    const int64_t X = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (X >= p.m2) return;
+    int64_t jx[3];
+    TW wx[3];
+    const int cx = pt_support<TW>(X, p.n2, w2, jx, wx);
+    for (int64_t Zc = blockIdx.z; Zc < p.m0; Zc += gridDim.z) {
+        int64_t jz[3] = {0, 0, 0};
+        TW wz[3] = {TW(1), TW(0), TW(0)};
+        const int cz = HZ ? pt_support<TW>(Zc, p.n0, w0, jz, wz) : 1;
+        for (int64_t Yc = blockIdx.y; Yc < p.m1; Yc += gridDim.y) {
+            int64_t jy[3] = {0, 0, 0};
+            TW wy[3] = {TW(1), TW(0), TW(0)};
+            const int cy = HY ? pt_support<TW>(Yc, p.n1, w1, jy, wy) : 1;
+            const int64_t ze = HZ ? 2 * Zc : 0, ye = HY ? 2 * Yc : 0;
+            TW s = TW(0);
+            for (int a = 0; a < cz; ++a) {
+                for (int b = 0; b < cy; ++b) {
+                    const T *row = A + (jz[a] * p.n1 + jy[b]) * p.n2;
+                    const TW wab = wz[a] * wy[b];
+                    for (int c = 0; c < cx; ++c) {
+                        if (jz[a] == ze && jy[b] == ye && jx[c] == 2 * X) continue;  // the node itself
+                        s += wab * wx[c] * static_cast<TW>(row[jx[c]]);
+                    }
+                }
+            }
+            T *pe = A + (ze * p.n1 + ye) * p.n2 + 2 * X;
+            const TW base = B ? B[(Zc * p.m1 + Yc) * p.m2 + X] : static_cast<TW>(*pe);
+            *pe = static_cast<T>(p.sign > 0 ? base + s : base - s);
+        }
+    }
+}
+
+}  // namespace mg

@@ -159,7 +159,7 @@ const double *tab_ptr<double>(const mgard_plan *P, int64_t off) { return P->tab6
 int act_of(int ndim) { return ndim == 1 ? ACT_1D : (ndim == 2 ? ACT_2D : ACT_3D); }
 
 enum { KIND_RESTRICT_DEC = 0, KIND_RESTRICT_REC = 1, KIND_SOLVE = 2, KIND_SOLVE_FUSED = 3,
-       KIND_PLACE = 4, KIND_INTERP = 5, KIND_PLACE_EVEN = 6 };
+       KIND_PLACE = 4, KIND_INTERP = 5, KIND_PLACE_EVEN = 6, KIND_ADJ = 7 };
 
 cudaEvent_t prof_event(const mgard_plan *P)
 {
@@ -210,9 +210,10 @@ cudaError_t run_restrict_level(const mgard_plan *P, int j, int mode, void *A, ch
 }
 
 // Solves of M_{l-1} along every active dimension, fastest first; the last
-// (slowest) one applies V += z (sign +1) or V -= z (sign -1).
+// (slowest) one applies V += z (sign +1), V -= z (sign -1) or leaves z in F
+// (sign 0).  With src, the first sweep reads its right-hand sides from src.
 template <typename TW>
-cudaError_t run_solves(const mgard_plan *P, int j, int sign, char *ws, cudaStream_t st)
+cudaError_t run_solves(const mgard_plan *P, int j, int sign, char *ws, cudaStream_t st, const void *src = nullptr)
 {
     const mgard_level &L = P->lv[j];
     const int nd = P->ndim;
@@ -231,7 +232,8 @@ cudaError_t run_solves(const mgard_plan *P, int j, int sign, char *ws, cudaStrea
         sp.chunk = 0;
         sp.nw = 0;
         sp.lpb = 32;
-        sp.vmode = (q == nd - 1) ? (sign > 0 ? 1 : 2) : 0;
+        sp.vmode = (q == nd - 1) ? (sign > 0 ? 1 : (sign < 0 ? 2 : 0)) : 0;
+        sp.src = (q == 0) ? src : nullptr;  // the first sweep may read its right-hand sides elsewhere
         cudaError_t err = timed(P, sp.vmode ? KIND_SOLVE_FUSED : KIND_SOLVE, j, st,
                                 [&] { return launch_solve<TW>(sp, L.svar, st); });
         if (err != cudaSuccess) return err;
@@ -313,6 +315,99 @@ mgard_status exec_recompose(const mgard_plan *P, void *data, char *ws, cudaStrea
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
         err = (j == 0) ? run_interp_level<TU, TW>(P, j, A, ws, st) : run_interp_level<TW, TW>(P, j, A, ws, st);
         if (err != cudaSuccess) return cuda_fail(err, "recompose: interpolation kernel");
+    }
+    return MGARD_OK;
+}
+
+template <typename T, typename TW>
+AdjParams adj_params(const mgard_plan *P, int j, void *A, const void *Z, int sign)
+{
+    const mgard_level &L = P->lv[j];
+    AdjParams p;
+    p.A = A;
+    p.Z = Z;
+    p.n0 = L.n[0]; p.n1 = L.n[1]; p.n2 = L.n[2];
+    p.m0 = L.m[0]; p.m1 = L.m[1]; p.m2 = L.m[2];
+    p.k0 = tab_ptr<TW>(P, L.k_off[0]); p.k1 = tab_ptr<TW>(P, L.k_off[1]); p.k2 = tab_ptr<TW>(P, L.k_off[2]);
+    p.w0 = tab_ptr<T>(P, L.w_off[0]); p.w1 = tab_ptr<T>(P, L.w_off[1]); p.w2 = tab_ptr<T>(P, L.w_off[2]);
+    p.sign = sign;
+    return p;
+}
+
+template <typename T, typename TW>
+cudaError_t run_gather(const mgard_plan *P, int j, void *A, char *ws, cudaStream_t st)
+{
+    const PlaceParams p = place_params<T>(P, j, A, ws);
+    return timed(P, KIND_ADJ, j, st, [&] { return launch_gather<T, TW>(P->act, p, st); });
+}
+
+template <typename T, typename TW>
+cudaError_t run_adj_odd(const mgard_plan *P, int j, void *A, const void *Z, int sign, cudaStream_t st)
+{
+    const AdjParams p = adj_params<T, TW>(P, j, A, Z, sign);
+    return timed(P, KIND_ADJ, j, st, [&] { return launch_adj_odd<T, TW>(P->act, p, st); });
+}
+
+template <typename T, typename TW>
+cudaError_t run_adj_even(const mgard_plan *P, int j, void *A, const void *B, int sign, cudaStream_t st)
+{
+    const AdjParams p = adj_params<T, TW>(P, j, A, B, sign);
+    return timed(P, KIND_ADJ, j, st, [&] { return launch_adj_even<T, TW>(P->act, p, st); });
+}
+
+// Transpose of the decomposition (back-propagation through it), coarsest
+// level first: gather the coarse nodes of every level, then per level
+// z = M_{l-1}^{-1} V_j, odd <- odd + K^T z, even <- V_j - Pi^T odd.
+template <typename TU, typename TW>
+mgard_status exec_decompose_adjoint(const mgard_plan *P, void *data, char *ws, cudaStream_t st)
+{
+    cudaError_t err;
+    for (int j = 0; j < P->L; ++j) {
+        void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
+        err = (j == 0) ? run_gather<TU, TW>(P, j, A, ws, st) : run_gather<TW, TW>(P, j, A, ws, st);
+        if (err != cudaSuccess) return cuda_fail(err, "decompose_adjoint: gather kernel");
+    }
+    for (int j = P->L - 1; j >= 0; --j) {
+        const mgard_level &L = P->lv[j];
+        void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
+        err = run_solves<TW>(P, j, 0, ws, st, ws + L.v_off);
+        if (err != cudaSuccess) return cuda_fail(err, "decompose_adjoint: solve kernel");
+        err = (j == 0) ? run_adj_odd<TU, TW>(P, j, A, ws + L.f_off, +1, st)
+                       : run_adj_odd<TW, TW>(P, j, A, ws + L.f_off, +1, st);
+        if (err != cudaSuccess) return cuda_fail(err, "decompose_adjoint: odd-node kernel");
+        err = (j == 0) ? run_adj_even<TU, TW>(P, j, A, ws + L.v_off, -1, st)
+                       : run_adj_even<TW, TW>(P, j, A, ws + L.v_off, -1, st);
+        if (err != cudaSuccess) return cuda_fail(err, "decompose_adjoint: even-node kernel");
+    }
+    return MGARD_OK;
+}
+
+// Transpose of the recomposition, finest level first: even <- even + Pi^T
+// odd, gather it into V_j, z = M_{l-1}^{-1} V_j, odd <- odd - K^T z; after
+// the coarser levels, V_j goes back to the even nodes.
+template <typename TU, typename TW>
+mgard_status exec_recompose_adjoint(const mgard_plan *P, void *data, char *ws, cudaStream_t st)
+{
+    cudaError_t err;
+    for (int j = 0; j < P->L; ++j) {
+        const mgard_level &L = P->lv[j];
+        void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
+        err = (j == 0) ? run_adj_even<TU, TW>(P, j, A, nullptr, +1, st)
+                       : run_adj_even<TW, TW>(P, j, A, nullptr, +1, st);
+        if (err != cudaSuccess) return cuda_fail(err, "recompose_adjoint: even-node kernel");
+        err = (j == 0) ? run_gather<TU, TW>(P, j, A, ws, st) : run_gather<TW, TW>(P, j, A, ws, st);
+        if (err != cudaSuccess) return cuda_fail(err, "recompose_adjoint: gather kernel");
+        err = run_solves<TW>(P, j, 0, ws, st, ws + L.v_off);
+        if (err != cudaSuccess) return cuda_fail(err, "recompose_adjoint: solve kernel");
+        err = (j == 0) ? run_adj_odd<TU, TW>(P, j, A, ws + L.f_off, -1, st)
+                       : run_adj_odd<TW, TW>(P, j, A, ws + L.f_off, -1, st);
+        if (err != cudaSuccess) return cuda_fail(err, "recompose_adjoint: odd-node kernel");
+    }
+    for (int j = P->L - 1; j >= 0; --j) {
+        void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
+        const PlaceParams p = (j == 0) ? place_params<TU>(P, j, A, ws) : place_params<TW>(P, j, A, ws);
+        err = (j == 0) ? launch_scatter<TU, TW>(P->act, p, st) : launch_scatter<TW, TW>(P->act, p, st);
+        if (err != cudaSuccess) return cuda_fail(err, "recompose_adjoint: scatter kernel");
     }
     return MGARD_OK;
 }
@@ -584,6 +679,32 @@ mgard_status mgard_recompose(const mgard_plan *P, void *d_data, void *d_ws, size
     case MGARD_F32: return exec_recompose<float, float>(P, d_data, ws, st);
     case MGARD_F64: return exec_recompose<double, double>(P, d_data, ws, st);
     default: return exec_recompose<float, double>(P, d_data, ws, st);
+    }
+}
+
+mgard_status mgard_decompose_adjoint(const mgard_plan *P, void *d_data, void *d_ws, size_t ws_bytes, void *stream)
+{
+    mgard_status s = check_call(P, d_data, d_ws, ws_bytes);
+    if (s != MGARD_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(d_ws);
+    switch (P->dtype) {
+    case MGARD_F32: return exec_decompose_adjoint<float, float>(P, d_data, ws, st);
+    case MGARD_F64: return exec_decompose_adjoint<double, double>(P, d_data, ws, st);
+    default: return exec_decompose_adjoint<float, double>(P, d_data, ws, st);
+    }
+}
+
+mgard_status mgard_recompose_adjoint(const mgard_plan *P, void *d_data, void *d_ws, size_t ws_bytes, void *stream)
+{
+    mgard_status s = check_call(P, d_data, d_ws, ws_bytes);
+    if (s != MGARD_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(d_ws);
+    switch (P->dtype) {
+    case MGARD_F32: return exec_recompose_adjoint<float, float>(P, d_data, ws, st);
+    case MGARD_F64: return exec_recompose_adjoint<double, double>(P, d_data, ws, st);
+    default: return exec_recompose_adjoint<float, double>(P, d_data, ws, st);
     }
 }
 

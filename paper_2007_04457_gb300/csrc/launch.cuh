@@ -46,4 +46,14 @@ cudaError_t launch_scatter(int act, const PlaceParams &p, cudaStream_t st);
 template <typename T, typename TW>
 cudaError_t launch_interp(int act, const PlaceParams &p, cudaStream_t st);
 
+// Transposed level maps (adjoint.cuh).
+template <typename T, typename TW>
+cudaError_t launch_gather(int act, const PlaceParams &p, cudaStream_t st);
+
+template <typename T, typename TW>
+cudaError_t launch_adj_odd(int act, const AdjParams &p, cudaStream_t st);
+
+template <typename T, typename TW>
+cudaError_t launch_adj_even(int act, const AdjParams &p, cudaStream_t st);
+
 }  // namespace mg

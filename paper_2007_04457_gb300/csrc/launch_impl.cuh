@@ -4,6 +4,7 @@
 
 #include <algorithm>
 
+#include "adjoint.cuh"
 #include "interp.cuh"
 #include "launch.cuh"
 #include "restrict.cuh"
@@ -176,13 +177,51 @@ cudaError_t launch_interp(int act, const PlaceParams &p, cudaStream_t st)
     return cudaGetLastError();
 }
 
+#define MG_ACT_SWITCH(KERNEL, G, B, P)                                          \
+    switch (act) {                                                             \
+    case ACT_1D: KERNEL<T, TW, ACT_1D><<<G, B, 0, st>>>(P); break;             \
+    case ACT_2D: KERNEL<T, TW, ACT_2D><<<G, B, 0, st>>>(P); break;             \
+    case ACT_3D: KERNEL<T, TW, ACT_3D><<<G, B, 0, st>>>(P); break;             \
+    default: return cudaErrorInvalidValue;                                     \
+    }
+
+template <typename T, typename TW>
+cudaError_t launch_gather(int act, const PlaceParams &p, cudaStream_t st)
+{
+    dim3 g, b;
+    detail::node_grid(p.m2, p.m1, p.m0, &g, &b);
+    MG_ACT_SWITCH(k_gather, g, b, p)
+    return cudaGetLastError();
+}
+
+template <typename T, typename TW>
+cudaError_t launch_adj_odd(int act, const AdjParams &p, cudaStream_t st)
+{
+    dim3 g, b;
+    detail::node_grid(p.n2, p.n1, p.n0, &g, &b);
+    MG_ACT_SWITCH(k_adj_odd, g, b, p)
+    return cudaGetLastError();
+}
+
+template <typename T, typename TW>
+cudaError_t launch_adj_even(int act, const AdjParams &p, cudaStream_t st)
+{
+    dim3 g, b;
+    detail::node_grid(p.m2, p.m1, p.m0, &g, &b);
+    MG_ACT_SWITCH(k_adj_even, g, b, p)
+    return cudaGetLastError();
+}
+
 #define MG_INSTANTIATE_LEVEL(T, TW)                                                              \
     template cudaError_t restrict_shape<T, TW>(int, int, int, RestrictShape *);                  \
     template cudaError_t launch_restrict<T, TW>(int, int, int, const RestrictParams &, int,     \
                                                 cudaStream_t);                                   \
     template cudaError_t launch_coef<T, TW>(int, const PlaceParams &, cudaStream_t);            \
     template cudaError_t launch_scatter<T, TW>(int, const PlaceParams &, cudaStream_t);         \
-    template cudaError_t launch_interp<T, TW>(int, const PlaceParams &, cudaStream_t);
+    template cudaError_t launch_interp<T, TW>(int, const PlaceParams &, cudaStream_t);         \
+    template cudaError_t launch_gather<T, TW>(int, const PlaceParams &, cudaStream_t);         \
+    template cudaError_t launch_adj_odd<T, TW>(int, const AdjParams &, cudaStream_t);          \
+    template cudaError_t launch_adj_even<T, TW>(int, const AdjParams &, cudaStream_t);
 
 #define MG_INSTANTIATE_SOLVE(TW) \
     template cudaError_t launch_solve<TW>(const SolveParams &, int, cudaStream_t);

@@ -43,7 +43,8 @@ struct SolveParams {
     int nw;                  // warps per block (chunks per line)
     int chunk;               // nodes per chunk
     int vmode;               // 0: F <- z, 1: V += z, 2: V -= z
-    int lpb;                 // lines per block (shared-memory variant)
+    int lpb;                 // lines per block
+    const void *src;         // right-hand sides read from here instead of F (may be null)
 };
 
 // Element-wise level kernels: placement of coefficients and coarse values
@@ -54,6 +55,16 @@ struct PlaceParams {
     const void *V;           // compact coarse array (type TW)
     int64_t n0, n1, n2, m0, m1, m2;
     const void *w0, *w1, *w2;  // interpolation weight pairs per fine node, type T
+};
+
+// Transposed level maps (adjoint.cuh).
+struct AdjParams {
+    void *A;                 // level array (type T)
+    const void *Z;           // k_adj_odd: solved coarse array; k_adj_even: compact base or null (type TW)
+    int64_t n0, n1, n2, m0, m1, m2;
+    const void *k0, *k1, *k2;  // R*M stencil rows, type TW
+    const void *w0, *w1, *w2;  // interpolation weight pairs, type T
+    int sign;                // +1 or -1
 };
 
 }  // namespace mg

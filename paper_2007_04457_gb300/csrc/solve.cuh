@@ -165,8 +165,9 @@ __global__ void __launch_bounds__(CH > 0 ? 32 * kSolveRegWarps : 1024, 2) k_solv
         const int64_t b_lane = myline / inner * (inner * m) + myline % inner;
 
         // stage the panel
+        const TW *in = p.src ? static_cast<const TW *>(p.src) : F;
         if (contiguous) {
-            const TW *src = F + line0 * m;
+            const TW *src = in + line0 * m;
             int l = tid / m, i = tid - (tid / m) * m;
             const int step_l = nthr / m, step_i = nthr - (nthr / m) * m;
             for (int e = tid; e < nl * m; e += nthr) {
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(CH > 0 ? 32 * kSolveRegWarps : 1024, 2) k_solv
                 if (i >= m) { i -= m; ++l; }
             }
         } else if (lane < nl) {
-            for (int i = w; i < m; i += nw) cp_async_elem(tile + lane * pitch + i, F + b_lane + (int64_t)i * stride, true);
+            for (int i = w; i < m; i += nw) cp_async_elem(tile + lane * pitch + i, in + b_lane + (int64_t)i * stride, true);
         }
         cp_async_commit();
         cp_async_wait<0>();

@@ -53,6 +53,8 @@ def _load() -> ctypes.CDLL:
         "mgard_plan_launches": ([vp, ctypes.c_int], ctypes.c_int),
         "mgard_decompose": ([vp, vp, vp, sz, vp], ctypes.c_int),
         "mgard_recompose": ([vp, vp, vp, sz, vp], ctypes.c_int),
+        "mgard_decompose_adjoint": ([vp, vp, vp, sz, vp], ctypes.c_int),
+        "mgard_recompose_adjoint": ([vp, vp, vp, sz, vp], ctypes.c_int),
         "mgard_decompose_host": ([vp, vp, vp, vp, vp, sz, vp], ctypes.c_int),
         "mgard_recompose_host": ([vp, vp, vp, vp, vp, sz, vp], ctypes.c_int),
         "mgard_profile_enable": ([vp, ctypes.c_int], ctypes.c_int),
@@ -122,6 +124,14 @@ def mgard_decompose(plan: int, d_data: int, d_ws: int, ws_bytes: int, stream: in
 
 def mgard_recompose(plan: int, d_data: int, d_ws: int, ws_bytes: int, stream: int) -> None:
     _check(LIB.mgard_recompose(plan, d_data, d_ws, ws_bytes, stream), "mgard_recompose")
+
+
+def mgard_decompose_adjoint(plan: int, d_data: int, d_ws: int, ws_bytes: int, stream: int) -> None:
+    _check(LIB.mgard_decompose_adjoint(plan, d_data, d_ws, ws_bytes, stream), "mgard_decompose_adjoint")
+
+
+def mgard_recompose_adjoint(plan: int, d_data: int, d_ws: int, ws_bytes: int, stream: int) -> None:
+    _check(LIB.mgard_recompose_adjoint(plan, d_data, d_ws, ws_bytes, stream), "mgard_recompose_adjoint")
 
 
 def mgard_decompose_host(plan: int, h_in: int, h_out: int, d_data: int, d_ws: int, ws_bytes: int,
@@ -230,6 +240,21 @@ class Plan:
         """In-place recomposition of a CUDA tensor; returns it."""
         mgard_recompose(self.handle, *self._args(data, workspace, stream))
         return data
+
+    def decompose_adjoint(self, data, workspace=None, stream=None):
+        """In place: data (a cotangent of the decomposition's output) becomes
+        the cotangent of its input (transpose of decompose)."""
+        mgard_decompose_adjoint(self.handle, *self._args(data, workspace, stream))
+        return data
+
+    def recompose_adjoint(self, data, workspace=None, stream=None):
+        """In place transpose of recompose."""
+        mgard_recompose_adjoint(self.handle, *self._args(data, workspace, stream))
+        return data
+
+    def tune(self, level: int, param: int, value: int) -> None:
+        """Launch-shape tuning of one level (see mgard_plan_tune)."""
+        mgard_plan_tune(self.handle, level, param, value)
 
     def close(self):
         if getattr(self, "handle", None):
