@@ -29,6 +29,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -227,6 +229,81 @@ def cpu_baseline_sample():
             "sample": f"257^3 sub-grid of the same generator, FP64 oracle, {reps} decompose+recompose"}
 
 
+def _timed(torch, stream, fn, steps):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_batched(torch, mgard, synth, dev, stream, rank):
+    """256 FP32 fields of uneven dyadic sizes (240 cubes with sides drawn from
+    {17, 33, 65, 129, 257}, 16 fields of 1025 x 1025) refactored by one
+    CUDA-graph launch per direction, tile shapes from the autotuner; compared
+    with the same fields refactored one by one."""
+    from paper_2007_04457_gb300 import autotune
+
+    shapes = synth.batch_shapes(seed=4)
+    plans, fields, tuned = [], [], {}
+    for i, shp in enumerate(shapes):
+        p = mgard.Plan(shp, dtype="f32")
+        f = synth.sinusoid_field_torch(shp, 12 if len(shp) == 3 else 8, 4 + i + 1000 * rank, dev, torch.float32)
+        if shp not in tuned:
+            tuned[shp] = autotune.tune(p, f.clone(), top=2, reps=2)
+        else:
+            autotune.apply(p, tuned[shp]["cfg"], tuned[shp]["warps"])
+        plans.append(p)
+        fields.append(f)
+    batch = mgard.Batch(plans, streams=8)
+    ws = batch.workspace(dev)
+    step = lambda: (batch.decompose(fields, ws, stream), batch.recompose(fields, ws, stream))
+    for _ in range(3):
+        step()
+    ms = _timed(torch, stream, step, 5)
+    total = 0
+    for p in plans:
+        d, r = algorithmic_bytes(p.shape, p.levels, 4)
+        total += d + r
+    # the same fields one at a time, per distinct shape x multiplicity
+    single_ms = 0.0
+    for shp, cnt in {s: shapes.count(s) for s in set(shapes)}.items():
+        i = shapes.index(shp)
+        p, f = plans[i], fields[i]
+        w = p.workspace(dev)
+        one = lambda: (p.decompose(f, w, stream), p.recompose(f, w, stream))
+        one()
+        single_ms += cnt * _timed(torch, stream, one, 3)
+    return {"value": total / (ms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": ms, "fields": len(shapes),
+            "nodes": int(sum(int(np.prod(s)) for s in shapes)), "graph_launches_per_step": 2,
+            "single_field_ms_per_step": single_ms, "speedup_vs_single_fields": single_ms / ms,
+            "tuned": {"x".join(map(str, k)): [v["cfg"], v["warps"]] for k, v in tuned.items()}}
+
+
+def run_mixed(torch, mgard, synth, dev, stream, rank, max_over_ranks):
+    """1025 x 1025 x 513 FP32 field (12 modes + Gaussian blob), FP64 solves and
+    coarse-level accumulation, 9 levels."""
+    shape = (1025, 1025, 513)
+    plan = mgard.Plan(shape, dtype="f32_mixed")
+    u = synth.sinusoid_field_torch(shape, 12, 3 + rank, dev, torch.float32, blob=True)
+    ws = plan.workspace(dev)
+    step = lambda: (plan.decompose(u, ws, stream), plan.recompose(u, ws, stream))
+    for _ in range(3):
+        step()
+    ms = max_over_ranks(_timed(torch, stream, step, 5))
+    d, r = algorithmic_bytes(shape, plan.levels, 4)
+    out = {"value": (d + r) / (ms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": ms, "levels": plan.levels,
+           "workload": "1025x1025x513 FP32 field, FP64 solves and coarse arrays"}
+    del u, ws
+    plan.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -236,6 +313,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -372,6 +451,9 @@ def main():
                "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes,
                "ms_per_step": mse / ke, "steps": ke}
 
+    batched = None if args.no_batch else run_batched(torch, mgard, synth, dev, stream, rank)
+    mixed = None if args.no_mixed else run_mixed(torch, mgard, synth, dev, stream, rank, max_over_ranks)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample()
@@ -391,6 +473,8 @@ def main():
             "roofline": roof,
             "finest_level_kernel_share": finest_share,
             "fp64": fp64,
+            "mixed": mixed,
+            "batched": batched,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),

@@ -168,6 +168,30 @@ MGARD_API mgard_status mgard_decompose_adjoint(const mgard_plan *plan, void *d_d
 MGARD_API mgard_status mgard_recompose_adjoint(const mgard_plan *plan, void *d_data, void *d_ws,
                                      size_t ws_bytes, void *stream);
 
+/* Batches of independent fields (each with its own plan: shapes, levels and
+ * tile settings may differ).  A batch call replays one CUDA graph that holds
+ * every field's level kernels, spread over `streams` internal streams so
+ * fields run concurrently; the graph is captured on the first call for a
+ * given set of data pointers / workspace and re-captured when they change.
+ * Not part of the paper (its fields are processed one at a time).
+ *   mgard_batch_create     plans: nfields plan pointers, kept (not copied)
+ *                          and not freed by the batch; streams: 1..32
+ *   mgard_batch_workspace_bytes   one workspace holding every field's slice
+ *   mgard_batch_decompose / mgard_batch_recompose
+ *                          d_data: nfields device pointers (host array);
+ *                          the graph runs on `stream`
+ * The first call on a stream captures: it must not itself be inside a
+ * stream capture. */
+typedef struct mgard_batch mgard_batch;
+MGARD_API mgard_status mgard_batch_create(int nfields, mgard_plan *const *plans, int streams,
+                                          mgard_batch **out);
+MGARD_API mgard_status mgard_batch_destroy(mgard_batch *batch);
+MGARD_API size_t mgard_batch_workspace_bytes(const mgard_batch *batch);
+MGARD_API mgard_status mgard_batch_decompose(mgard_batch *batch, void *const *d_data, void *d_ws,
+                                             size_t ws_bytes, void *stream);
+MGARD_API mgard_status mgard_batch_recompose(mgard_batch *batch, void *const *d_data, void *d_ws,
+                                             size_t ws_bytes, void *stream);
+
 /* Human-readable name of a status code (static string). */
 MGARD_API const char *mgard_status_string(mgard_status status);
 

@@ -63,6 +63,12 @@ def _load() -> ctypes.CDLL:
                                 ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "mgard_plan_tune": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "mgard_plan_get_tune": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "mgard_batch_create": ([ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)],
+                               ctypes.c_int),
+        "mgard_batch_destroy": ([vp], ctypes.c_int),
+        "mgard_batch_workspace_bytes": ([vp], sz),
+        "mgard_batch_decompose": ([vp, ctypes.POINTER(vp), vp, sz, vp], ctypes.c_int),
+        "mgard_batch_recompose": ([vp, ctypes.POINTER(vp), vp, sz, vp], ctypes.c_int),
         "mgard_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "mgard_last_error": ([], ctypes.c_char_p),
     }
@@ -259,6 +265,80 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             mgard_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------- batches
+
+def mgard_batch_create(plans, streams: int = 8) -> int:
+    arr = (ctypes.c_void_p * len(plans))(*plans)
+    out = ctypes.c_void_p()
+    _check(LIB.mgard_batch_create(len(plans), arr, streams, ctypes.byref(out)), "mgard_batch_create")
+    return out.value
+
+
+def mgard_batch_destroy(batch: int) -> None:
+    _check(LIB.mgard_batch_destroy(batch), "mgard_batch_destroy")
+
+
+def mgard_batch_workspace_bytes(batch: int) -> int:
+    return LIB.mgard_batch_workspace_bytes(batch)
+
+
+def mgard_batch_decompose(batch: int, d_data, d_ws: int, ws_bytes: int, stream: int) -> None:
+    arr = (ctypes.c_void_p * len(d_data))(*d_data)
+    _check(LIB.mgard_batch_decompose(batch, arr, d_ws, ws_bytes, stream), "mgard_batch_decompose")
+
+
+def mgard_batch_recompose(batch: int, d_data, d_ws: int, ws_bytes: int, stream: int) -> None:
+    arr = (ctypes.c_void_p * len(d_data))(*d_data)
+    _check(LIB.mgard_batch_recompose(batch, arr, d_ws, ws_bytes, stream), "mgard_batch_recompose")
+
+
+class Batch:
+    """Independent fields (one Plan each) refactored by one CUDA-graph launch
+    per call.  The plans must outlive the batch."""
+
+    def __init__(self, plans, streams: int = 8):
+        self.plans = list(plans)
+        self.handle = mgard_batch_create([p.handle for p in self.plans], streams)
+        self.workspace_bytes = mgard_batch_workspace_bytes(self.handle)
+        self._ws = None
+
+    def workspace(self, device=None):
+        torch = _torch()
+        if self._ws is None:
+            self._ws = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=device or "cuda")
+        return self._ws
+
+    def _args(self, fields, workspace, stream):
+        torch = _torch()
+        if len(fields) != len(self.plans):
+            raise ValueError("one tensor per plan")
+        for t, p in zip(fields, self.plans):
+            if not t.is_cuda or not t.is_contiguous() or t.dtype != p.torch_dtype:
+                raise ValueError("fields must be contiguous CUDA tensors of their plan's dtype")
+        ws = workspace if workspace is not None else self.workspace(fields[0].device)
+        s = stream if stream is not None else torch.cuda.current_stream(fields[0].device)
+        return [t.data_ptr() for t in fields], ws.data_ptr(), ws.numel() * ws.element_size(), s.cuda_stream
+
+    def decompose(self, fields, workspace=None, stream=None):
+        mgard_batch_decompose(self.handle, *self._args(fields, workspace, stream))
+        return fields
+
+    def recompose(self, fields, workspace=None, stream=None):
+        mgard_batch_recompose(self.handle, *self._args(fields, workspace, stream))
+        return fields
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mgard_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
