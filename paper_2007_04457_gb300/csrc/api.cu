@@ -33,6 +33,14 @@ mgard_status cuda_fail(cudaError_t err, const char *what)
     return MGARD_ERR_CUDA;
 }
 
+}  // namespace
+
+// Error reporting for the other translation units of the library.
+mgard_status mg_fail(mgard_status st, const std::string &msg) { return fail(st, msg); }
+mgard_status mg_cuda_fail(cudaError_t err, const char *what) { return cuda_fail(err, what); }
+
+namespace {
+
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }

@@ -16,6 +16,9 @@
 
 #include "mgard.h"
 
+mgard_status mg_fail(mgard_status st, const std::string &msg);
+mgard_status mg_cuda_fail(cudaError_t err, const char *what);
+
 namespace {
 
 constexpr size_t kSliceAlign = 256;
@@ -108,29 +111,32 @@ size_t mgard_batch_workspace_bytes(const mgard_batch *B) { return B ? B->ws_byte
 static mgard_status batch_run(mgard_batch *B, int dir, void *const *d_data, void *d_ws, size_t ws_bytes,
                               void *stream)
 {
-    if (!B || !d_data) return MGARD_ERR_INVALID_ARG;
-    if (B->ws_bytes > 0 && (!d_ws || ws_bytes < B->ws_bytes)) return MGARD_ERR_WORKSPACE;
-    if (reinterpret_cast<uintptr_t>(d_ws) % kSliceAlign != 0) return MGARD_ERR_WORKSPACE;
+    if (!B || !d_data) return mg_fail(MGARD_ERR_INVALID_ARG, "batch: NULL batch or data array");
+    if (B->ws_bytes > 0 && (!d_ws || ws_bytes < B->ws_bytes))
+        return mg_fail(MGARD_ERR_WORKSPACE, "batch: workspace missing or too small");
+    if (reinterpret_cast<uintptr_t>(d_ws) % kSliceAlign != 0)
+        return mg_fail(MGARD_ERR_WORKSPACE, "batch: workspace must be 256-byte aligned");
     const int n = (int)B->plans.size();
+    for (int i = 0; i < n; ++i)
+        if (!d_data[i]) return mg_fail(MGARD_ERR_INVALID_ARG, "batch: NULL field pointer");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Graph &G = B->graphs[dir];
-    const bool same = G.exec && G.ws == d_ws && std::equal(G.data.begin(), G.data.end(), d_data) &&
-                      (int)G.data.size() == n;
+    const bool same = G.exec && G.ws == d_ws && (int)G.data.size() == n &&
+                      std::equal(G.data.begin(), G.data.end(), d_data);
     if (!same) {
         if (G.exec) {
             cudaGraphExecDestroy(G.exec);
             G.exec = nullptr;
         }
-        // relaxed capture: the launchers' one-time function-attribute calls
-        // are allowed while capturing
-        cudaStreamCaptureStatus cs;
-        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
-            return MGARD_ERR_INVALID_ARG;
-        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) return MGARD_ERR_CUDA;
+        // relaxed capture on the first internal stream: the launchers'
+        // one-time function-attribute calls are allowed while capturing
+        cudaStream_t origin = B->streams[0];
+        cudaError_t err = cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed);
+        if (err != cudaSuccess) return mg_cuda_fail(err, "batch: begin capture");
         mgard_status status = MGARD_OK;
         const int ns = (int)B->streams.size();
-        cudaEventRecord(B->events[0], st);
-        for (int s = 0; s < ns; ++s) cudaStreamWaitEvent(B->streams[s], B->events[0], 0);
+        cudaEventRecord(B->events[0], origin);
+        for (int s = 1; s < ns; ++s) cudaStreamWaitEvent(B->streams[s], B->events[0], 0);
         for (int i = 0; i < n && status == MGARD_OK; ++i) {
             char *ws = static_cast<char *>(d_ws) + B->offsets[i];
             const size_t wsb = mgard_workspace_bytes(B->plans[i]);
@@ -138,27 +144,28 @@ static mgard_status batch_run(mgard_batch *B, int dir, void *const *d_data, void
             status = dir == 0 ? mgard_decompose(B->plans[i], d_data[i], ws, wsb, fs)
                               : mgard_recompose(B->plans[i], d_data[i], ws, wsb, fs);
         }
-        for (int s = 0; s < ns; ++s) {
-            cudaEventRecord(B->events[1 + s], B->streams[s]);
-            cudaStreamWaitEvent(st, B->events[1 + s], 0);
+        for (int s = 1; s < ns; ++s) {
+            cudaEventRecord(B->events[s], B->streams[s]);
+            cudaStreamWaitEvent(origin, B->events[s], 0);
         }
         cudaGraph_t graph = nullptr;
-        cudaError_t err = cudaStreamEndCapture(st, &graph);
+        err = cudaStreamEndCapture(origin, &graph);
         if (status != MGARD_OK) {
             if (graph) cudaGraphDestroy(graph);
             return status;
         }
-        if (err != cudaSuccess) return MGARD_ERR_CUDA;
+        if (err != cudaSuccess) return mg_cuda_fail(err, "batch: end capture");
         err = cudaGraphInstantiate(&G.exec, graph, 0);
         cudaGraphDestroy(graph);
         if (err != cudaSuccess) {
             G.exec = nullptr;
-            return MGARD_ERR_CUDA;
+            return mg_cuda_fail(err, "batch: graph instantiation");
         }
         G.data.assign(d_data, d_data + n);
         G.ws = d_ws;
     }
-    return cudaGraphLaunch(G.exec, st) == cudaSuccess ? MGARD_OK : MGARD_ERR_CUDA;
+    const cudaError_t err = cudaGraphLaunch(G.exec, st);
+    return err == cudaSuccess ? MGARD_OK : mg_cuda_fail(err, "batch: graph launch");
 }
 
 mgard_status mgard_batch_decompose(mgard_batch *B, void *const *d_data, void *d_ws, size_t ws_bytes, void *stream)
