@@ -192,6 +192,37 @@ MGARD_API mgard_status mgard_batch_decompose(mgard_batch *batch, void *const *d_
 MGARD_API mgard_status mgard_batch_recompose(mgard_batch *batch, void *const *d_data, void *d_ws,
                                              size_t ws_bytes, void *stream);
 
+/* ---- Decomposition without any device allocation --------------------------
+ * The paper has no counterpart: it is a deployment variant of
+ * mgard_decompose for callers that cannot allocate device memory where they
+ * need the transform -- e.g. a process whose device memory is held by its own
+ * pool allocator, or a loop that must not call cudaMalloc/cudaFree because
+ * they synchronize the whole device.  It computes what mgard_plan_create on a
+ * uniform grid (coords = NULL) followed by mgard_decompose computes.
+ *
+ *   ndim, dims, nlevels, dtype   as for mgard_plan_create (uniform grid)
+ *   d_data                       the field, device memory, in place
+ *   stream                       cudaStream_t as void*, NULL = legacy default
+ *
+ * The tables and the workspace live in one static device array of
+ * MGARD_NOALLOC_SCRATCH_BYTES bytes (one per device, created when the
+ * library's module is loaded on it).  A shape whose tables plus workspace do
+ * not fit fails with MGARD_ERR_WORKSPACE before anything is launched.  The
+ * workspace takes about 8/7 bytes per node in 3D and 8/3 in 2D for FP32
+ * (twice that for FP64 and mixed): 257^3 and 2049^2 fit in FP32,
+ * 257x257x129 in FP64.
+ * Nothing in the array has to start at zero: each call writes, on `stream`,
+ * the tables and workspace regions it then reads.  All calls on a device
+ * share the array, so calls must not overlap: two calls on different streams,
+ * or from different host threads, without an order between them, race on
+ * it.  Calls in sequence on one stream are safe.  The first call on each
+ * device looks up the array's address (cudaGetSymbolAddress) and caches it;
+ * make that first call before any stream capture.  The tables are uploaded
+ * from pageable host memory on every call. */
+#define MGARD_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+MGARD_API mgard_status mgard_decompose_noalloc(int ndim, const int64_t *dims, int nlevels, mgard_dtype dtype,
+                                               void *d_data, void *stream);
+
 /* Human-readable name of a status code (static string). */
 MGARD_API const char *mgard_status_string(mgard_status status);
 

@@ -74,6 +74,7 @@ struct mgard_plan {
     std::vector<mgard_level> lv;
     double *tab64 = nullptr;
     float *tab32 = nullptr;
+    bool owns_tables = true;
     size_t ws_bytes = 0;
     int row_grid;
     // kernel timing (measurement support): event pairs around the launches of
@@ -479,8 +480,13 @@ const char *mgard_status_string(mgard_status s)
 
 const char *mgard_last_error(void) { return g_last_error.c_str(); }
 
-mgard_status mgard_plan_create(int ndim, const int64_t *dims, int nlevels, const double *const *coords,
-                               mgard_dtype dtype, mgard_plan **out)
+}  // extern "C"
+
+// Host part of plan creation: validation, level geometry, the tables (in
+// double, returned in *tab) and the workspace layout.  Allocates no device
+// memory; the table pointers of the plan are left null.
+static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, const double *const *coords,
+                                    mgard_dtype dtype, mgard_plan **out, std::vector<double> *tab_out)
 {
     if (!out) return fail(MGARD_ERR_INVALID_ARG, "plan_create: out is NULL");
     *out = nullptr;
@@ -594,20 +600,90 @@ mgard_status mgard_plan_create(int ndim, const int64_t *dims, int nlevels, const
     }
     P->ws_bytes = ws;
 
-    // device tables in double and float
-    std::vector<float> tab32(tab.begin(), tab.end());
-    err = cudaMalloc(&P->tab64, tab.size() * sizeof(double));
-    if (err == cudaSuccess) err = cudaMalloc(&P->tab32, tab32.size() * sizeof(float));
-    if (err == cudaSuccess) err = cudaMemcpy(P->tab64, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
-    if (err == cudaSuccess) err = cudaMemcpy(P->tab32, tab32.data(), tab32.size() * sizeof(float), cudaMemcpyHostToDevice);
-    for (int j = 0; j < L && err == cudaSuccess; ++j) {
+    *tab_out = std::move(tab);
+    *out = P;
+    return MGARD_OK;
+}
+
+// Launch configuration of every level (needs the device, allocates nothing).
+static cudaError_t configure_plan(mgard_plan *P)
+{
+    cudaError_t err = cudaSuccess;
+    for (int j = 0; j < P->L && err == cudaSuccess; ++j) {
         mgard_level &lv = P->lv[j];
-        switch (dtype) {
+        switch (P->dtype) {
         case MGARD_F32: err = configure_level<float, float>(P, lv, j == 0); break;
         case MGARD_F64: err = configure_level<double, double>(P, lv, j == 0); break;
         default: err = configure_level<float, double>(P, lv, j == 0); break;
         }
     }
+    return err;
+}
+
+// Bytes of the device tables of a plan built by build_plan_host: the double
+// tables, then the float tables, 256-byte aligned.
+static size_t table_bytes(const std::vector<double> &tab)
+{
+    return align_up(tab.size() * sizeof(double)) + align_up(tab.size() * sizeof(float));
+}
+
+// A uniform-grid plan whose tables live in caller-provided device memory
+// `dev` (256-byte aligned, `dev_bytes` long), copied there on `stream`; the
+// plan does not own (or free) them.  Fails with MGARD_ERR_WORKSPACE, before
+// touching the device, unless the tables (*used bytes) and the plan's
+// workspace after them both fit.  Used by the entry point that must not
+// allocate.
+mgard_status mg_plan_in_place(int ndim, const int64_t *dims, int nlevels, mgard_dtype dtype, void *dev,
+                              size_t dev_bytes, cudaStream_t stream, mgard_plan **out, size_t *used)
+{
+    std::vector<double> tab;
+    mgard_plan *P = nullptr;
+    mgard_status s = build_plan_host(ndim, dims, nlevels, nullptr, dtype, &P, &tab);
+    if (s != MGARD_OK) return s;
+    *used = table_bytes(tab);
+    if (*used + P->ws_bytes > dev_bytes) {
+        const std::string need = std::to_string(*used + P->ws_bytes);
+        delete P;
+        return fail(MGARD_ERR_WORKSPACE, "this shape needs " + need + " bytes of scratch (tables and workspace); the static scratch holds " +
+                                             std::to_string(dev_bytes));
+    }
+    std::vector<float> tab32(tab.begin(), tab.end());
+    P->tab64 = static_cast<double *>(dev);
+    P->tab32 = reinterpret_cast<float *>(static_cast<char *>(dev) + align_up(tab.size() * sizeof(double)));
+    P->owns_tables = false;
+    // pageable host sources: each copy has consumed its buffer when it returns
+    cudaError_t err = cudaMemcpyAsync(P->tab64, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(P->tab32, tab32.data(), tab32.size() * sizeof(float), cudaMemcpyHostToDevice, stream);
+    if (err == cudaSuccess) err = configure_plan(P);
+    if (err != cudaSuccess) {
+        delete P;
+        return cuda_fail(err, "static plan");
+    }
+    *out = P;
+    return MGARD_OK;
+}
+
+// Decomposition with a host-built plan (used by the entry point that must not
+// allocate; validation as in mgard_decompose).
+mgard_status mg_decompose_with(const mgard_plan *P, void *d_data, void *d_ws, size_t ws_bytes, cudaStream_t st);
+
+extern "C" {
+
+mgard_status mgard_plan_create(int ndim, const int64_t *dims, int nlevels, const double *const *coords,
+                               mgard_dtype dtype, mgard_plan **out)
+{
+    std::vector<double> tab;
+    mgard_plan *P = nullptr;
+    mgard_status s = build_plan_host(ndim, dims, nlevels, coords, dtype, &P, &tab);
+    if (s != MGARD_OK) return s;
+    // device tables in double and float
+    std::vector<float> tab32(tab.begin(), tab.end());
+    cudaError_t err = cudaMalloc(&P->tab64, tab.size() * sizeof(double));
+    if (err == cudaSuccess) err = cudaMalloc(&P->tab32, tab32.size() * sizeof(float));
+    if (err == cudaSuccess) err = cudaMemcpy(P->tab64, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(P->tab32, tab32.data(), tab32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = configure_plan(P);
     if (err != cudaSuccess) {
         mgard_plan_destroy(P);
         return cuda_fail(err, "plan_create: device tables");
@@ -619,8 +695,10 @@ mgard_status mgard_plan_create(int ndim, const int64_t *dims, int nlevels, const
 mgard_status mgard_plan_destroy(mgard_plan *P)
 {
     if (!P) return MGARD_OK;
-    if (P->tab64) cudaFree(P->tab64);
-    if (P->tab32) cudaFree(P->tab32);
+    if (P->owns_tables) {
+        if (P->tab64) cudaFree(P->tab64);
+        if (P->tab32) cudaFree(P->tab32);
+    }
     for (auto &r : P->prof_pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -663,6 +741,15 @@ static mgard_status check_call(const mgard_plan *P, void *data, void *ws, size_t
     if (dev != P->device) return fail(MGARD_ERR_INVALID_ARG, "the plan was created on another device");
     return MGARD_OK;
 }
+
+}  // extern "C"
+
+mgard_status mg_decompose_with(const mgard_plan *P, void *d_data, void *d_ws, size_t ws_bytes, cudaStream_t st)
+{
+    return mgard_decompose(P, d_data, d_ws, ws_bytes, st);
+}
+
+extern "C" {
 
 mgard_status mgard_decompose(const mgard_plan *P, void *d_data, void *d_ws, size_t ws_bytes, void *stream)
 {

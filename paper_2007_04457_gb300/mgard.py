@@ -69,6 +69,7 @@ def _load() -> ctypes.CDLL:
         "mgard_batch_workspace_bytes": ([vp], sz),
         "mgard_batch_decompose": ([vp, ctypes.POINTER(vp), vp, sz, vp], ctypes.c_int),
         "mgard_batch_recompose": ([vp, ctypes.POINTER(vp), vp, sz, vp], ctypes.c_int),
+        "mgard_decompose_noalloc": ([ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
         "mgard_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "mgard_last_error": ([], ctypes.c_char_p),
     }
@@ -174,6 +175,16 @@ def mgard_plan_tune(plan: int, level: int, param: int, value: int) -> None:
 
 def mgard_plan_get_tune(plan: int, level: int, param: int) -> int:
     return LIB.mgard_plan_get_tune(plan, level, param)
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def mgard_decompose_noalloc(ndim, dims, nlevels, dtype, d_data: int, stream: int) -> None:
+    """Uniform-grid decomposition with tables and workspace in the library's
+    static scratch (no device allocation; calls must not overlap)."""
+    d = (ctypes.c_int64 * ndim)(*[int(v) for v in dims])
+    _check(LIB.mgard_decompose_noalloc(ndim, d, nlevels, dtype, d_data, stream), "mgard_decompose_noalloc")
 
 
 def mgard_status_string(status: int) -> str:
