@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 SHAPE = (513, 513, 513)
 N_MODES = 12
 SEED = 2
-KIND_NAMES = {0: "restrict_dec", 1: "restrict_rec", 2: "solve", 3: "solve_fused",
+KIND_NAMES = {0: "restrict_dec", 1: "restrict_rec", 2: "solve", 3: "solve_fused", 8: "small",
               4: "coef", 5: "interp", 6: "scatter"}
 
 

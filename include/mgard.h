@@ -112,14 +112,17 @@ MGARD_API mgard_status mgard_decompose(const mgard_plan *plan, void *d_data, voi
 MGARD_API mgard_status mgard_recompose(const mgard_plan *plan, void *d_data, void *d_ws,
                              size_t ws_bytes, void *stream);
 
-/* Launch-shape tuning of one level (step j = 0 is the finest level L).  The
- * result of a call does not depend on these settings beyond floating-point
- * rounding of the solve order, which they do not change: only tile shapes
- * and kernel variants are affected.
+/* Launch-shape tuning of one level (step j = 0 is the finest level L).
+ * Params 0-2 change only tile shapes and kernel variants, not the result.
  *   param 0  restriction tile: 0 = 8 x 64, 1 = 4 x 64, 2 = 16 x 64 coarse nodes
  *   param 1  warps (chunks) per line in the correction solves, 1..32, or
  *            0 = automatic (about 16 nodes per chunk)
  *   param 2  coarse planes per restriction work item (0 = automatic)
+ *   param 3  plan-wide (any valid level): 0 = run the coarse levels whose
+ *            array fits in one block's shared memory (at most 227 KB, sides
+ *            <= 257) in a single launch per direction (default); 1 = run
+ *            every level with the tiled per-level kernels.  The two differ
+ *            only in floating-point rounding order.
  * Returns MGARD_ERR_INVALID_ARG for an unknown parameter or value. */
 MGARD_API mgard_status mgard_plan_tune(mgard_plan *plan, int level, int param, int value);
 

@@ -77,6 +77,11 @@ struct mgard_plan {
     bool owns_tables = true;
     size_t ws_bytes = 0;
     int row_grid;
+    // levels small_j .. L-1 run in the single-block kernel (small_j = L: none)
+    int small_j = 0;
+    int small_auto = 0;    // the finest level whose array fits the kernel
+    size_t small_smem = 0;
+    int small_hcap = 0;
     // kernel timing (measurement support): event pairs around the launches of
     // the prof_levels finest levels
     struct ProfRec {
@@ -168,7 +173,7 @@ const double *tab_ptr<double>(const mgard_plan *P, int64_t off) { return P->tab6
 int act_of(int ndim) { return ndim == 1 ? ACT_1D : (ndim == 2 ? ACT_2D : ACT_3D); }
 
 enum { KIND_RESTRICT_DEC = 0, KIND_RESTRICT_REC = 1, KIND_SOLVE = 2, KIND_SOLVE_FUSED = 3,
-       KIND_PLACE = 4, KIND_INTERP = 5, KIND_PLACE_EVEN = 6, KIND_ADJ = 7 };
+       KIND_PLACE = 4, KIND_INTERP = 5, KIND_PLACE_EVEN = 6, KIND_ADJ = 7, KIND_SMALL = 8 };
 
 cudaEvent_t prof_event(const mgard_plan *P)
 {
@@ -280,6 +285,29 @@ cudaError_t run_interp_level(const mgard_plan *P, int j, void *A, char *ws, cuda
     return timed(P, KIND_INTERP, j, st, [&] { return launch_interp<T, TW>(P->act, p, st); });
 }
 
+// Levels small_j .. L-1 in one block, on the array of level small_j (the
+// user array when small_j = 0, else V_{small_j - 1}).
+template <typename T, typename TW>
+cudaError_t run_small(const mgard_plan *P, int mode, void *A, cudaStream_t st)
+{
+    const int j0 = P->small_j;
+    const int64_t *n = (j0 == 0) ? P->n : P->lv[j0 - 1].m;
+    SmallParams sp;
+    sp.A = A;
+    for (int d = 0; d < 3; ++d) sp.n[d] = (int)n[d];
+    sp.nlev = P->L - j0;
+    sp.hcap = P->small_hcap;
+    for (int i = 0; i < sp.nlev; ++i) {
+        const mgard_level &L = P->lv[j0 + i];
+        for (int d = 0; d < 3; ++d) {
+            sp.w[i][d] = tab_ptr<TW>(P, L.w_off[d]);
+            sp.k[i][d] = tab_ptr<TW>(P, L.k_off[d]);
+            sp.fac[i][d] = tab_ptr<TW>(P, L.t_off[d]);
+        }
+    }
+    return timed(P, KIND_SMALL, j0, st, [&] { return launch_small<T, TW>(mode, sp, P->small_smem, st); });
+}
+
 // Decomposition, levels L..1 (Section II-A): level j = 0 works on the user
 // array (element type TU), deeper levels on the compact coarse arrays V_{j-1}
 // of the workspace (type TW).  Each level's restriction only reads its array;
@@ -289,7 +317,8 @@ template <typename TU, typename TW>
 mgard_status exec_decompose(const mgard_plan *P, void *data, char *ws, cudaStream_t st)
 {
     cudaError_t err;
-    for (int j = 0; j < P->L; ++j) {
+    const int J = P->small_j;
+    for (int j = 0; j < J; ++j) {
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
         err = (j == 0) ? run_restrict_level<TU, TW>(P, j, MODE_DEC, A, ws, st)
                        : run_restrict_level<TW, TW>(P, j, MODE_DEC, A, ws, st);
@@ -297,7 +326,12 @@ mgard_status exec_decompose(const mgard_plan *P, void *data, char *ws, cudaStrea
         err = run_solves<TW>(P, j, +1, ws, st);
         if (err != cudaSuccess) return cuda_fail(err, "decompose: correction solve kernel");
     }
-    for (int j = P->L - 1; j >= 0; --j) {
+    if (J < P->L) {
+        void *A = (J == 0) ? data : (void *)(ws + P->lv[J - 1].v_off);
+        err = (J == 0) ? run_small<TU, TW>(P, MODE_DEC, A, st) : run_small<TW, TW>(P, MODE_DEC, A, st);
+        if (err != cudaSuccess) return cuda_fail(err, "decompose: single-block coarse-level kernel");
+    }
+    for (int j = J - 1; j >= 0; --j) {
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
         err = (j == 0) ? run_place_level<TU, TW>(P, j, A, ws, st) : run_place_level<TW, TW>(P, j, A, ws, st);
         if (err != cudaSuccess) return cuda_fail(err, "decompose: coefficient placement kernel");
@@ -312,13 +346,19 @@ template <typename TU, typename TW>
 mgard_status exec_recompose(const mgard_plan *P, void *data, char *ws, cudaStream_t st)
 {
     cudaError_t err;
-    for (int j = 0; j < P->L; ++j) {
+    const int J = P->small_j;
+    for (int j = 0; j < J; ++j) {
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
         err = (j == 0) ? run_restrict_level<TU, TW>(P, j, MODE_REC, A, ws, st)
                        : run_restrict_level<TW, TW>(P, j, MODE_REC, A, ws, st);
         if (err != cudaSuccess) return cuda_fail(err, "recompose: load-vector kernel");
     }
-    for (int j = P->L - 1; j >= 0; --j) {
+    if (J < P->L) {
+        void *A = (J == 0) ? data : (void *)(ws + P->lv[J - 1].v_off);
+        err = (J == 0) ? run_small<TU, TW>(P, MODE_REC, A, st) : run_small<TW, TW>(P, MODE_REC, A, st);
+        if (err != cudaSuccess) return cuda_fail(err, "recompose: single-block coarse-level kernel");
+    }
+    for (int j = J - 1; j >= 0; --j) {
         err = run_solves<TW>(P, j, -1, ws, st);
         if (err != cudaSuccess) return cuda_fail(err, "recompose: correction solve kernel");
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
@@ -600,6 +640,24 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
     }
     P->ws_bytes = ws;
 
+    // the finest level whose array the single-block kernel takes
+    P->small_auto = L;
+    for (int j = 0; j < L; ++j) {
+        const int64_t *nj = (j == 0) ? P->n : P->lv[j - 1].m;
+        const int64_t es = (int64_t)P->elem_ws;
+        const int64_t base = small_elems(nj), hp = small_hplane(nj);
+        const bool sides_ok = nj[0] <= kSmallMaxSide && nj[1] <= kSmallMaxSide && nj[2] <= kSmallMaxSide;
+        if (sides_ok && (base + hp) * es <= kSmallMaxBytes && L - j <= kSmallMaxLevels) {
+            // H: as many first-level fine planes as fit, at most all of them
+            const int64_t planes = std::min<int64_t>(nj[0], (kSmallMaxBytes / es - base) / hp);
+            P->small_auto = j;
+            P->small_hcap = (int)(planes * hp);
+            P->small_smem = (size_t)((base + planes * hp) * es);
+            break;
+        }
+    }
+    P->small_j = P->small_auto;
+
     *tab_out = std::move(tab);
     *out = P;
     return MGARD_OK;
@@ -718,7 +776,7 @@ int mgard_plan_launches(const mgard_plan *P, int recompose)
     // per level: one restriction + ndim solve sweeps + the element-wise
     // kernel(s): interpolation (recompose) or coefficients + coarse placement
     const int tail = recompose ? 1 : 2;
-    return P->L * (1 + P->ndim + tail);
+    return P->small_j * (1 + P->ndim + tail) + (P->small_j < P->L ? 1 : 0);
 }
 
 static mgard_status check_call(const mgard_plan *P, void *data, void *ws, size_t ws_bytes)
@@ -830,6 +888,10 @@ mgard_status mgard_plan_tune(mgard_plan *P, int level, int param, int value)
         if (value < 0) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: chunk planes");
         L.zreq = value;
         break;
+    case 3:
+        if (value != 0 && value != 1) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: single-block switch");
+        P->small_j = value ? P->L : P->small_auto;
+        return MGARD_OK;
     default: return fail(MGARD_ERR_INVALID_ARG, "plan_tune: unknown parameter");
     }
     cudaError_t err = reconfigure(P, level);
@@ -849,6 +911,7 @@ int mgard_plan_get_tune(const mgard_plan *P, int level, int param)
     case 0: return L.rcfg;
     case 1: return L.svar;
     case 2: return L.zchunk;
+    case 3: return P->small_j == P->L ? 1 : 0;
     default: return -1;
     }
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "params.h"
+#include "small_params.h"
 
 namespace mg {
 
@@ -45,6 +46,11 @@ cudaError_t launch_scatter(int act, const PlaceParams &p, cudaStream_t st);
 
 template <typename T, typename TW>
 cudaError_t launch_interp(int act, const PlaceParams &p, cudaStream_t st);
+
+// All remaining levels of a small array in one block (small.cuh); smem =
+// small_elems(n) * sizeof(TW) bytes of dynamic shared memory.
+template <typename T, typename TW>
+cudaError_t launch_small(int mode, const SmallParams &p, size_t smem, cudaStream_t st);
 
 // Transposed level maps (adjoint.cuh).
 template <typename T, typename TW>

@@ -8,6 +8,7 @@
 #include "interp.cuh"
 #include "launch.cuh"
 #include "restrict.cuh"
+#include "small.cuh"
 #include "solve.cuh"
 
 namespace mg {
@@ -212,6 +213,17 @@ cudaError_t launch_adj_even(int act, const AdjParams &p, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <typename T, typename TW>
+cudaError_t launch_small(int mode, const SmallParams &p, size_t smem, cudaStream_t st)
+{
+    void (*fn)(SmallParams) = (mode == MODE_DEC) ? k_small<T, TW, MODE_DEC> : k_small<T, TW, MODE_REC>;
+    cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    fn<<<1, kSmallThreads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
 #define MG_INSTANTIATE_LEVEL(T, TW)                                                              \
     template cudaError_t restrict_shape<T, TW>(int, int, int, RestrictShape *);                  \
     template cudaError_t launch_restrict<T, TW>(int, int, int, const RestrictParams &, int,     \
@@ -221,7 +233,8 @@ cudaError_t launch_adj_even(int act, const AdjParams &p, cudaStream_t st)
     template cudaError_t launch_interp<T, TW>(int, const PlaceParams &, cudaStream_t);         \
     template cudaError_t launch_gather<T, TW>(int, const PlaceParams &, cudaStream_t);         \
     template cudaError_t launch_adj_odd<T, TW>(int, const AdjParams &, cudaStream_t);          \
-    template cudaError_t launch_adj_even<T, TW>(int, const AdjParams &, cudaStream_t);
+    template cudaError_t launch_adj_even<T, TW>(int, const AdjParams &, cudaStream_t);          \
+    template cudaError_t launch_small<T, TW>(int, const SmallParams &, size_t, cudaStream_t);
 
 #define MG_INSTANTIATE_SOLVE(TW) \
     template cudaError_t launch_solve<TW>(const SolveParams &, int, cudaStream_t);
