@@ -273,7 +273,7 @@ template <typename T, typename TW>
 cudaError_t run_place_level(const mgard_plan *P, int j, void *A, char *ws, cudaStream_t st)
 {
     const PlaceParams p = place_params<T>(P, j, A, ws);
-    cudaError_t err = timed(P, KIND_PLACE, j, st, [&] { return launch_coef<T, TW>(P->act, p, st); });
+    cudaError_t err = timed(P, KIND_PLACE, j, st, [&] { return launch_coef<T, TW>(P->act, p, P->num_sms, st); });
     if (err != cudaSuccess) return err;
     return timed(P, KIND_PLACE_EVEN, j, st, [&] { return launch_scatter<T, TW>(P->act, p, st); });
 }
@@ -282,7 +282,7 @@ template <typename T, typename TW>
 cudaError_t run_interp_level(const mgard_plan *P, int j, void *A, char *ws, cudaStream_t st)
 {
     const PlaceParams p = place_params<T>(P, j, A, ws);
-    return timed(P, KIND_INTERP, j, st, [&] { return launch_interp<T, TW>(P->act, p, st); });
+    return timed(P, KIND_INTERP, j, st, [&] { return launch_interp<T, TW>(P->act, p, P->num_sms, st); });
 }
 
 // Levels small_j .. L-1 in one block, on the array of level small_j (the

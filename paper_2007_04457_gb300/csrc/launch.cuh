@@ -36,16 +36,17 @@ constexpr int kMaxLine = 4096;
 template <typename TW>
 cudaError_t launch_solve(const SolveParams &p, int nw_req, cudaStream_t st);
 
-// Element-wise kernels (one thread per node): coefficients of a decomposed
-// level, placement of its final coarse values, and recomposition of a level.
+// Element-wise kernels: coefficients of a decomposed level (warp-tile
+// sweep), placement of its final coarse values (one thread per coarse node),
+// and recomposition of a level (warp-tile sweep).
 template <typename T, typename TW>
-cudaError_t launch_coef(int act, const PlaceParams &p, cudaStream_t st);
+cudaError_t launch_coef(int act, const PlaceParams &p, int num_sms, cudaStream_t st);
 
 template <typename T, typename TW>
 cudaError_t launch_scatter(int act, const PlaceParams &p, cudaStream_t st);
 
 template <typename T, typename TW>
-cudaError_t launch_interp(int act, const PlaceParams &p, cudaStream_t st);
+cudaError_t launch_interp(int act, const PlaceParams &p, int num_sms, cudaStream_t st);
 
 // All remaining levels of a small array in one block (small.cuh); smem =
 // small_elems(n) * sizeof(TW) bytes of dynamic shared memory.

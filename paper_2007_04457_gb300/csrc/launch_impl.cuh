@@ -9,6 +9,7 @@
 #include "launch.cuh"
 #include "restrict.cuh"
 #include "small.cuh"
+#include "sweep.cuh"
 #include "solve.cuh"
 
 namespace mg {
@@ -134,20 +135,51 @@ inline void node_grid(int64_t nx, int64_t ny, int64_t nz, dim3 *grid, dim3 *bloc
                  (unsigned)std::min<int64_t>(nz, 65535));
 }
 
-}  // namespace detail
-
-template <typename T, typename TW>
-cudaError_t launch_coef(int act, const PlaceParams &p, cudaStream_t st)
+// Plane chunking of k_sweep: enough warp items for about 16 resident warps
+// per SM twice over, chunks of an even number of fine planes.
+inline int64_t sweep_rows(int act, size_t elem)
 {
-    dim3 g, b;
-    detail::node_grid((p.n2 + 3) / 4, p.n1, p.n0, &g, &b);  // 4 nodes per thread
+    return (act & 2) ? (elem == 4 ? 16 : 8) : 1;
+}
+
+inline void sweep_chunks(PlaceParams &p, int act, int64_t R, int num_sms)
+{
+    const int64_t tiles = ((p.n2 + 31) / 32) * ((act & 2) ? (p.n1 + R - 1) / R : 1);
+    if (!(act & 4)) {
+        p.zchunk = 1;
+        p.nzc = 1;
+        return;
+    }
+    const int64_t want = (int64_t)num_sms * 32;
+    const int64_t nz = std::max<int64_t>(1, std::min<int64_t>((want + tiles - 1) / tiles, (p.n0 - 1) / 2));
+    int64_t zc = (p.n0 + nz - 1) / nz;
+    zc += zc & 1;
+    p.zchunk = std::max<int64_t>(2, zc);
+    p.nzc = (p.n0 + p.zchunk - 1) / p.zchunk;
+}
+
+template <typename T, typename TW, int MODE>
+cudaError_t launch_sweep(int act, PlaceParams p, int num_sms, cudaStream_t st)
+{
+    const int64_t R = sweep_rows(act, sizeof(T));
+    sweep_chunks(p, act, R, num_sms);
+    const int64_t items = ((p.n2 + 31) / 32) * ((act & 2) ? (p.n1 + R - 1) / R : 1) * p.nzc;
+    const int64_t blocks = std::min<int64_t>((items + kSweepWarps - 1) / kSweepWarps, 1 << 30);
     switch (act) {
-    case ACT_1D: k_coef<T, TW, ACT_1D><<<g, b, 0, st>>>(p); break;
-    case ACT_2D: k_coef<T, TW, ACT_2D><<<g, b, 0, st>>>(p); break;
-    case ACT_3D: k_coef<T, TW, ACT_3D><<<g, b, 0, st>>>(p); break;
+    case ACT_1D: k_sweep<T, TW, ACT_1D, MODE><<<(unsigned)blocks, 32 * kSweepWarps, 0, st>>>(p); break;
+    case ACT_2D: k_sweep<T, TW, ACT_2D, MODE><<<(unsigned)blocks, 32 * kSweepWarps, 0, st>>>(p); break;
+    case ACT_3D: k_sweep<T, TW, ACT_3D, MODE><<<(unsigned)blocks, 32 * kSweepWarps, 0, st>>>(p); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+}  // namespace detail
+
+template <typename T, typename TW>
+cudaError_t launch_coef(int act, const PlaceParams &p, int num_sms, cudaStream_t st)
+{
+    return detail::launch_sweep<T, TW, MODE_DEC>(act, p, num_sms, st);
 }
 
 template <typename T, typename TW>
@@ -165,17 +197,9 @@ cudaError_t launch_scatter(int act, const PlaceParams &p, cudaStream_t st)
 }
 
 template <typename T, typename TW>
-cudaError_t launch_interp(int act, const PlaceParams &p, cudaStream_t st)
+cudaError_t launch_interp(int act, const PlaceParams &p, int num_sms, cudaStream_t st)
 {
-    dim3 g, b;
-    detail::node_grid((p.n2 + 3) / 4, p.n1, p.n0, &g, &b);  // 4 nodes per thread
-    switch (act) {
-    case ACT_1D: k_interp<T, TW, ACT_1D><<<g, b, 0, st>>>(p); break;
-    case ACT_2D: k_interp<T, TW, ACT_2D><<<g, b, 0, st>>>(p); break;
-    case ACT_3D: k_interp<T, TW, ACT_3D><<<g, b, 0, st>>>(p); break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    return detail::launch_sweep<T, TW, MODE_REC>(act, p, num_sms, st);
 }
 
 #define MG_ACT_SWITCH(KERNEL, G, B, P)                                          \
@@ -228,9 +252,9 @@ cudaError_t launch_small(int mode, const SmallParams &p, size_t smem, cudaStream
     template cudaError_t restrict_shape<T, TW>(int, int, int, RestrictShape *);                  \
     template cudaError_t launch_restrict<T, TW>(int, int, int, const RestrictParams &, int,     \
                                                 cudaStream_t);                                   \
-    template cudaError_t launch_coef<T, TW>(int, const PlaceParams &, cudaStream_t);            \
+    template cudaError_t launch_coef<T, TW>(int, const PlaceParams &, int, cudaStream_t);       \
     template cudaError_t launch_scatter<T, TW>(int, const PlaceParams &, cudaStream_t);         \
-    template cudaError_t launch_interp<T, TW>(int, const PlaceParams &, cudaStream_t);         \
+    template cudaError_t launch_interp<T, TW>(int, const PlaceParams &, int, cudaStream_t);    \
     template cudaError_t launch_gather<T, TW>(int, const PlaceParams &, cudaStream_t);         \
     template cudaError_t launch_adj_odd<T, TW>(int, const AdjParams &, cudaStream_t);          \
     template cudaError_t launch_adj_even<T, TW>(int, const AdjParams &, cudaStream_t);          \

@@ -55,6 +55,7 @@ struct PlaceParams {
     const void *V;           // compact coarse array (type TW)
     int64_t n0, n1, n2, m0, m1, m2;
     const void *w0, *w1, *w2;  // interpolation weight pairs per fine node, type T
+    int64_t zchunk, nzc;     // k_sweep: fine planes per work item (even), chunk count
 };
 
 // Transposed level maps (adjoint.cuh).

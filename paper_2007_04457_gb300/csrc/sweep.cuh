@@ -1,0 +1,175 @@
+// sweep.cuh -- the element-wise level kernels as warp-tile sweeps.
+//
+// k_sweep<MODE_DEC> (decomposition, after the coarser levels are done):
+//   every node of N_l \ N_{l-1} receives its coefficient u - Pi_{l-1} u
+//   (Section II-A-1), the N_{l-1} nodes are rewritten with their own
+//   unchanged value (whole sectors are written, and a neighbouring tile that
+//   reads them as interpolation corners sees the same bits either way).
+// k_sweep<MODE_REC> (recomposition, Section II-A): the N_{l-1} nodes
+//   receive the corrected coarse values V, every other node its coefficient
+//   plus the multilinear interpolant of V.
+//
+// The interpolant is evaluated separably, dim 2 first, then dim 1, then dim
+// 0, each step an explicitly rounded two-point combination (lerp2), so the
+// coefficients are bit-identical to the C the restriction kernel computed.
+//
+// Work item of one warp: 32 consecutive columns (lane = column) x 16 fine
+// rows (1 in 1D) x a chunk of fine planes.  The warp streams the chunk's even planes;
+// for each it forms the dim-2 interpolant X of its even rows (odd columns
+// from the lane's neighbours by shuffles, even columns exact), the dim-1
+// interpolant of its odd rows, and keeps that plane's interpolant I2 in
+// registers; the odd plane before it then needs only the two I2 planes
+// around it.  A tile reads one halo row (its next even row) and a chunk one
+// halo plane (its next even plane); in both only nodes of N_{l-1} are used.
+#pragma once
+
+#include "common.cuh"
+#include "params.h"
+
+namespace mg {
+
+constexpr int kSweepWarps = 4;  // warps per block
+
+// fine rows per warp item (1 for one-dimensional grids; fewer for 8-byte
+// elements, whose register arrays are twice as large)
+template <int ACT, int ELEM>
+struct SweepRows {
+    static constexpr int value = (ACT & 2) ? (ELEM == 4 ? 16 : 8) : 1;
+};
+
+template <typename T, typename TW, int ACT, int MODE>
+__global__ void __launch_bounds__(32 * kSweepWarps, 4) k_sweep(PlaceParams p)
+{
+    constexpr bool HZ = (ACT & 4) != 0, HY = (ACT & 2) != 0;
+    constexpr bool DEC = (MODE == MODE_DEC);
+    constexpr int R = SweepRows<ACT, (int)sizeof(T)>::value;
+    constexpr int RE = R / 2 + 1;  // even rows of a tile, with its halo row
+    T *__restrict__ A = static_cast<T *>(p.A);
+    const TW *__restrict__ V = static_cast<const TW *>(p.V);
+    const T *__restrict__ w0 = static_cast<const T *>(p.w0);
+    const T *__restrict__ w1 = static_cast<const T *>(p.w1);
+    const T *__restrict__ w2 = static_cast<const T *>(p.w2);
+    const int64_t n0 = p.n0, n1 = p.n1, n2 = p.n2, m1 = p.m1, m2 = p.m2;
+    const int sn2 = (int)n2;  // row stride (a level array row has < 2^31 nodes)
+    const int L = threadIdx.x & 31;
+    const int64_t warp0 = (int64_t)blockIdx.x * kSweepWarps + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * kSweepWarps;
+    const int64_t tiles_x = (n2 + 31) / 32;
+    const int64_t tiles_y = HY ? (n1 + R - 1) / R : 1;
+    const int64_t zc = p.zchunk;
+    const int64_t items = tiles_x * tiles_y * p.nzc;
+
+    for (int64_t item = warp0; item < items; item += nwarps) {
+        const int64_t tx = item % tiles_x;
+        const int64_t rest = item / tiles_x;
+        const int64_t ty = rest % tiles_y;
+        const int64_t tz = rest / tiles_y;
+        const int64_t x = tx * 32 + L;
+        const bool xv = x < n2;
+        const bool xo = xv && (x & 1);          // odd columns are interior (n2 - 1 is even)
+        const T wl2 = xo ? w2[2 * x] : T(1), wr2 = xo ? w2[2 * x + 1] : T(0);
+        const int64_t y0 = ty * R;
+        const int nrow = (int)min64(R, n1 - y0);           // own rows
+        const bool hrow = HY && (y0 + R < n1);              // halo row y0 + R exists
+        const int64_t z0 = HZ ? tz * zc : 0;
+        const int64_t z1 = HZ ? min64(z0 + zc, n0) : 1;     // own planes [z0, z1)
+        const int64_t zlast = (HZ && z1 < n0) ? z1 : z1 - 1;  // even: halo plane or the last plane
+
+        T I2p[R], I2c[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) I2p[r] = I2c[r] = T(0);
+
+        for (int64_t z = z0; z <= zlast; z += (HZ ? 2 : 1)) {
+            const bool own = z < z1;
+            const bool odd_plane = HZ && z > z0;  // the odd plane z - 1 is processed with this one
+            // the tile's first row at column x, in this plane and the odd one
+            T *plane = A + (z * n1 + y0) * n2 + (xv ? x : 0);
+            T *oplane = A + ((odd_plane ? z - 1 : z) * n1 + y0) * n2 + (xv ? x : 0);
+            // ---- every load of the step first (the stores below go to the same
+            // array, so loads issued after them could not be moved ahead)
+            T ue[RE], va[RE], vb[RE], uo[R], uz[R];
+#pragma unroll
+            for (int e = 0; e < RE; ++e) {
+                const int r = 2 * e;
+                ue[e] = va[e] = vb[e] = T(0);
+                const bool live = (HY || r == 0) && (r < nrow || (r == R && hrow));
+                const bool mine = own && r < nrow;
+                const T *row = plane + r * sn2;
+                if constexpr (DEC) {
+                    // outside the tile's own rows and planes only N_{l-1} nodes
+                    // (even columns) are read: the others belong to another tile
+                    if (live && xv && (mine || !(x & 1))) ue[e] = row[0];
+                } else {
+                    if (live) {
+                        const TW *vrow = V + ((z >> (HZ ? 1 : 0)) * m1 + ((y0 + r) >> 1)) * m2;
+                        if (xv) va[e] = static_cast<T>(vrow[x >> 1]);
+                        if (xo) vb[e] = static_cast<T>(vrow[(x >> 1) + 1]);
+                    }
+                    if (live && mine && xo) ue[e] = row[0];
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                uo[r] = uz[r] = T(0);
+                if (r >= nrow) continue;
+                if (HY && (r & 1) && own && xv) uo[r] = plane[r * sn2];
+                if (odd_plane && xv) uz[r] = oplane[r * sn2];
+            }
+            // ---- dim-2 interpolant of the even rows
+            T Xe[RE];
+#pragma unroll
+            for (int e = 0; e < RE; ++e) {
+                if constexpr (DEC) {
+                    T un = __shfl_down_sync(0xffffffffu, ue[e], 1);
+                    const T up = __shfl_up_sync(0xffffffffu, ue[e], 1);
+                    const int r = 2 * e;
+                    const bool live = (HY || r == 0) && (r < nrow || (r == R && hrow));
+                    if (L == 31 && xo && live) un = plane[r * sn2 + 1];
+                    Xe[e] = xo ? lerp2(wl2, up, wr2, un) : ue[e];
+                } else {
+                    Xe[e] = xo ? lerp2(wl2, va[e], wr2, vb[e]) : va[e];
+                }
+            }
+            // ---- the plane's interpolant I2 (dim 1 on the odd rows)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (HY && (r & 1) && r < nrow) {
+                    const T wyl = w1[2 * (y0 + r)], wyr = w1[2 * (y0 + r) + 1];
+                    I2c[r] = lerp2(wyl, Xe[r / 2], wyr, Xe[r / 2 + 1]);
+                } else {
+                    I2c[r] = Xe[r / 2];
+                }
+            }
+            // ---- stores
+            if (own && xv) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (r >= nrow) break;
+                    T out;
+                    if (HY && (r & 1)) {
+                        out = DEC ? sub_rn(uo[r], I2c[r]) : add_rn(uo[r], I2c[r]);
+                    } else {
+                        const T u = ue[r / 2];
+                        if constexpr (DEC) out = xo ? sub_rn(u, Xe[r / 2]) : u;
+                        else out = xo ? add_rn(u, Xe[r / 2]) : Xe[r / 2];
+                    }
+                    plane[r * sn2] = out;
+                }
+            }
+            if (odd_plane && xv) {
+                const int64_t zo = z - 1;
+                const T wzl = w0[2 * zo], wzr = w0[2 * zo + 1];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (r >= nrow) break;
+                    const T I = lerp2(wzl, I2p[r], wzr, I2c[r]);
+                    oplane[r * sn2] = DEC ? sub_rn(uz[r], I) : add_rn(uz[r], I);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) I2p[r] = I2c[r];
+        }
+    }
+}
+
+}  // namespace mg
