@@ -4,10 +4,10 @@ Section III-C tunes thread-block sizes with a performance model that counts
 memory transactions per configuration, then times only the best-ranked few
 configurations.  This module does the same for the GB300 kernels:
 
-* ``restriction_model`` estimates, for a tile height, the bytes the fused
-  restriction kernel moves at the finest level (every tile loads its rows
-  plus a 2-row/2-column halo in whole 32-byte sectors, and the last tile of a
-  dimension may be ragged), relative to the bytes of the field;
+* ``restriction_model`` estimates, for a tile height, the bytes the
+  load-vector kernel moves at the finest level (every tile loads its rows
+  plus a 3-row/4-column halo in whole 32-byte sectors, and the last tile of
+  a dimension may be ragged), relative to the bytes of the field;
 * ``tune`` ranks the tile configurations by that estimate, keeps the best
   ``top`` (three, as the paper does), times each of them with every solve
   warp count on the real plan, applies the fastest and caches it per
@@ -19,7 +19,7 @@ import json
 import math
 import os
 
-TILE_ROWS = {0: 8, 1: 4, 2: 16}    # restriction config -> coarse rows per tile
+CONFIGS = (0, 1, 2)                 # load-vector tile configurations
 TILE_COLS = 64                      # coarse columns per tile
 SOLVE_WARPS = (0, 8, 16)            # 0 = automatic
 SECTOR = 32
@@ -34,6 +34,13 @@ def _tiles(m: int, t: int):
     return [t] * (n - 1) + [m - t * (n - 1)]
 
 
+def tile_rows(cfg: int, ndim: int, elem_bytes: int) -> int:
+    """Coarse rows per tile of the load-vector kernel for configuration
+    ``cfg`` (8, 4 or 16; the same for every dimension count and element
+    size)."""
+    return {0: 8, 1: 4, 2: 16}[cfg]
+
+
 def restriction_model(shape, elem_bytes: int, cfg: int) -> float:
     """Estimated loaded bytes / field bytes of the finest-level restriction
     for tile configuration ``cfg`` (>= 1; smaller is better)."""
@@ -42,7 +49,7 @@ def restriction_model(shape, elem_bytes: int, cfg: int) -> float:
         return 1.0
     n1, n2 = shape[-2], shape[-1]
     m1, m2 = (n1 - 1) // 2 + 1, (n2 - 1) // 2 + 1
-    rows = sum(2 * t + 3 for t in _tiles(m1, TILE_ROWS[cfg]))
+    rows = sum(2 * t + 3 for t in _tiles(m1, tile_rows(cfg, len(shape), elem_bytes)))
     cols_bytes = sum(math.ceil((2 * t + 8) * elem_bytes / SECTOR) * SECTOR for t in _tiles(m2, TILE_COLS))
     planes = shape[0] if len(shape) == 3 else 1
     loaded = rows * cols_bytes * planes
@@ -50,9 +57,17 @@ def restriction_model(shape, elem_bytes: int, cfg: int) -> float:
 
 
 def ranked_configs(shape, elem_bytes: int, top: int = 3):
-    """Tile configurations ordered by the model, best first, cut to ``top``."""
-    order = sorted(TILE_ROWS, key=lambda c: (restriction_model(shape, elem_bytes, c), c))
-    return order[:top]
+    """Tile configurations ordered by the model, best first, without
+    configurations that give the same tile as a better one, cut to ``top``."""
+    ndim = len([n for n in shape if int(n) > 1])
+    order = sorted(CONFIGS, key=lambda c: (restriction_model(shape, elem_bytes, c), c))
+    out, seen = [], set()
+    for c in order:
+        t = tile_rows(c, ndim, elem_bytes)
+        if t not in seen:
+            seen.add(t)
+            out.append(c)
+    return out[:top]
 
 
 def _cache_path():

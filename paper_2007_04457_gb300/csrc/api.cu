@@ -55,7 +55,8 @@ struct mgard_level {
     int64_t k_off[3];    // R*M stencil rows (5 per coarse node)
     int64_t t_off[3];    // tridiagonal factors of M_{l-1} (3 per coarse node)
     size_t v_off, f_off; // workspace offsets of V_j and F_j (bytes)
-    int rcfg;            // fused-restriction tile configuration
+    int rcfg;            // load-vector tile configuration
+    bool rcfg_user;      // set by mgard_plan_tune (else chosen per level)
     int svar;            // warps per line in the solve kernel (0 = automatic)
     int zreq;            // requested coarse planes per restriction item (0 = automatic)
     int zchunk, nzc, tiles_y, tiles_x;
@@ -268,13 +269,19 @@ PlaceParams place_params(const mgard_plan *P, int j, void *A, char *ws)
     return p;
 }
 
-// Coefficients and final coarse values into the level array (decomposition).
+// Coefficients of a decomposition level, in place (before its restriction).
 template <typename T, typename TW>
-cudaError_t run_place_level(const mgard_plan *P, int j, void *A, char *ws, cudaStream_t st)
+cudaError_t run_coef_level(const mgard_plan *P, int j, void *A, char *ws, cudaStream_t st)
 {
     const PlaceParams p = place_params<T>(P, j, A, ws);
-    cudaError_t err = timed(P, KIND_PLACE, j, st, [&] { return launch_coef<T, TW>(P->act, p, P->num_sms, st); });
-    if (err != cudaSuccess) return err;
+    return timed(P, KIND_PLACE, j, st, [&] { return launch_coef<T, TW>(P->act, p, P->num_sms, st); });
+}
+
+// Final coarse values V_j into the N_{l-1} nodes of the level array.
+template <typename T, typename TW>
+cudaError_t run_scatter_level(const mgard_plan *P, int j, void *A, char *ws, cudaStream_t st)
+{
+    const PlaceParams p = place_params<T>(P, j, A, ws);
     return timed(P, KIND_PLACE_EVEN, j, st, [&] { return launch_scatter<T, TW>(P->act, p, st); });
 }
 
@@ -310,9 +317,11 @@ cudaError_t run_small(const mgard_plan *P, int mode, void *A, cudaStream_t st)
 
 // Decomposition, levels L..1 (Section II-A): level j = 0 works on the user
 // array (element type TU), deeper levels on the compact coarse arrays V_{j-1}
-// of the workspace (type TW).  Each level's restriction only reads its array;
-// after all levels, coarsest first, every level array receives its
-// coefficients and the final values of its coarse nodes.
+// of the workspace (type TW).  Per level: the coefficients go in place (they
+// depend only on the level's own values), the restriction reads them and
+// gathers the coarse nodes into V_j, and the solves add the correction to
+// V_j.  The levels from small_j on run in one block; then, coarsest first,
+// every level array receives the final values of its coarse nodes.
 template <typename TU, typename TW>
 mgard_status exec_decompose(const mgard_plan *P, void *data, char *ws, cudaStream_t st)
 {
@@ -320,9 +329,11 @@ mgard_status exec_decompose(const mgard_plan *P, void *data, char *ws, cudaStrea
     const int J = P->small_j;
     for (int j = 0; j < J; ++j) {
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
+        err = (j == 0) ? run_coef_level<TU, TW>(P, j, A, ws, st) : run_coef_level<TW, TW>(P, j, A, ws, st);
+        if (err != cudaSuccess) return cuda_fail(err, "decompose: coefficient kernel");
         err = (j == 0) ? run_restrict_level<TU, TW>(P, j, MODE_DEC, A, ws, st)
                        : run_restrict_level<TW, TW>(P, j, MODE_DEC, A, ws, st);
-        if (err != cudaSuccess) return cuda_fail(err, "decompose: coefficient/load-vector kernel");
+        if (err != cudaSuccess) return cuda_fail(err, "decompose: load-vector kernel");
         err = run_solves<TW>(P, j, +1, ws, st);
         if (err != cudaSuccess) return cuda_fail(err, "decompose: correction solve kernel");
     }
@@ -333,8 +344,8 @@ mgard_status exec_decompose(const mgard_plan *P, void *data, char *ws, cudaStrea
     }
     for (int j = J - 1; j >= 0; --j) {
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
-        err = (j == 0) ? run_place_level<TU, TW>(P, j, A, ws, st) : run_place_level<TW, TW>(P, j, A, ws, st);
-        if (err != cudaSuccess) return cuda_fail(err, "decompose: coefficient placement kernel");
+        err = (j == 0) ? run_scatter_level<TU, TW>(P, j, A, ws, st) : run_scatter_level<TW, TW>(P, j, A, ws, st);
+        if (err != cudaSuccess) return cuda_fail(err, "decompose: coarse placement kernel");
     }
     return MGARD_OK;
 }
@@ -461,28 +472,29 @@ mgard_status exec_recompose_adjoint(const mgard_plan *P, void *data, char *ws, c
     return MGARD_OK;
 }
 
+// Launch configuration of a level's load-vector kernel for tile
+// configuration L.rcfg (tile grid, plane chunks, grid size).
 template <typename TU, typename TW>
-cudaError_t configure_level(mgard_plan *P, mgard_level &L, bool finest)
+cudaError_t configure_restrict(const mgard_plan *P, mgard_level &L, bool finest, int64_t *items_out,
+                               int64_t *slots_out)
 {
     RestrictShape sh;
     cudaError_t err = finest ? restrict_shape<TU, TW>(P->act, MODE_DEC, L.rcfg, &sh)
                              : restrict_shape<TW, TW>(P->act, MODE_DEC, L.rcfg, &sh);
-    if (err != cudaSuccess) return err;
-    RestrictShape shr;
-    err = finest ? restrict_shape<TU, TW>(P->act, MODE_REC, L.rcfg, &shr)
-                 : restrict_shape<TW, TW>(P->act, MODE_REC, L.rcfg, &shr);
     if (err != cudaSuccess) return err;
     // tiles of ty x tx coarse nodes; the last tile of a dimension also takes
     // the final node, so there are ceil((m-1)/t) tiles
     L.tiles_y = (P->act == ACT_1D) ? 1 : (int)std::max<int64_t>(1, (L.m[1] - 1 + sh.ty - 1) / sh.ty);
     L.tiles_x = (int)std::max<int64_t>(1, (L.m[2] - 1 + sh.tx - 1) / sh.tx);
     const int64_t tiles = (int64_t)L.tiles_y * L.tiles_x;
-    const int64_t slots = (int64_t)std::max(1, sh.blocks_per_sm) * P->num_sms;
+    const int64_t ipb = std::max(1, sh.items_per_block);
+    const int64_t slots = (int64_t)std::max(1, sh.blocks_per_sm) * P->num_sms * ipb;  // resident items
     if (P->act == ACT_3D) {
-        // enough items for about two per resident CTA, chunks of >= 4 planes;
-        // the last chunk takes the final plane
+        // enough items for about two per resident slot, chunks of >= 2 coarse
+        // planes (each chunk also reads 3 fine planes of its neighbours); the
+        // last chunk takes the final plane
         int64_t nzc = std::max<int64_t>(1, (2 * slots + tiles - 1) / tiles);
-        nzc = std::min<int64_t>(nzc, std::max<int64_t>(1, (L.m[0] - 1) / 4));
+        nzc = std::min<int64_t>(nzc, std::max<int64_t>(1, (L.m[0] - 1) / 2));
         L.zchunk = (int)std::max<int64_t>(1, (L.m[0] - 1 + nzc - 1) / nzc);
         if (L.zreq > 0) L.zchunk = L.zreq;
         L.nzc = (int)std::max<int64_t>(1, (L.m[0] - 1 + L.zchunk - 1) / L.zchunk);
@@ -491,13 +503,47 @@ cudaError_t configure_level(mgard_plan *P, mgard_level &L, bool finest)
         L.nzc = 1;
     }
     if (P->act == ACT_1D) {
-        // per-coarse-node kernel: items are blocks of sh.tx coarse nodes
+        // per-coarse-node kernel: blocks of sh.tx coarse nodes
         L.tiles_x = (int)std::max<int64_t>(1, (L.m[2] + sh.tx - 1) / sh.tx);
     }
     const int64_t items = (P->act == ACT_1D) ? L.tiles_x : tiles * L.nzc;
-    L.rgrid_dec = (int)std::min<int64_t>(items, std::max(1, sh.blocks_per_sm) * (int64_t)P->num_sms);
-    L.rgrid_rec = (int)std::min<int64_t>(items, std::max(1, shr.blocks_per_sm) * (int64_t)P->num_sms);
+    const int64_t blocks = (items + ipb - 1) / ipb;
+    L.rgrid_dec = L.rgrid_rec = (int)std::min<int64_t>(blocks, std::max(1, sh.blocks_per_sm) * (int64_t)P->num_sms);
+    *items_out = items;
+    *slots_out = slots;
     return cudaSuccess;
+}
+
+// Unless the tile configuration was set by mgard_plan_tune, take the tallest
+// tile (fewest halo rows re-read) that still gives every resident slot of the
+// GPU a work item (small levels need short tiles to spread over the SMs),
+// else the one with the most items.
+template <typename TU, typename TW>
+cudaError_t configure_level(mgard_plan *P, mgard_level &L, bool finest)
+{
+    int64_t items = 0, slots = 0;
+    if (L.rcfg_user || P->act == ACT_1D) return configure_restrict<TU, TW>(P, L, finest, &items, &slots);
+    int best = 0;
+    int64_t best_items = -1;
+    static const int order[kRestrictConfigs] = {2, 0, 1};  // 16, 8, 4 coarse rows
+    for (int cfg : order) {
+        L.rcfg = cfg;
+        cudaError_t err = configure_restrict<TU, TW>(P, L, finest, &items, &slots);
+        if (err != cudaSuccess) {  // e.g. more shared memory than the device has
+            cudaGetLastError();
+            continue;
+        }
+        if (items >= slots) {
+            best = cfg;
+            break;
+        }
+        if (items > best_items) {
+            best_items = items;
+            best = cfg;
+        }
+    }
+    L.rcfg = best;
+    return configure_restrict<TU, TW>(P, L, finest, &items, &slots);
 }
 
 }  // namespace
@@ -626,10 +672,9 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
         lv.f_off = ws;
         ws = align_up(ws + mbytes);
         lv.rcfg = 0;
+        lv.rcfg_user = false;
         lv.svar = 0;
         lv.zreq = 0;
-        if (P->act != ACT_1D && (j == 0 ? P->elem_user : P->elem_ws) == 8)
-            lv.rcfg = 1;  // 8-byte levels: 4 x 64 tiles keep two CTAs per SM
         for (int k = 0; k < nd; ++k) {
             const int q = 3 - nd + k;
             if (lv.m[q] > kMaxLine) {
@@ -879,6 +924,7 @@ mgard_status mgard_plan_tune(mgard_plan *P, int level, int param, int value)
     case 0:
         if (value < 0 || value >= kRestrictConfigs) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: tile config");
         L.rcfg = value;
+        L.rcfg_user = true;
         break;
     case 1:
         if (value < 0 || value > 32) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: solve warps");

@@ -9,15 +9,16 @@
 
 namespace mg {
 
-// Tile shapes of the fused restriction kernel selectable per level (coarse
-// nodes in dims 1 x 2; a last tile absorbs the final node of a dimension):
-//   2D/3D: cfg 0 = 8 x 64, cfg 1 = 4 x 64, cfg 2 = 16 x 64;  1D: 64
+// Tile shapes of the load-vector kernel selectable per level (coarse nodes in
+// dims 1 x 2; a last tile absorbs the final node of a dimension):
+//   2D/3D: cfg 0 = 8 x 64, cfg 1 = 4 x 64, cfg 2 = 16 x 64;  1D: 256 per block
 constexpr int kRestrictConfigs = 3;
 
 struct RestrictShape {
-    int ty, tx;          // coarse nodes per tile in dims 1 and 2
-    size_t smem;         // dynamic shared memory bytes
-    int blocks_per_sm;   // occupancy of the instantiation
+    int ty, tx;            // coarse nodes per tile in dims 1 and 2
+    size_t smem;           // dynamic shared memory bytes
+    int blocks_per_sm;     // occupancy of the instantiation
+    int items_per_block;   // work items a block runs at once
 };
 
 template <typename T, typename TW>

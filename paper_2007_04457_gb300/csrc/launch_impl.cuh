@@ -18,40 +18,43 @@ namespace detail {
 
 struct RestrictEntry {
     void (*fn)(RestrictParams);
-    int ty, tx;
-    size_t smem;
+    int ty, tx;          // coarse rows / columns per tile (1D: coarse nodes per block)
+    size_t smem;         // dynamic shared memory bytes
 };
 
-template <typename T, typename TW, int ACT, int MODE, int TY>
+template <typename T, typename TW, int ACT, int TY>
 RestrictEntry restrict_entry()
 {
-    using G = RestrictGeom<T, ACT, MODE, TY>;
-    return {k_restrict<T, TW, ACT, MODE, TY>, G::TY, kRestrictTX, sizeof(T) * (size_t)G::TOTAL};
+    using G = RestrictGeom<T, ACT, TY>;
+    return {k_restrict<T, TW, ACT, TY>, G::TY, kRestrictTX, sizeof(T) * (size_t)G::TOTAL};
 }
 
-template <typename T, typename TW, int ACT, int MODE>
+// Tile configuration 0 / 1 / 2 = 8 / 4 / 16 coarse rows.  Both directions
+// read a level array that holds coefficients on N_l \ N_{l-1} (the
+// decomposition writes them before its restriction), so one kernel serves
+// both.
+template <typename T, typename TW, int ACT>
 RestrictEntry restrict_pick_cfg(int cfg)
 {
     if constexpr (ACT == ACT_1D) {
-        return {k_restrict1d<T, TW, MODE>, 1, 256, 0};
+        return {k_restrict1d<T, TW>, 1, 256, 0};
     } else {
         switch (cfg) {
-        case 1: return restrict_entry<T, TW, ACT, MODE, 4>();
-        case 2: return restrict_entry<T, TW, ACT, MODE, 16>();
-        default: return restrict_entry<T, TW, ACT, MODE, 8>();
+        case 1: return restrict_entry<T, TW, ACT, 4>();
+        case 2: return restrict_entry<T, TW, ACT, 16>();
+        default: return restrict_entry<T, TW, ACT, 8>();
         }
     }
 }
 
 template <typename T, typename TW>
-bool restrict_pick(int act, int mode, int cfg, RestrictEntry *e)
+bool restrict_pick(int act, int cfg, RestrictEntry *e)
 {
     if (cfg < 0 || cfg >= kRestrictConfigs) return false;
-    const bool dec = (mode == MODE_DEC);
     switch (act) {
-    case ACT_1D: *e = dec ? restrict_pick_cfg<T, TW, ACT_1D, MODE_DEC>(cfg) : restrict_pick_cfg<T, TW, ACT_1D, MODE_REC>(cfg); return true;
-    case ACT_2D: *e = dec ? restrict_pick_cfg<T, TW, ACT_2D, MODE_DEC>(cfg) : restrict_pick_cfg<T, TW, ACT_2D, MODE_REC>(cfg); return true;
-    case ACT_3D: *e = dec ? restrict_pick_cfg<T, TW, ACT_3D, MODE_DEC>(cfg) : restrict_pick_cfg<T, TW, ACT_3D, MODE_REC>(cfg); return true;
+    case ACT_1D: *e = restrict_pick_cfg<T, TW, ACT_1D>(cfg); return true;
+    case ACT_2D: *e = restrict_pick_cfg<T, TW, ACT_2D>(cfg); return true;
+    case ACT_3D: *e = restrict_pick_cfg<T, TW, ACT_3D>(cfg); return true;
     default: return false;
     }
 }
@@ -71,8 +74,9 @@ inline cudaError_t prepare(void (*fn)(RestrictParams), size_t smem, int *bps)
 template <typename T, typename TW>
 cudaError_t restrict_shape(int act, int mode, int cfg, RestrictShape *out)
 {
+    (void)mode;
     detail::RestrictEntry e;
-    if (!detail::restrict_pick<T, TW>(act, mode, cfg, &e)) return cudaErrorInvalidValue;
+    if (!detail::restrict_pick<T, TW>(act, cfg, &e)) return cudaErrorInvalidValue;
     int bps = 0;
     cudaError_t err = detail::prepare(e.fn, e.smem, &bps);
     if (err != cudaSuccess) return err;
@@ -80,14 +84,16 @@ cudaError_t restrict_shape(int act, int mode, int cfg, RestrictShape *out)
     out->tx = e.tx;
     out->smem = e.smem;
     out->blocks_per_sm = bps;
+    out->items_per_block = 1;
     return cudaSuccess;
 }
 
 template <typename T, typename TW>
 cudaError_t launch_restrict(int act, int mode, int cfg, const RestrictParams &p, int grid, cudaStream_t st)
 {
+    (void)mode;
     detail::RestrictEntry e;
-    if (!detail::restrict_pick<T, TW>(act, mode, cfg, &e)) return cudaErrorInvalidValue;
+    if (!detail::restrict_pick<T, TW>(act, cfg, &e)) return cudaErrorInvalidValue;
     e.fn<<<grid, kRestrictThreads, e.smem, st>>>(p);
     return cudaGetLastError();
 }

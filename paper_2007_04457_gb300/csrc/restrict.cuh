@@ -1,26 +1,21 @@
-// restrict.cuh -- fused coefficient + load-vector kernel (one level).
+// restrict.cuh -- load vector and coarse gather of one level (both directions).
 //
-// For a level array A with node counts (n0, n1, n2) and coarse counts
-// (m0, m1, m2) = ((n-1)/2 + 1), one pass computes
-//   MODE_DEC: C = A - Pi_{l-1} A on N_l \ N_{l-1} (multilinear interpolation
-//             from the even-index corners, Section II-A-1);
-//   MODE_REC: C = A on N_l \ N_{l-1} (A already holds coefficients);
-// and in both modes
-//   F = (K_0 (x) K_1 (x) K_2) C,  K = P^T M_l (mass then transfer along each
-//       dimension, a 5-point stencil per coarse node, Section III-A-2)
-//   V = A restricted to N_{l-1} (compact).
-// The kernel only reads A: tiles overlap in their halos, so writing
-// coefficients in place here would race with neighbouring tiles that still
-// need the original values.  The decomposition writes them afterwards
-// (k_place), with the same explicitly rounded interpolation, so the stored
-// coefficients are bit-identical to the C used here.
+// The level array A holds the coefficients C on N_l \ N_{l-1} (the
+// decomposition writes them before this pass) and coarse values on N_{l-1}.
+// One pass computes
+//   F = (K_0 (x) K_1 (x) K_2) C,  C = A on N_l \ N_{l-1}, 0 on N_{l-1}
+//       (K = P^T M_l: mass then transfer along each dimension, a 5-point
+//       stencil per coarse node, Section III-A-2)
+//   V = A restricted to N_{l-1} (compact)
+// and only reads A.
 //
-// Work item = tile of TY x 64 coarse nodes in dims (1, 2) (the last tile of a
+// Two- and three-dimensional levels (k_restrict): work item = tile of TY x
+// 64 coarse nodes in dims (1, 2) (the last tile of a
 // dimension absorbs the final node, so it may hold TY+1 x 65) x a chunk of
 // coarse planes in dim 0.  The CTA streams the fine planes of its chunk
 // through shared memory with cp.async, one step ahead; each step handles the
-// odd plane 2Z-1 and the even plane 2Z, so the dim-0 parts of both the
-// interpolation and the stencil reduce to rolling register accumulators.
+// odd plane 2Z-1 and the even plane 2Z, so the dim-0 part of the stencil
+// reduces to rolling register accumulators.
 //
 // Every warp shuffle below runs in all 32 lanes (full mask) and the lanes
 // that need a halo value select it afterwards; a shuffle under a lane
@@ -28,12 +23,13 @@
 //
 // Thread mapping inside a plane: warp w takes slab rows w, w+8, ...; lane L
 // takes the four fine columns 4L..4L+3 of the tile (coarse columns 2L and
-// 2L+1), so the interpolation parities are uniform within a warp, the row
-// loads are 128-bit shared-memory loads, and the 5-point dim-2 stencil takes
-// its two left and one right neighbour values from the adjacent lanes by
-// shuffles.  Lane 0 also covers the two fine columns left of the tile and
-// lane 31 the one on its right (and the 65th coarse column of a last tile).
-// The dim-1 stencil then reads the dim-2-restricted rows from shared memory.
+// 2L+1), so the row loads are 128-bit shared-memory loads, and the 5-point
+// dim-2 stencil takes its two left and one right neighbour values from the
+// adjacent lanes by shuffles.  Lane 0 also covers the two fine columns left
+// of the tile and lane 31 the one on its right (and the 65th coarse column
+// of a last tile).  The dim-1 stencil then reads the dim-2-restricted rows
+// from shared memory.
+// One-dimensional levels (k_restrict1d): one thread per coarse node.
 #pragma once
 
 #include "common.cuh"
@@ -44,11 +40,10 @@ namespace mg {
 constexpr int kRestrictThreads = 256;
 constexpr int kRestrictTX = 64;  // coarse columns per tile (+1 in a last tile)
 
-template <typename T, int ACT, int MODE, int TY_>
+template <typename T, int ACT, int TY_>
 struct RestrictGeom {
     static constexpr bool HZ = (ACT & 4) != 0;
     static constexpr bool HY = (ACT & 2) != 0;
-    static constexpr bool DEC = (MODE == MODE_DEC);
     static constexpr int TY = HY ? TY_ : 1;
     static constexpr int RYM = HY ? 2 * TY + 5 : 1;   // slab rows, sized for a TY+1 last tile
     static constexpr int SP = 136;                    // slab pitch: fine cols 2X0-4 .. 2X0+131
@@ -59,11 +54,9 @@ struct RestrictGeom {
     static constexpr int PPT = (OUTS + NT - 1) / NT;       // output slots per thread
 
     // shared memory layout, in elements of T
-    static constexpr int OFF_SLAB = 0;                                      // 4 slabs
-    static constexpr int OFF_I = OFF_SLAB + 4 * RYM * SP;                   // 2 interpolant planes
-    static constexpr int OFF_H = OFF_I + ((DEC && HZ) ? 2 * RYM * SP : 0);  // 2 restricted planes
-    static constexpr int OFF_WY = OFF_H + 2 * RYM * HP;                     // dim-1 weights
-    static constexpr int OFF_KY = OFF_WY + 2 * RYM;                         // dim-1 stencil rows
+    static constexpr int OFF_SLAB = 0;                   // 4 slabs
+    static constexpr int OFF_H = OFF_SLAB + 4 * RYM * SP;  // 2 restricted planes
+    static constexpr int OFF_KY = OFF_H + 2 * RYM * HP;    // dim-1 stencil rows
     static constexpr int TOTAL = OFF_KY + 5 * (TY + 1);
 };
 
@@ -128,29 +121,24 @@ constexpr int restrict_min_blocks()
     return (sizeof(T) == 4 && TY_ <= 4) ? 4 : 2;
 }
 
-template <typename T, typename TW, int ACT, int MODE, int TY_>
+template <typename T, typename TW, int ACT, int TY_>
 __global__ void __launch_bounds__(kRestrictThreads, (restrict_min_blocks<T, TY_>()))
 k_restrict(RestrictParams p)
 {
-    using G = RestrictGeom<T, ACT, MODE, TY_>;
-    constexpr bool HZ = G::HZ, HY = G::HY, DEC = G::DEC;
+    using G = RestrictGeom<T, ACT, TY_>;
+    constexpr bool HZ = G::HZ, HY = G::HY;
     constexpr int TY = G::TY, RYM = G::RYM, SP = G::SP, HP = G::HP;
     constexpr int NT = G::NT, NWARP = G::NWARP, PPT = G::PPT;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     T *slab = sm + G::OFF_SLAB;
-    T *Ib = sm + G::OFF_I;
     T *Hb = sm + G::OFF_H;
-    T *swy = sm + G::OFF_WY;
     T *sky = sm + G::OFF_KY;
 
     const T *A = static_cast<const T *>(p.A);
     TW *F = static_cast<TW *>(p.F);
     TW *V = static_cast<TW *>(p.V);
-    const T *w0 = static_cast<const T *>(p.w0);
-    const T *w1 = static_cast<const T *>(p.w1);
-    const T *w2 = static_cast<const T *>(p.w2);
     const T *k0 = static_cast<const T *>(p.k0);
     const T *k1 = static_cast<const T *>(p.k1);
     const T *k2 = static_cast<const T *>(p.k2);
@@ -178,19 +166,8 @@ k_restrict(RestrictParams p)
         const int64_t Zfirst = (HZ && Zs > 0) ? Zs - 1 : Zs;
         const int64_t Zlast = HZ ? min64(Ze, m0 - 1) : 0;
 
-        // per-lane tables: dim-2 weights of the odd columns 4L+1, 4L+3 (and
-        // lane 0's halo column -1), stencil rows of coarse columns 2L, 2L+1
-        // (and lane 31's column 64 of a 65-wide tile)
-        auto wxl_at = [&](int64_t gx) -> T {
-            return (gx > 0 && gx < n2 - 1 && (gx & 1)) ? w2[2 * gx] : T(0);
-        };
-        auto wxr_at = [&](int64_t gx) -> T {
-            return (gx > 0 && gx < n2 - 1 && (gx & 1)) ? w2[2 * gx + 1] : T(0);
-        };
-        const int64_t gxl = 2 * X0 + 4 * L;  // fine column of the lane's first node
-        const T wa1 = wxl_at(gxl + 1), wb1 = wxr_at(gxl + 1);
-        const T wa3 = wxl_at(gxl + 3), wb3 = wxr_at(gxl + 3);
-        const T wah = wxl_at(2 * X0 - 1), wbh = wxr_at(2 * X0 - 1);
+        // per-lane stencil rows of coarse columns 2L, 2L+1 (and lane 31's
+        // column 64 of a 65-wide tile)
         T ka[5], kb[5], kc[5];
 #pragma unroll
         for (int t = 0; t < 5; ++t) {
@@ -209,12 +186,6 @@ k_restrict(RestrictParams p)
 
         __syncthreads();  // the previous item is done with shared memory
         if constexpr (HY) {
-            for (int r = tid; r < RY; r += NT) {
-                const int64_t gy = gy0 + r;
-                const bool odd = (gy > 0) && (gy < n1 - 1) && (gy & 1);
-                swy[2 * r] = odd ? w1[2 * gy] : T(0);
-                swy[2 * r + 1] = odd ? w1[2 * gy + 1] : T(0);
-            }
             for (int e = tid; e < 5 * (TY + 1); e += NT) {
                 const int Y = e / 5;
                 sky[e] = (Y < TYo) ? k1[5 * (Y0 + Y) + (e % 5)] : T(0);
@@ -261,15 +232,8 @@ k_restrict(RestrictParams p)
             const bool own_even = (Z >= Zs) && (Z < Ze);
             const T *So = slab + (2 * s) * (RYM * SP);
             const T *Se = slab + (2 * s + 1) * (RYM * SP);
-            T *Icur = Ib + s * (RYM * SP);
-            const T *Iprev = Ib + (1 - s) * (RYM * SP);
             T *He = Hb + RYM * HP;
             T *Ho = Hb;
-            T wzl = T(0), wzr = T(0);
-            if (has_odd) {
-                wzl = w0[2 * (2 * Z - 1)];
-                wzr = w0[2 * (2 * Z - 1) + 1];
-            }
 
             cp_async_wait<1>();
             __syncthreads();
@@ -282,61 +246,8 @@ k_restrict(RestrictParams p)
                 ld4(Se + rb, u);
                 const T uh128 = Se[r * SP + 132];
                 const T uhm2 = Se[r * SP + 2], uhm1 = Se[r * SP + 3];
-                // even plane
-                if constexpr (DEC) {
-                    T I[4], Ih2, Ih1, Ih128;
-                    if (!ro) {
-                        const T sn = shfl_dn(u[0]);  // every lane shuffles, then selects
-                        const T un = (L == 31) ? uh128 : sn;
-                        I[0] = u[0];
-                        I[1] = lerp2(wa1, u[0], wb1, u[2]);
-                        I[2] = u[2];
-                        I[3] = lerp2(wa3, u[2], wb3, un);
-                        Ih2 = uhm2;
-                        Ih1 = lerp2(wah, uhm2, wbh, u[0]);
-                        Ih128 = uh128;
-                        C[0] = T(0);
-                        C[1] = sub_rn(u[1], I[1]);
-                        C[2] = T(0);
-                        C[3] = sub_rn(u[3], I[3]);
-                        chl2 = T(0);
-                        chl1 = sub_rn(uhm1, Ih1);
-                        ch128 = T(0);
-                    } else {
-                        const T wyl = swy[2 * r], wyr = swy[2 * r + 1];
-                        T um[4], up[4];
-                        ld4(Se + rb - SP, um);
-                        ld4(Se + rb + SP, up);
-                        const T umh = Se[(r - 1) * SP + 132], uph = Se[(r + 1) * SP + 132];
-                        const T smn = shfl_dn(um[0]), spn = shfl_dn(up[0]);
-                        const T umn = (L == 31) ? umh : smn;
-                        const T upn = (L == 31) ? uph : spn;
-                        const T xm1 = lerp2(wa1, um[0], wb1, um[2]), xm3 = lerp2(wa3, um[2], wb3, umn);
-                        const T xp1 = lerp2(wa1, up[0], wb1, up[2]), xp3 = lerp2(wa3, up[2], wb3, upn);
-                        I[0] = lerp2(wyl, um[0], wyr, up[0]);
-                        I[1] = lerp2(wyl, xm1, wyr, xp1);
-                        I[2] = lerp2(wyl, um[2], wyr, up[2]);
-                        I[3] = lerp2(wyl, xm3, wyr, xp3);
-                        const T umh2 = Se[(r - 1) * SP + 2], uph2 = Se[(r + 1) * SP + 2];
-                        const T xmh1 = lerp2(wah, umh2, wbh, um[0]), xph1 = lerp2(wah, uph2, wbh, up[0]);
-                        Ih2 = lerp2(wyl, umh2, wyr, uph2);
-                        Ih1 = lerp2(wyl, xmh1, wyr, xph1);
-                        Ih128 = lerp2(wyl, umh, wyr, uph);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) C[k] = sub_rn(u[k], I[k]);
-                        chl2 = sub_rn(uhm2, Ih2);
-                        chl1 = sub_rn(uhm1, Ih1);
-                        ch128 = sub_rn(uh128, Ih128);
-                    }
-                    if constexpr (HZ) {
-                        st4(Icur + rb, I);
-                        if (L == 0) {
-                            Icur[r * SP + 2] = Ih2;
-                            Icur[r * SP + 3] = Ih1;
-                        }
-                        if (L == 31) Icur[r * SP + 132] = Ih128;
-                    }
-                } else {
+                // even plane: coarse nodes (even row, even column) carry no coefficient
+                {
                     C[0] = ro ? u[0] : T(0);
                     C[1] = u[1];
                     C[2] = ro ? u[2] : T(0);
@@ -372,17 +283,7 @@ k_restrict(RestrictParams p)
                 if (has_odd) {
                     T v[4];
                     ld4(So + rb, v);
-                    T ohm2 = So[r * SP + 2], ohm1 = So[r * SP + 3], oh128 = So[r * SP + 132];
-                    if constexpr (DEC) {
-                        T ip[4], ic[4];
-                        ld4(Iprev + rb, ip);
-                        ld4(Icur + rb, ic);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) v[k] = sub_rn(v[k], lerp2(wzl, ip[k], wzr, ic[k]));
-                        ohm2 = sub_rn(ohm2, lerp2(wzl, Iprev[r * SP + 2], wzr, Icur[r * SP + 2]));
-                        ohm1 = sub_rn(ohm1, lerp2(wzl, Iprev[r * SP + 3], wzr, Icur[r * SP + 3]));
-                        oh128 = sub_rn(oh128, lerp2(wzl, Iprev[r * SP + 132], wzr, Icur[r * SP + 132]));
-                    }
+                    const T ohm2 = So[r * SP + 2], ohm1 = So[r * SP + 3], oh128 = So[r * SP + 132];
                     T cl2 = shfl_upw(v[2]), cl3 = shfl_upw(v[3]);
                     const T cr0 = shfl_dn(v[0]);
                     if (L == 0) { cl2 = ohm2; cl3 = ohm1; }
@@ -478,25 +379,18 @@ k_restrict(RestrictParams p)
     }
 }
 
-// One-dimensional grids: one thread per coarse node I.  Only the odd fine
-// nodes 2I-1 and 2I+1 carry coefficients, so F[I] = K[I][1] C(2I-1) +
-// K[I][3] C(2I+1), evaluated in the rounding order of the tiled kernel, and
-// V[I] = A[2I].  The tiled kernel above is not instantiated for 1D.
-template <typename T, typename TW, int MODE>
+// One thread per coarse node I (both directions: the decomposition writes
+// its coefficients before this pass).
+template <typename T, typename TW>
 __global__ void __launch_bounds__(256) k_restrict1d(RestrictParams p)
 {
     const T *__restrict__ A = static_cast<const T *>(p.A);
     TW *__restrict__ F = static_cast<TW *>(p.F);
     TW *__restrict__ V = static_cast<TW *>(p.V);
-    const T *__restrict__ w2 = static_cast<const T *>(p.w2);
     const T *__restrict__ k2 = static_cast<const T *>(p.k2);
     const int64_t n2 = p.n2, m2 = p.m2;
     auto coef = [&](int64_t j) -> T {  // C at the odd fine node j (0 outside the grid)
-        if (j < 1 || j > n2 - 2) return T(0);
-        if constexpr (MODE == MODE_DEC)
-            return sub_rn(A[j], lerp2(w2[2 * j], A[j - 1], w2[2 * j + 1], A[j + 1]));
-        else
-            return A[j];
+        return (j < 1 || j > n2 - 2) ? T(0) : A[j];
     };
     for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < m2;
          I += (int64_t)gridDim.x * blockDim.x) {

@@ -5,12 +5,16 @@ from paper_2007_04457_gb300 import autotune
 def test_model_counts_halo_rows():
     # taller tiles re-read fewer halo rows on a big grid
     big = (513, 513, 513)
-    v = {c: autotune.restriction_model(big, 4, c) for c in autotune.TILE_ROWS}
+    v = {c: autotune.restriction_model(big, 4, c) for c in autotune.CONFIGS}
     assert v[2] < v[0] < v[1]
     assert all(x > 1.0 for x in v.values())
     # on a grid one tile tall the tall tile wastes nothing extra
     small = (17, 17, 17)
     assert autotune.restriction_model(small, 4, 2) <= autotune.restriction_model(small, 4, 1)
+
+
+def test_tile_rows():
+    assert [autotune.tile_rows(c, 3, 4) for c in autotune.CONFIGS] == [8, 4, 16]
 
 
 def test_tiles_absorb_the_last_node():
