@@ -250,7 +250,7 @@ cudaError_t run_solves(const mgard_plan *P, int j, int sign, char *ws, cudaStrea
         sp.vmode = (q == nd - 1) ? (sign > 0 ? 1 : (sign < 0 ? 2 : 0)) : 0;
         sp.src = (q == 0) ? src : nullptr;  // the first sweep may read its right-hand sides elsewhere
         cudaError_t err = timed(P, sp.vmode ? KIND_SOLVE_FUSED : KIND_SOLVE, j, st,
-                                [&] { return launch_solve<TW>(sp, L.svar, st); });
+                                [&] { return launch_solve<TW>(sp, L.svar, P->num_sms, st); });
         if (err != cudaSuccess) return err;
     }
     return cudaSuccess;

@@ -32,10 +32,11 @@ cudaError_t launch_restrict(int act, int mode, int cfg, const RestrictParams &p,
 // shared memory).
 constexpr int kMaxLine = 4096;
 
-// Solves along dimension k of a compact array; nw_req = warps (chunks) per
-// line, 0 = automatic (about 8 nodes per chunk, at most 32 warps).
+// Solves along dimension k of a compact array; nw_req = 0: register-chunk
+// kernel (16 or 32 nodes per warp) for lines up to 576 nodes; nw_req > 0:
+// the shared-memory panel kernel with that many warps (chunks) per line.
 template <typename TW>
-cudaError_t launch_solve(const SolveParams &p, int nw_req, cudaStream_t st);
+cudaError_t launch_solve(const SolveParams &p, int nw_req, int num_sms, cudaStream_t st);
 
 // Element-wise kernels: coefficients of a decomposed level (warp-tile
 // sweep), placement of its final coarse values (one thread per coarse node),

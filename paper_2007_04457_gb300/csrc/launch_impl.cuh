@@ -98,11 +98,41 @@ cudaError_t launch_restrict(int act, int mode, int cfg, const RestrictParams &p,
     return cudaGetLastError();
 }
 
+// k_solve_chunks: 16 nodes per warp and line up to 18 x 16 = 288 nodes, 32
+// up to 576.
 template <typename TW>
-cudaError_t launch_solve(const SolveParams &p_in, int nw_req, cudaStream_t st)
+cudaError_t launch_solve_chunks(const SolveParams &p, int num_sms, cudaStream_t st)
+{
+    const int ch = (p.m <= 16 * kSolveChunkWarps) ? 16 : 32;
+    const int nw = (p.m + ch - 1) / ch;
+    const bool contig = (p.inner == 1);
+    const size_t smem = solve_chunks_elems(p.m, nw, ch, contig) * sizeof(TW);
+    void (*fn)(SolveParams);
+    if (ch == 16) fn = contig ? k_solve_chunks<TW, 16, true> : k_solve_chunks<TW, 16, false>;
+    else fn = contig ? k_solve_chunks<TW, 32, true> : k_solve_chunks<TW, 32, false>;
+    cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int bps = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 32 * nw, smem);
+    if (err != cudaSuccess) return err;
+    const int64_t panels = (p.nlines + 31) / 32;
+    const int64_t grid = std::min<int64_t>(panels, (int64_t)std::max(1, bps) * num_sms);
+    fn<<<(unsigned)grid, dim3(32, nw), smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+// nw_req = 0: k_solve_chunks for lines up to 576 nodes (and shared memory
+// for the contiguous case); otherwise (or nw_req > 0) the shared-memory
+// panel kernel with nw_req warps (0: about 16 nodes per chunk).
+template <typename TW>
+cudaError_t launch_solve(const SolveParams &p_in, int nw_req, int num_sms, cudaStream_t st)
 {
     SolveParams p = p_in;
     if (p.nlines <= 0) return cudaSuccess;
+    if (nw_req == 0 && p.m <= 32 * kSolveChunkWarps && (int64_t)p.m * p.stride < (int64_t(1) << 31) &&
+        solve_chunks_elems(p.m, kSolveChunkWarps, 32, p.inner == 1) * sizeof(TW) <= 200 * 1024)
+        return launch_solve_chunks<TW>(p, num_sms, st);
     int nw = nw_req > 0 ? nw_req : std::min(32, std::max(1, (p.m + 15) / 16));
     nw = std::max(1, std::min(nw, std::min(32, p.m)));
     p.nw = nw;
@@ -267,6 +297,6 @@ cudaError_t launch_small(int mode, const SmallParams &p, size_t smem, cudaStream
     template cudaError_t launch_small<T, TW>(int, const SmallParams &, size_t, cudaStream_t);
 
 #define MG_INSTANTIATE_SOLVE(TW) \
-    template cudaError_t launch_solve<TW>(const SolveParams &, int, cudaStream_t);
+    template cudaError_t launch_solve<TW>(const SolveParams &, int, int, cudaStream_t);
 
 }  // namespace mg

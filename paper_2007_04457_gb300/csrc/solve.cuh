@@ -214,4 +214,188 @@ __global__ void __launch_bounds__(CH > 0 ? 32 * kSolveRegWarps : 1024, 2) k_solv
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// k_solve_chunks: lane = line (a block takes a panel of 32 lines), warp w =
+// nodes [w CH, w CH + CH) of every line, held in registers.  Both sweeps are
+// first-order linear recurrences, so each warp runs its chunk from a zero
+// carry and corrects afterwards:
+//   forward   y_i = y_i^loc + Pf_i c_w,  Pf_i = prod_{k=s..i} (-a_k)
+//   backward  z_i = z_i^loc + Qb_i d_w,  Qb_i = prod_{k=i..e} (-q_k)
+// where the carries c_w (y at the end of the chunk before) and d_w (z at the
+// start of the chunk after) are composed from the other warps' chunk-end
+// values through shared memory.  Pf and Qb depend only on the factors, so
+// they are tabulated once per block.  For a non-contiguous dimension every
+// node index of the panel is a row of 32 adjacent elements, loaded straight
+// into registers; lines along the contiguous dimension form one contiguous
+// block, staged through shared memory with 16-byte copies.
+// ---------------------------------------------------------------------------
+
+// Shared memory of k_solve_chunks, in elements of TW: factors and
+// corrections (5 m), carries (2 x 32 nw), and the staging buffers: CONTIG two
+// panels of 32 lines x m; otherwise two F chunks and one V chunk per thread.
+inline size_t solve_chunks_elems(int m, int nw, int ch, bool contig)
+{
+    const size_t stage = contig ? 2 * (size_t)((32 * m + 3) & ~3) : 3 * (size_t)nw * ch * 32;
+    return 5 * (size_t)m + 2 * 32 * (size_t)nw + stage + 4;
+}
+
+// at most 18 warps (chunks) per block
+constexpr int kSolveChunkWarps = 18;
+
+template <typename TW, int CH, bool CONTIG>
+__global__ void __launch_bounds__(32 * kSolveChunkWarps) k_solve_chunks(SolveParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int m = p.m, nw = blockDim.y;
+    const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane, nthr = 32 * nw;
+    TW *sfac = reinterpret_cast<TW *>(smem_raw);  // a, inv, q per node
+    TW *Pf = sfac + 3 * m;
+    TW *Qb = Pf + m;
+    TW *ca = Qb + m;                              // forward chunk-end values [nw][32]
+    TW *cb = ca + 32 * nw;                        // backward chunk-start values [nw][32]
+    TW *stg = reinterpret_cast<TW *>((reinterpret_cast<uintptr_t>(cb + 32 * nw) + 15) & ~uintptr_t(15));
+    // CONTIG: two panel buffers of tpitch elements; otherwise per thread two
+    // F chunks and a V chunk, element j of thread (w, lane) at (w CH + j) 32 + lane
+    const int tpitch = (32 * m + 3) & ~3;
+    const int cpitch = nw * CH * 32;
+    TW *vst = stg + 2 * cpitch;
+    const TW *fac = static_cast<const TW *>(p.fac);
+    TW *F = static_cast<TW *>(p.F);
+    TW *V = static_cast<TW *>(p.V);
+    const TW *in = p.src ? static_cast<const TW *>(p.src) : F;
+    const int s = w * CH;
+    const int len = max(0, min(CH, m - s));
+    const int64_t inner = p.inner;
+    const int stride = (int)p.stride;  // a line spans m * stride < 2^31 elements (checked by the launcher)
+    const int64_t npanels = (p.nlines + 31) / 32;
+
+    for (int i = tid; i < 3 * m; i += nthr) sfac[i] = fac[i];
+    __syncthreads();
+    if (lane == 0) {
+        TW pr = TW(1);
+        for (int j = 0; j < len; ++j) {
+            pr = -sfac[3 * (s + j)] * pr;
+            Pf[s + j] = pr;
+        }
+        pr = TW(1);
+        for (int j = len - 1; j >= 0; --j) {
+            pr = -sfac[3 * (s + j) + 2] * pr;
+            Qb[s + j] = pr;
+        }
+    }
+
+    auto lines_of = [&](int64_t panel) { return (int)min64(32, p.nlines - panel * 32); };
+    auto base_of = [&](int64_t panel) {
+        const int64_t line = panel * 32 + min(lane, lines_of(panel) - 1);
+        return line / inner * (inner * m) + line % inner;
+    };
+    // asynchronous staging of a panel into buffer b
+    auto stage = [&](int64_t panel, int b) {
+        if (panel >= npanels) return;
+        if constexpr (CONTIG) {
+            // the panel's lines are one contiguous block, 16-byte aligned
+            const TW *src = in + panel * 32 * m;
+            TW *dst = stg + b * tpitch;
+            const int tot = lines_of(panel) * m;
+            constexpr int E = 16 / sizeof(TW);
+            const int nchunk = tot / E;
+            for (int c = tid; c < nchunk; c += nthr) cp_async16(dst + c * E, src + c * E);
+            for (int e = nchunk * E + tid; e < tot; e += nthr) cp_async_elem(dst + e, src + e, true);
+        } else {
+            // each thread copies its own chunk of its own line
+            const bool lv = lane < lines_of(panel);
+            const TW *src = in + base_of(panel) + (int64_t)s * stride;
+            TW *dst = stg + b * cpitch + s * 32 + lane;
+            for (int j = 0; j < len; ++j) cp_async_elem(dst + j * 32, lv ? src + j * stride : in, lv);
+        }
+    };
+
+    int buf = 0;
+    stage(blockIdx.x, 0);
+    cp_async_commit();
+    __syncthreads();  // Pf, Qb ready
+
+    for (int64_t panel = blockIdx.x; panel < npanels; panel += gridDim.x) {
+        const int nl = lines_of(panel);
+        const bool lv = lane < nl;
+        const int64_t base = CONTIG ? 0 : base_of(panel);
+        // V of this panel (fused update), then the next panel, in flight
+        // during the solve as two separate copy groups
+        if (!CONTIG && p.vmode != 0) {
+            const TW *src = V + base + (int64_t)s * stride;
+            TW *dst = vst + s * 32 + lane;
+            for (int j = 0; j < len; ++j) cp_async_elem(dst + j * 32, lv ? src + j * stride : V, lv);
+        }
+        cp_async_commit();
+        stage(panel + gridDim.x, buf ^ 1);
+        cp_async_commit();
+        cp_async_wait<2>();  // this panel's staging is complete
+        if constexpr (CONTIG) __syncthreads();
+        TW y[CH];
+        if constexpr (CONTIG) {
+            const TW *t = stg + buf * tpitch;
+#pragma unroll
+            for (int j = 0; j < CH; ++j) y[j] = (j < len && lv) ? t[lane * m + s + j] : TW(0);
+        } else {
+            const TW *t = stg + buf * cpitch + s * 32 + lane;
+#pragma unroll
+            for (int j = 0; j < CH; ++j) y[j] = (j < len) ? t[j * 32] : TW(0);
+        }
+        // forward sweep
+        TW t = TW(0);
+#pragma unroll
+        for (int j = 0; j < CH; ++j)
+            if (j < len) {
+                t = y[j] - sfac[3 * (s + j)] * t;
+                y[j] = t;
+            }
+        ca[w * 32 + lane] = t;
+        __syncthreads();
+        TW c = TW(0);
+        for (int k = 0; k < w; ++k) c = ca[k * 32 + lane] + Pf[min(k * CH + CH, m) - 1] * c;
+#pragma unroll
+        for (int j = 0; j < CH; ++j)
+            if (j < len) y[j] += Pf[s + j] * c;
+        // backward sweep
+        t = TW(0);
+#pragma unroll
+        for (int j = CH - 1; j >= 0; --j)
+            if (j < len) {
+                t = sfac[3 * (s + j) + 1] * y[j] - sfac[3 * (s + j) + 2] * t;
+                y[j] = t;
+            }
+        cb[w * 32 + lane] = t;
+        __syncthreads();
+        c = TW(0);
+        for (int k = nw - 1; k > w; --k) c = cb[k * 32 + lane] + Qb[k * CH] * c;
+#pragma unroll
+        for (int j = 0; j < CH; ++j)
+            if (j < len) y[j] += Qb[s + j] * c;
+        // result: z into F, or V +- z
+        const TW sg = (p.vmode == 2) ? TW(-1) : TW(1);
+        if constexpr (CONTIG) {
+            TW *t2 = stg + buf * tpitch;
+#pragma unroll
+            for (int j = 0; j < CH; ++j)
+                if (j < len && lv) t2[lane * m + s + j] = y[j];
+            __syncthreads();
+            TW *dst = ((p.vmode == 0) ? F : V) + panel * 32 * m;
+            for (int e = tid; e < nl * m; e += nthr) dst[e] = (p.vmode == 0) ? t2[e] : dst[e] + sg * t2[e];
+        } else {
+            cp_async_wait<1>();  // the V chunk
+            TW *dst = ((p.vmode == 0) ? F : V) + base + (int64_t)s * stride;
+            const TW *vv = vst + s * 32 + lane;
+            if (lv) {
+#pragma unroll
+                for (int j = 0; j < CH; ++j)
+                    if (j < len) dst[j * stride] = (p.vmode == 0) ? y[j] : vv[j * 32] + sg * y[j];
+            }
+        }
+        buf ^= 1;
+        __syncthreads();  // carries and buffers are reused by the next panel
+    }
+    cp_async_wait<0>();
+}
+
 }  // namespace mg
