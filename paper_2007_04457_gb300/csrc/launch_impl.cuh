@@ -130,9 +130,12 @@ cudaError_t launch_solve(const SolveParams &p_in, int nw_req, int num_sms, cudaS
 {
     SolveParams p = p_in;
     if (p.nlines <= 0) return cudaSuccess;
-    if (nw_req == 0 && p.m <= 32 * kSolveChunkWarps && (int64_t)p.m * p.stride < (int64_t(1) << 31) &&
-        solve_chunks_elems(p.m, kSolveChunkWarps, 32, p.inner == 1) * sizeof(TW) <= 200 * 1024)
-        return launch_solve_chunks<TW>(p, num_sms, st);
+    if (nw_req == 0 && p.m <= 32 * kSolveChunkWarps && (int64_t)p.m * p.stride < (int64_t(1) << 31)) {
+        const int ch = (p.m <= 16 * kSolveChunkWarps) ? 16 : 32;
+        const int nw = (p.m + ch - 1) / ch;
+        if (solve_chunks_elems(p.m, nw, ch, p.inner == 1) * sizeof(TW) <= 200 * 1024)
+            return launch_solve_chunks<TW>(p, num_sms, st);
+    }
     int nw = nw_req > 0 ? nw_req : std::min(32, std::max(1, (p.m + 15) / 16));
     nw = std::max(1, std::min(nw, std::min(32, p.m)));
     p.nw = nw;
@@ -175,7 +178,8 @@ inline void node_grid(int64_t nx, int64_t ny, int64_t nz, dim3 *grid, dim3 *bloc
 // per SM twice over, chunks of an even number of fine planes.
 inline int64_t sweep_rows(int act, size_t elem)
 {
-    return (act & 2) ? (elem == 4 ? 16 : 8) : 1;
+    (void)elem;
+    return (act & 2) ? 8 : 1;
 }
 
 inline void sweep_chunks(PlaceParams &p, int act, int64_t R, int num_sms)

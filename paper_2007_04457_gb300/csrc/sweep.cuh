@@ -13,7 +13,7 @@
 // 0, each step an explicitly rounded two-point combination (lerp2), so the
 // coefficients are bit-identical to the C the restriction kernel computed.
 //
-// Work item of one warp: 32 consecutive columns (lane = column) x 16 fine
+// Work item of one warp: 32 consecutive columns (lane = column) x 8 fine
 // rows (1 in 1D) x a chunk of fine planes.  The warp streams the chunk's even planes;
 // for each it forms the dim-2 interpolant X of its even rows (odd columns
 // from the lane's neighbours by shuffles, even columns exact), the dim-1
@@ -30,15 +30,21 @@ namespace mg {
 
 constexpr int kSweepWarps = 4;  // warps per block
 
-// fine rows per warp item (1 for one-dimensional grids; fewer for 8-byte
-// elements, whose register arrays are twice as large)
+// fine rows per warp item (1 for one-dimensional grids): 8 rows keep the
+// registers of 4-byte elements at 80, six blocks (24 warps) per SM
 template <int ACT, int ELEM>
 struct SweepRows {
-    static constexpr int value = (ACT & 2) ? (ELEM == 4 ? 16 : 8) : 1;
+    static constexpr int value = (ACT & 2) ? 8 : 1;
+};
+
+// resident blocks the registers are sized for (8-byte elements need more)
+template <int ELEM>
+struct SweepMinBlocks {
+    static constexpr int value = ELEM == 4 ? 6 : 4;
 };
 
 template <typename T, typename TW, int ACT, int MODE>
-__global__ void __launch_bounds__(32 * kSweepWarps, 4) k_sweep(PlaceParams p)
+__global__ void __launch_bounds__(32 * kSweepWarps, SweepMinBlocks<(int)sizeof(T)>::value) k_sweep(PlaceParams p)
 {
     constexpr bool HZ = (ACT & 4) != 0, HY = (ACT & 2) != 0;
     constexpr bool DEC = (MODE == MODE_DEC);
