@@ -4,6 +4,7 @@
 // k_scatter: after a decomposition level's coefficients are in place
 //   (sweep.cuh), the N_{l-1} nodes receive the final coarse values V (Fig. 3:
 //   each node keeps the value of the coarsest level it belongs to).
+// node_iter serves the one-thread-per-node kernels of adjoint.cuh.
 #pragma once
 
 #include "common.cuh"
@@ -30,20 +31,42 @@ __device__ __forceinline__ NodeIter node_iter()
     return it;
 }
 
+// One warp per row of N_{l-1} nodes (even row of an even plane): the row is
+// read whole and written back whole with V in its even columns, so every
+// written sector is complete (no partial-sector merges in L2).  Per chunk of
+// 128 columns all loads are issued before the stores.
+constexpr int kScatterWarps = 8;
+
 template <typename T, typename TW, int ACT>
-__global__ void __launch_bounds__(kRowThreads) k_scatter(PlaceParams p)
+__global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(PlaceParams p)
 {
     constexpr bool HZ = (ACT & 4) != 0, HY = (ACT & 2) != 0;
-    T *__restrict__ A = static_cast<T *>(p.A);
+    T *A = static_cast<T *>(p.A);
     const TW *__restrict__ V = static_cast<const TW *>(p.V);
-    const NodeIter it = node_iter();
-    const int64_t X = it.x;
-    if (X >= p.m2) return;
-    for (int64_t Z = it.z0; Z < p.m0; Z += it.zstep) {
-        const int64_t z = HZ ? 2 * Z : 0;
-        for (int64_t Y = it.y0; Y < p.m1; Y += it.ystep) {
-            const int64_t y = HY ? 2 * Y : 0;
-            A[(z * p.n1 + y) * p.n2 + 2 * X] = static_cast<T>(V[(Z * p.m1 + Y) * p.m2 + X]);
+    const int L = threadIdx.x & 31;
+    const int64_t rows = p.m0 * p.m1;
+    const int64_t n2 = p.n2;
+    for (int64_t row = (int64_t)blockIdx.x * kScatterWarps + (threadIdx.x >> 5); row < rows;
+         row += (int64_t)gridDim.x * kScatterWarps) {
+        const int64_t Z = row / p.m1, Y = row - (row / p.m1) * p.m1;
+        const int64_t z = HZ ? 2 * Z : 0, y = HY ? 2 * Y : 0;
+        T *arow = A + (z * p.n1 + y) * n2;
+        const TW *vrow = V + row * p.m2;
+        for (int64_t x0 = 0; x0 < n2; x0 += 128) {
+            T a[4];
+            TW v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t x = x0 + 32 * k + L;
+                const bool in = x < n2;
+                a[k] = (in && (x & 1)) ? arow[x] : T(0);
+                v[k] = (in && !(x & 1)) ? vrow[x >> 1] : TW(0);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t x = x0 + 32 * k + L;
+                if (x < n2) arow[x] = (x & 1) ? a[k] : static_cast<T>(v[k]);
+            }
         }
     }
 }

@@ -225,8 +225,9 @@ cudaError_t launch_coef(int act, const PlaceParams &p, int num_sms, cudaStream_t
 template <typename T, typename TW>
 cudaError_t launch_scatter(int act, const PlaceParams &p, cudaStream_t st)
 {
-    dim3 g, b;
-    detail::node_grid(p.m2, p.m1, p.m0, &g, &b);
+    const int64_t rows = p.m0 * p.m1;
+    const int64_t blocks = std::min<int64_t>((rows + kScatterWarps - 1) / kScatterWarps, 1 << 20);
+    const dim3 g((unsigned)blocks), b(32 * kScatterWarps);
     switch (act) {
     case ACT_1D: k_scatter<T, TW, ACT_1D><<<g, b, 0, st>>>(p); break;
     case ACT_2D: k_scatter<T, TW, ACT_2D><<<g, b, 0, st>>>(p); break;
