@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 SHAPE = (513, 513, 513)
 N_MODES = 12
 SEED = 2
-KIND_NAMES = {0: "restrict_dec", 1: "restrict_rec", 2: "solve", 3: "solve_fused", 8: "small",
+KIND_NAMES = {0: "restrict_dec", 1: "restrict_rec", 2: "solve", 3: "solve_fused", 8: "small", 9: "multi",
               4: "coef", 5: "interp", 6: "scatter"}
 
 
@@ -284,6 +284,38 @@ def run_batched(torch, mgard, synth, dev, stream, rank):
             "tuned": {"x".join(map(str, k)): [v["cfg"], v["warps"]] for k, v in tuned.items()}}
 
 
+def run_adjoint(torch, mgard, synth, dev, stream, rank):
+    """257^3 FP32, loss ||recompose(mask * decompose(u)) - u||^2 with a fixed
+    10% keep-mask on the finest coefficients: forward + backward through the
+    hand-written adjoint kernels (torch.autograd), against twice the plain
+    decompose + recompose of the same field."""
+    import numpy as np
+
+    from paper_2007_04457_gb300 import autograd as ag
+
+    shape = (257, 257, 257)
+    plan = mgard.Plan(shape, dtype="f32")
+    u0 = synth.sinusoid_field_torch(shape, 12, 5 + rank, dev, torch.float32)
+    mask = torch.from_numpy(synth.keep_mask(shape, seed=5).astype(np.float32)).to(dev)
+    ws = plan.workspace(dev)
+
+    def fwd_bwd():
+        u = u0.detach().requires_grad_(True)
+        loss = ag.masked_reconstruction_loss(u, plan, mask)
+        loss.backward()
+
+    plain = lambda: (plan.decompose(u0, ws, stream), plan.recompose(u0, ws, stream))
+    for _ in range(3):
+        fwd_bwd()
+        plain()
+    ms = _timed(torch, stream, fwd_bwd, 5)
+    ms_plain = _timed(torch, stream, plain, 5)
+    out = {"ms_per_step": ms, "plain_dec_rec_ms": ms_plain, "ratio_vs_2x_plain": ms / (2 * ms_plain),
+           "workload": "257^3 FP32 masked reconstruction loss, forward + backward (adjoint kernels)"}
+    plan.close()
+    return out
+
+
 def run_mixed(torch, mgard, synth, dev, stream, rank, max_over_ranks):
     """1025 x 1025 x 513 FP32 field (12 modes + Gaussian blob), FP64 solves and
     coarse-level accumulation, 9 levels."""
@@ -315,6 +347,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -451,8 +484,34 @@ def main():
                "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes,
                "ms_per_step": mse / ke, "steps": ke}
 
+    # decomposition and recomposition timed separately (paper-style metric:
+    # input bytes per second; the paper's pass model puts the attainable
+    # rate at the measured single-pass bandwidth / 8.43 for 3D)
+    ed0 = torch.cuda.Event(enable_timing=True)
+    ed1 = torch.cuda.Event(enable_timing=True)
+    t_dec = t_rec = 0.0
+    for _ in range(5):
+        ed0.record(stream)
+        plan.decompose(u, ws, stream)
+        ed1.record(stream)
+        torch.cuda.synchronize()
+        t_dec += ed0.elapsed_time(ed1)
+        ed0.record(stream)
+        plan.recompose(u, ws, stream)
+        ed1.record(stream)
+        torch.cuda.synchronize()
+        t_rec += ed0.elapsed_time(ed1)
+    t_dec, t_rec = max_over_ranks(t_dec / 5), max_over_ranks(t_rec / 5)
+    in_bytes = int(np.prod(SHAPE)) * S
+    paper_metric = {"decompose_input_gbs": in_bytes / (t_dec / 1e3) / 1e9,
+                    "recompose_input_gbs": in_bytes / (t_rec / 1e3) / 1e9,
+                    "decompose_ms": t_dec, "recompose_ms": t_rec,
+                    "pass_model_peak_gbs": peak / 8.43,
+                    "decompose_frac_of_pass_model": in_bytes / (t_dec / 1e3) / 1e9 / (peak / 8.43)}
+
     batched = None if args.no_batch else run_batched(torch, mgard, synth, dev, stream, rank)
     mixed = None if args.no_mixed else run_mixed(torch, mgard, synth, dev, stream, rank, max_over_ranks)
+    adjoint = None if args.no_adjoint else run_adjoint(torch, mgard, synth, dev, stream, rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -475,6 +534,8 @@ def main():
             "fp64": fp64,
             "mixed": mixed,
             "batched": batched,
+            "adjoint": adjoint,
+            "paper_metric": paper_metric,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),

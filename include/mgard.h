@@ -118,11 +118,18 @@ MGARD_API mgard_status mgard_recompose(const mgard_plan *plan, void *d_data, voi
  *   param 1  warps (chunks) per line in the correction solves, 1..32, or
  *            0 = automatic (about 16 nodes per chunk)
  *   param 2  coarse planes per restriction work item (0 = automatic)
- *   param 3  plan-wide (any valid level): 0 = run the coarse levels whose
- *            array fits in one block's shared memory (at most 227 KB, sides
- *            <= 257) in a single launch per direction (default); 1 = run
- *            every level with the tiled per-level kernels.  The two differ
- *            only in floating-point rounding order.
+ *   param 3  plan-wide (any valid level): 0 = run the coarse end of the
+ *            hierarchy in a single launch per direction (default); 1 = run
+ *            every level with the tiled per-level kernels.
+ *   param 4  plan-wide: 0 = the single launch is the cooperative kernel when
+ *            the plan has one (every level from the first whose sides are
+ *            <= 129 nodes, the grid running each level and one block the
+ *            last few in shared memory), else the single-block kernel (the
+ *            levels whose array fits one block's shared memory, at most
+ *            227 KB, sides <= 257); 1 = always the single-block kernel.
+ *   The forms of params 3 and 4 differ only in floating-point rounding order.
+ *   mgard_plan_get_tune also reports param 5: the first level the
+ *   cooperative kernel runs (-1: none).
  * Returns MGARD_ERR_INVALID_ARG for an unknown parameter or value. */
 MGARD_API mgard_status mgard_plan_tune(mgard_plan *plan, int level, int param, int value);
 

@@ -83,6 +83,16 @@ struct mgard_plan {
     int small_auto = 0;    // the finest level whose array fits the kernel
     size_t small_smem = 0;
     int small_hcap = 0;
+    // levels coop_j .. L-1 in one cooperative launch (coop_j = L: none):
+    // coop_j .. coop_s-1 by the whole grid, coop_s .. L-1 by block 0 in
+    // shared memory; coop_auto is the plan's choice, coop_off a tune switch
+    int coop_j = 0, coop_auto = 0, coop_s = 0;
+    bool coop_off = false;
+    int coop_grid = 0;
+    size_t coop_smem = 0;
+    int coop_hcap = 0;
+    size_t coop_bar_off = 0;
+    std::vector<size_t> coop_g_off;   // per grid level: G (n0 x m1 x m2)
     // kernel timing (measurement support): event pairs around the launches of
     // the prof_levels finest levels
     struct ProfRec {
@@ -174,7 +184,8 @@ const double *tab_ptr<double>(const mgard_plan *P, int64_t off) { return P->tab6
 int act_of(int ndim) { return ndim == 1 ? ACT_1D : (ndim == 2 ? ACT_2D : ACT_3D); }
 
 enum { KIND_RESTRICT_DEC = 0, KIND_RESTRICT_REC = 1, KIND_SOLVE = 2, KIND_SOLVE_FUSED = 3,
-       KIND_PLACE = 4, KIND_INTERP = 5, KIND_PLACE_EVEN = 6, KIND_ADJ = 7, KIND_SMALL = 8 };
+       KIND_PLACE = 4, KIND_INTERP = 5, KIND_PLACE_EVEN = 6, KIND_ADJ = 7, KIND_SMALL = 8,
+       KIND_MULTI = 9 };
 
 cudaEvent_t prof_event(const mgard_plan *P)
 {
@@ -315,18 +326,68 @@ cudaError_t run_small(const mgard_plan *P, int mode, void *A, cudaStream_t st)
     return timed(P, KIND_SMALL, j0, st, [&] { return launch_small<T, TW>(mode, sp, P->small_smem, st); });
 }
 
+// Levels coop_j .. L-1 in one cooperative launch (multi.cuh); level coop_j
+// works on the user array (type TX) when coop_j = 0.
+template <typename TX, typename TW>
+cudaError_t run_multi(const mgard_plan *P, int mode, void *data, char *ws, cudaStream_t st)
+{
+    const int j0 = P->coop_j;
+    MultiParams mp;
+    mp.nd = P->coop_s - j0;
+    for (int i = 0; i < mp.nd; ++i) {
+        const int j = j0 + i;
+        const mgard_level &L = P->lv[j];
+        MultiLevel &ml = mp.lv[i];
+        ml.X = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
+        ml.V = ws + L.v_off;
+        ml.F = ws + L.f_off;
+        ml.G = ws + P->coop_g_off[i];
+        for (int d = 0; d < 3; ++d) {
+            ml.n[d] = (int)L.n[d];
+            ml.m[d] = (int)L.m[d];
+            ml.w[d] = tab_ptr<TW>(P, L.w_off[d]);
+            ml.k[d] = tab_ptr<TW>(P, L.k_off[d]);
+            ml.fac[d] = tab_ptr<TW>(P, L.t_off[d]);
+        }
+    }
+    mp.small = P->coop_s < P->L ? 1 : 0;
+    if (mp.small) {
+        const int s0 = P->coop_s;
+        SmallParams &sp = mp.sp;
+        sp.A = ws + P->lv[s0 - 1].v_off;
+        for (int d = 0; d < 3; ++d) sp.n[d] = (int)P->lv[s0 - 1].m[d];
+        sp.nlev = P->L - s0;
+        sp.hcap = P->coop_hcap;
+        for (int i = 0; i < sp.nlev; ++i) {
+            const mgard_level &L = P->lv[s0 + i];
+            for (int d = 0; d < 3; ++d) {
+                sp.w[i][d] = tab_ptr<TW>(P, L.w_off[d]);
+                sp.k[i][d] = tab_ptr<TW>(P, L.k_off[d]);
+                sp.fac[i][d] = tab_ptr<TW>(P, L.t_off[d]);
+            }
+        }
+    }
+    mp.bar = reinterpret_cast<unsigned *>(ws + P->coop_bar_off);
+    mp.spin_limit = kMultiSpinLimit;
+    cudaError_t err = cudaMemsetAsync(mp.bar, 0, kMultiBarrierWords * sizeof(unsigned), st);
+    if (err != cudaSuccess) return err;
+    return timed(P, KIND_MULTI, j0, st, [&] { return launch_multi<TX, TW>(mode, mp, P->coop_grid, P->coop_smem, st); });
+}
+
 // Decomposition, levels L..1 (Section II-A): level j = 0 works on the user
 // array (element type TU), deeper levels on the compact coarse arrays V_{j-1}
 // of the workspace (type TW).  Per level: the coefficients go in place (they
 // depend only on the level's own values), the restriction reads them and
 // gathers the coarse nodes into V_j, and the solves add the correction to
-// V_j.  The levels from small_j on run in one block; then, coarsest first,
-// every level array receives the final values of its coarse nodes.
+// V_j.  The coarse levels run in one cooperative launch (from coop_j) or one
+// block (from small_j); then, coarsest first, every level array receives the
+// final values of its coarse nodes.
 template <typename TU, typename TW>
-mgard_status exec_decompose(const mgard_plan *P, void *data, char *ws, cudaStream_t st)
+mgard_status exec_decompose(const mgard_plan *P, void *data, char *ws, cudaStream_t st, bool allow_coop)
 {
     cudaError_t err;
-    const int J = P->small_j;
+    const bool coop = allow_coop && P->coop_j < P->L;
+    const int J = coop ? P->coop_j : P->small_j;
     for (int j = 0; j < J; ++j) {
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
         err = (j == 0) ? run_coef_level<TU, TW>(P, j, A, ws, st) : run_coef_level<TW, TW>(P, j, A, ws, st);
@@ -337,7 +398,10 @@ mgard_status exec_decompose(const mgard_plan *P, void *data, char *ws, cudaStrea
         err = run_solves<TW>(P, j, +1, ws, st);
         if (err != cudaSuccess) return cuda_fail(err, "decompose: correction solve kernel");
     }
-    if (J < P->L) {
+    if (coop) {
+        err = (J == 0) ? run_multi<TU, TW>(P, MODE_DEC, data, ws, st) : run_multi<TW, TW>(P, MODE_DEC, data, ws, st);
+        if (err != cudaSuccess) return cuda_fail(err, "decompose: cooperative coarse-level kernel");
+    } else if (J < P->L) {
         void *A = (J == 0) ? data : (void *)(ws + P->lv[J - 1].v_off);
         err = (J == 0) ? run_small<TU, TW>(P, MODE_DEC, A, st) : run_small<TW, TW>(P, MODE_DEC, A, st);
         if (err != cudaSuccess) return cuda_fail(err, "decompose: single-block coarse-level kernel");
@@ -354,17 +418,21 @@ mgard_status exec_decompose(const mgard_plan *P, void *data, char *ws, cudaStrea
 // gathered coarse array V_j (both depend only on stored coefficients), then
 // coarsest first: correction solve with V_j -= z, then interpolation.
 template <typename TU, typename TW>
-mgard_status exec_recompose(const mgard_plan *P, void *data, char *ws, cudaStream_t st)
+mgard_status exec_recompose(const mgard_plan *P, void *data, char *ws, cudaStream_t st, bool allow_coop)
 {
     cudaError_t err;
-    const int J = P->small_j;
+    const bool coop = allow_coop && P->coop_j < P->L;
+    const int J = coop ? P->coop_j : P->small_j;
     for (int j = 0; j < J; ++j) {
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
         err = (j == 0) ? run_restrict_level<TU, TW>(P, j, MODE_REC, A, ws, st)
                        : run_restrict_level<TW, TW>(P, j, MODE_REC, A, ws, st);
         if (err != cudaSuccess) return cuda_fail(err, "recompose: load-vector kernel");
     }
-    if (J < P->L) {
+    if (coop) {
+        err = (J == 0) ? run_multi<TU, TW>(P, MODE_REC, data, ws, st) : run_multi<TW, TW>(P, MODE_REC, data, ws, st);
+        if (err != cudaSuccess) return cuda_fail(err, "recompose: cooperative coarse-level kernel");
+    } else if (J < P->L) {
         void *A = (J == 0) ? data : (void *)(ws + P->lv[J - 1].v_off);
         err = (J == 0) ? run_small<TU, TW>(P, MODE_REC, A, st) : run_small<TW, TW>(P, MODE_REC, A, st);
         if (err != cudaSuccess) return cuda_fail(err, "recompose: single-block coarse-level kernel");
@@ -690,7 +758,7 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
     for (int j = 0; j < L; ++j) {
         const int64_t *nj = (j == 0) ? P->n : P->lv[j - 1].m;
         const int64_t es = (int64_t)P->elem_ws;
-        const int64_t base = small_elems(nj), hp = small_hplane(nj);
+        const int64_t base = small_elems(nj) + small_tab_elems(nj, L - j), hp = small_hplane(nj);
         const bool sides_ok = nj[0] <= kSmallMaxSide && nj[1] <= kSmallMaxSide && nj[2] <= kSmallMaxSide;
         if (sides_ok && (base + hp) * es <= kSmallMaxBytes && L - j <= kSmallMaxLevels) {
             // H: as many first-level fine planes as fit, at most all of them
@@ -703,9 +771,95 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
     }
     P->small_j = P->small_auto;
 
+    // the cooperative kernel: from the first level whose coarse lines fit one
+    // thread's registers, the grid runs every level until the array is small
+    // enough for block 0 to finish in shared memory (H: all fine planes)
+    P->coop_auto = L;
+    for (int j = 0; j < L; ++j) {
+        const int64_t *nj = (j == 0) ? P->n : P->lv[j - 1].m;
+        if (nj[0] <= kMultiMaxSide && nj[1] <= kMultiMaxSide && nj[2] <= kMultiMaxSide) {
+            P->coop_auto = j;
+            break;
+        }
+    }
+    if (P->coop_auto < L) {
+        const int j0 = P->coop_auto;
+        const int64_t es = (int64_t)P->elem_ws;
+        int s = j0;
+        int64_t sbytes = 0;
+        for (; s < L; ++s) {
+            const int64_t *ns = (s == 0) ? P->n : P->lv[s - 1].m;
+            sbytes = (small_elems(ns) + ns[0] * small_hplane(ns) + small_tab_elems(ns, L - s)) * es;
+            if (count(ns) <= kMultiSmallNodes && sbytes <= kMultiSmallBytes) break;
+        }
+        // shared memory of a block: the largest grid level's planes, or the
+        // levels block 0 finishes
+        int64_t smem = (s < L) ? sbytes : 0;
+        for (int j = j0; j < s; ++j)
+            smem = std::max(smem, (kMultiTabElems + multi_level_elems(P->lv[j].n, P->lv[j].m)) * es);
+        if (P->ndim >= 2 && s > j0 && s - j0 <= kMultiMaxLevels && L - s <= kSmallMaxLevels &&
+            smem <= kSmallMaxBytes) {
+            P->coop_s = s;
+            P->coop_smem = (size_t)smem;
+            if (s < L) {
+                const int64_t *ns = P->lv[s - 1].m;
+                P->coop_hcap = (int)(ns[0] * small_hplane(ns));
+            }
+            // per grid level the load vector reduced along dims 2 and 1, then
+            // the barrier words
+            for (int j = j0; j < s; ++j) {
+                const mgard_level &lv = P->lv[j];
+                P->coop_g_off.push_back(ws);
+                ws = align_up(ws + (size_t)(lv.n[0] * lv.m[1] * lv.m[2]) * P->elem_ws);
+            }
+            P->coop_bar_off = ws;
+            ws = align_up(ws + kMultiBarrierWords * sizeof(unsigned));
+            P->ws_bytes = ws;
+        } else {
+            P->coop_auto = L;
+        }
+    }
+    P->coop_j = P->coop_auto;
+
     *tab_out = std::move(tab);
     *out = P;
     return MGARD_OK;
+}
+
+// Grid of the cooperative kernel: every block resident (both directions), or
+// no cooperative kernel when the device cannot hold one block per SM.
+template <typename TX, typename TW>
+static cudaError_t coop_occupancy(const mgard_plan *P, int *bps)
+{
+    int a = 0, b = 0;
+    cudaError_t err = multi_occupancy<TX, TW>(MODE_DEC, P->coop_smem, &a);
+    if (err == cudaSuccess) err = multi_occupancy<TX, TW>(MODE_REC, P->coop_smem, &b);
+    *bps = std::min(a, b);
+    return err;
+}
+
+static cudaError_t configure_coop(mgard_plan *P)
+{
+    if (P->coop_auto >= P->L) return cudaSuccess;
+    int coop_ok = 0;
+    cudaError_t err = cudaDeviceGetAttribute(&coop_ok, cudaDevAttrCooperativeLaunch, P->device);
+    if (err != cudaSuccess) return err;
+    int bps = 0;
+    if (coop_ok) {
+        const bool user = P->coop_auto == 0;
+        switch (P->dtype) {
+        case MGARD_F32: err = coop_occupancy<float, float>(P, &bps); break;
+        case MGARD_F64: err = coop_occupancy<double, double>(P, &bps); break;
+        default: err = user ? coop_occupancy<float, double>(P, &bps) : coop_occupancy<double, double>(P, &bps); break;
+        }
+        if (err != cudaSuccess) return err;
+    }
+    if (bps < 1) {
+        P->coop_auto = P->coop_j = P->L;
+        return cudaSuccess;
+    }
+    P->coop_grid = bps * P->num_sms;
+    return cudaSuccess;
 }
 
 // Launch configuration of every level (needs the device, allocates nothing).
@@ -720,6 +874,7 @@ static cudaError_t configure_plan(mgard_plan *P)
         default: err = configure_level<float, double>(P, lv, j == 0); break;
         }
     }
+    if (err == cudaSuccess) err = configure_coop(P);
     return err;
 }
 
@@ -821,6 +976,7 @@ int mgard_plan_launches(const mgard_plan *P, int recompose)
     // per level: one restriction + ndim solve sweeps + the element-wise
     // kernel(s): interpolation (recompose) or coefficients + coarse placement
     const int tail = recompose ? 1 : 2;
+    if (P->coop_j < P->L) return P->coop_j * (1 + P->ndim + tail) + 1;
     return P->small_j * (1 + P->ndim + tail) + (P->small_j < P->L ? 1 : 0);
 }
 
@@ -852,32 +1008,39 @@ mgard_status mg_decompose_with(const mgard_plan *P, void *d_data, void *d_ws, si
     return mgard_decompose(P, d_data, d_ws, ws_bytes, st);
 }
 
+// Decomposition (dir 0) or recomposition (dir 1); allow_coop = false keeps
+// the cooperative kernel out (batches run fields concurrently on several
+// streams, and a cooperative launch holds every SM).
+mgard_status mg_transform(const mgard_plan *P, int dir, void *d_data, void *d_ws, size_t ws_bytes, cudaStream_t st,
+                          bool allow_coop)
+{
+    mgard_status s = check_call(P, d_data, d_ws, ws_bytes);
+    if (s != MGARD_OK) return s;
+    char *ws = static_cast<char *>(d_ws);
+    if (dir == 0) {
+        switch (P->dtype) {
+        case MGARD_F32: return exec_decompose<float, float>(P, d_data, ws, st, allow_coop);
+        case MGARD_F64: return exec_decompose<double, double>(P, d_data, ws, st, allow_coop);
+        default: return exec_decompose<float, double>(P, d_data, ws, st, allow_coop);
+        }
+    }
+    switch (P->dtype) {
+    case MGARD_F32: return exec_recompose<float, float>(P, d_data, ws, st, allow_coop);
+    case MGARD_F64: return exec_recompose<double, double>(P, d_data, ws, st, allow_coop);
+    default: return exec_recompose<float, double>(P, d_data, ws, st, allow_coop);
+    }
+}
+
 extern "C" {
 
 mgard_status mgard_decompose(const mgard_plan *P, void *d_data, void *d_ws, size_t ws_bytes, void *stream)
 {
-    mgard_status s = check_call(P, d_data, d_ws, ws_bytes);
-    if (s != MGARD_OK) return s;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    char *ws = static_cast<char *>(d_ws);
-    switch (P->dtype) {
-    case MGARD_F32: return exec_decompose<float, float>(P, d_data, ws, st);
-    case MGARD_F64: return exec_decompose<double, double>(P, d_data, ws, st);
-    default: return exec_decompose<float, double>(P, d_data, ws, st);
-    }
+    return mg_transform(P, 0, d_data, d_ws, ws_bytes, static_cast<cudaStream_t>(stream), true);
 }
 
 mgard_status mgard_recompose(const mgard_plan *P, void *d_data, void *d_ws, size_t ws_bytes, void *stream)
 {
-    mgard_status s = check_call(P, d_data, d_ws, ws_bytes);
-    if (s != MGARD_OK) return s;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    char *ws = static_cast<char *>(d_ws);
-    switch (P->dtype) {
-    case MGARD_F32: return exec_recompose<float, float>(P, d_data, ws, st);
-    case MGARD_F64: return exec_recompose<double, double>(P, d_data, ws, st);
-    default: return exec_recompose<float, double>(P, d_data, ws, st);
-    }
+    return mg_transform(P, 1, d_data, d_ws, ws_bytes, static_cast<cudaStream_t>(stream), true);
 }
 
 mgard_status mgard_decompose_adjoint(const mgard_plan *P, void *d_data, void *d_ws, size_t ws_bytes, void *stream)
@@ -937,6 +1100,12 @@ mgard_status mgard_plan_tune(mgard_plan *P, int level, int param, int value)
     case 3:
         if (value != 0 && value != 1) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: single-block switch");
         P->small_j = value ? P->L : P->small_auto;
+        P->coop_j = (value || P->coop_off) ? P->L : P->coop_auto;
+        return MGARD_OK;
+    case 4:
+        if (value != 0 && value != 1) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: cooperative switch");
+        P->coop_off = value != 0;
+        P->coop_j = (P->coop_off || P->small_j == P->L) ? P->L : P->coop_auto;
         return MGARD_OK;
     default: return fail(MGARD_ERR_INVALID_ARG, "plan_tune: unknown parameter");
     }
@@ -958,6 +1127,8 @@ int mgard_plan_get_tune(const mgard_plan *P, int level, int param)
     case 1: return L.svar;
     case 2: return L.zchunk;
     case 3: return P->small_j == P->L ? 1 : 0;
+    case 4: return P->coop_off ? 1 : 0;
+    case 5: return P->coop_j < P->L ? P->coop_j : -1;
     default: return -1;
     }
 }

@@ -18,6 +18,8 @@
 
 mgard_status mg_fail(mgard_status st, const std::string &msg);
 mgard_status mg_cuda_fail(cudaError_t err, const char *what);
+mgard_status mg_transform(const mgard_plan *P, int dir, void *d_data, void *d_ws, size_t ws_bytes, cudaStream_t st,
+                          bool allow_coop);
 
 namespace {
 
@@ -141,8 +143,9 @@ static mgard_status batch_run(mgard_batch *B, int dir, void *const *d_data, void
             char *ws = static_cast<char *>(d_ws) + B->offsets[i];
             const size_t wsb = mgard_workspace_bytes(B->plans[i]);
             cudaStream_t fs = B->streams[B->stream_of[i]];
-            status = dir == 0 ? mgard_decompose(B->plans[i], d_data[i], ws, wsb, fs)
-                              : mgard_recompose(B->plans[i], d_data[i], ws, wsb, fs);
+            // per-field kernels only: a cooperative launch would hold every
+            // SM and serialize the fields
+            status = mg_transform(B->plans[i], dir, d_data[i], ws, wsb, fs, false);
         }
         for (int s = 1; s < ns; ++s) {
             cudaEventRecord(B->events[s], B->streams[s]);

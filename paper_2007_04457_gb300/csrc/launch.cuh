@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "params.h"
+#include "multi_params.h"
 #include "small_params.h"
 
 namespace mg {
@@ -54,6 +55,15 @@ cudaError_t launch_interp(int act, const PlaceParams &p, int num_sms, cudaStream
 // small_elems(n) * sizeof(TW) bytes of dynamic shared memory.
 template <typename T, typename TW>
 cudaError_t launch_small(int mode, const SmallParams &p, size_t smem, cudaStream_t st);
+
+// The coarse levels in one cooperative launch (multi.cuh): blocks of the
+// kernel resident per SM with `smem` bytes of dynamic shared memory, and the
+// launch itself (grid <= that count x the SM count).
+template <typename TX, typename TW>
+cudaError_t multi_occupancy(int mode, size_t smem, int *blocks_per_sm);
+
+template <typename TX, typename TW>
+cudaError_t launch_multi(int mode, const MultiParams &p, int grid, size_t smem, cudaStream_t st);
 
 // Transposed level maps (adjoint.cuh).
 template <typename T, typename TW>

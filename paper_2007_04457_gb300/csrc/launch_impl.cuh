@@ -7,6 +7,7 @@
 #include "adjoint.cuh"
 #include "interp.cuh"
 #include "launch.cuh"
+#include "multi.cuh"
 #include "restrict.cuh"
 #include "small.cuh"
 #include "sweep.cuh"
@@ -289,6 +290,37 @@ cudaError_t launch_small(int mode, const SmallParams &p, size_t smem, cudaStream
     return cudaGetLastError();
 }
 
+template <typename TX, typename TW>
+cudaError_t multi_occupancy(int mode, size_t smem, int *blocks_per_sm)
+{
+    void (*fn)(MultiParams) = (mode == MODE_DEC) ? k_multi<TX, TW, MODE_DEC> : k_multi<TX, TW, MODE_REC>;
+    cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kMultiThreads, smem);
+}
+
+template <typename TX, typename TW>
+cudaError_t launch_multi(int mode, const MultiParams &p, int grid, size_t smem, cudaStream_t st)
+{
+    void (*fn)(MultiParams) = (mode == MODE_DEC) ? k_multi<TX, TW, MODE_DEC> : k_multi<TX, TW, MODE_REC>;
+    // the limit is per function: plans with other shapes may have lowered it
+    cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kMultiThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, p);
+}
+
 #define MG_INSTANTIATE_LEVEL(T, TW)                                                              \
     template cudaError_t restrict_shape<T, TW>(int, int, int, RestrictShape *);                  \
     template cudaError_t launch_restrict<T, TW>(int, int, int, const RestrictParams &, int,     \
@@ -299,7 +331,9 @@ cudaError_t launch_small(int mode, const SmallParams &p, size_t smem, cudaStream
     template cudaError_t launch_gather<T, TW>(int, const PlaceParams &, cudaStream_t);         \
     template cudaError_t launch_adj_odd<T, TW>(int, const AdjParams &, cudaStream_t);          \
     template cudaError_t launch_adj_even<T, TW>(int, const AdjParams &, cudaStream_t);          \
-    template cudaError_t launch_small<T, TW>(int, const SmallParams &, size_t, cudaStream_t);
+    template cudaError_t launch_small<T, TW>(int, const SmallParams &, size_t, cudaStream_t);    \
+    template cudaError_t multi_occupancy<T, TW>(int, size_t, int *);                             \
+    template cudaError_t launch_multi<T, TW>(int, const MultiParams &, int, size_t, cudaStream_t);
 
 #define MG_INSTANTIATE_SOLVE(TW) \
     template cudaError_t launch_solve<TW>(const SolveParams &, int, int, cudaStream_t);

@@ -17,8 +17,9 @@
 // whole transform.  Arithmetic is in TW; the global array has type T.
 //
 // Shared memory (elements of TW): the array U, then G (dims 1 and 2 reduced,
-// all fine planes of the first level), F (the first level's coarse grid) and
-// H (dim 2 reduced, a chunk of fine planes at a time; hcap elements).
+// all fine planes of the first level), F (the first level's coarse grid), H
+// (dim 2 reduced, a chunk of fine planes at a time; hcap elements) and the
+// tables of every level.
 #pragma once
 
 #include "common.cuh"
@@ -150,6 +151,49 @@ __device__ void small_load_vector(const TW *U, TW *G, TW *F, TW *H, int hcap, co
     __syncthreads();
 }
 
+// M z = f along one line of m nodes at stride s in shared memory, in place
+// (forward elimination with the multipliers a_i, back substitution with
+// 1/pivot and the scaled super-diagonal), a few nodes at a time so that the
+// loads of a group are in flight together.
+template <typename TW>
+__device__ __forceinline__ void line_solve_smem(TW *f, int s, int m, const TW *fac)
+{
+    constexpr int K = sizeof(TW) == 4 ? 8 : 4;
+    TW t = TW(0);
+    for (int b = 0; b < m; b += K) {
+        TW y[K], a[K];
+#pragma unroll
+        for (int u = 0; u < K; ++u)
+            if (b + u < m) {
+                y[u] = f[(b + u) * s];
+                a[u] = fac[3 * (b + u)];
+            }
+#pragma unroll
+        for (int u = 0; u < K; ++u)
+            if (b + u < m) {
+                t = y[u] - a[u] * t;
+                f[(b + u) * s] = t;
+            }
+    }
+    t = TW(0);
+    for (int b = m - 1; b >= 0; b -= K) {
+        TW y[K], iv[K], q[K];
+#pragma unroll
+        for (int u = 0; u < K; ++u)
+            if (b - u >= 0) {
+                y[u] = f[(b - u) * s];
+                iv[u] = fac[3 * (b - u) + 1];
+                q[u] = fac[3 * (b - u) + 2];
+            }
+#pragma unroll
+        for (int u = 0; u < K; ++u)
+            if (b - u >= 0) {
+                t = iv[u] * y[u] - q[u] * t;
+                f[(b - u) * s] = t;
+            }
+    }
+}
+
 // M_{l-1} z = F along every active dimension, in place, one thread per line.
 template <typename TW>
 __device__ void small_solves(TW *F, const SmallLevel<TW> &L)
@@ -162,28 +206,17 @@ __device__ void small_solves(TW *F, const SmallLevel<TW> &L)
         const int inner = (k == 2) ? 1 : (k == 1 ? nc[2] : nc[1] * nc[2]);
         const int nlines = nc[0] * nc[1] * nc[2] / m;
         const TW *fac = L.fac[k];
-        for (int line = tid; line < nlines; line += nt) {
-            TW *f = F + (line / inner) * (inner * m) + line % inner;
-            TW y = f[0];
-            for (int i = 1; i < m; ++i) {
-                y = f[i * inner] - fac[3 * i] * y;
-                f[i * inner] = y;
-            }
-            TW z = fac[3 * (m - 1) + 1] * y;
-            f[(m - 1) * inner] = z;
-            for (int i = m - 2; i >= 0; --i) {
-                z = fac[3 * i + 1] * f[i * inner] - fac[3 * i + 2] * z;
-                f[i * inner] = z;
-            }
-        }
+        for (int line = tid; line < nlines; line += nt)
+            line_solve_smem<TW>(F + (line / inner) * (inner * m) + line % inner, inner, m, fac);
         __syncthreads();
     }
 }
 
+// Every level of the array p.A in shared memory `smem` (small_elems + hcap
+// + small_tab_elems elements of TW), by the calling block.
 template <typename T, typename TW, int MODE>
-__global__ void __launch_bounds__(kSmallThreads, 1) k_small(SmallParams p)
+__device__ void small_run(const SmallParams &p, unsigned char *smem_raw)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     TW *U = reinterpret_cast<TW *>(smem_raw);
     const int n0 = p.n[0], n1 = p.n[1], n2 = p.n[2];
     const int N = n0 * n1 * n2;
@@ -193,11 +226,44 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(SmallParams p)
     TW *G = U + N;
     TW *F = G + n0 * m1 * m2;
     TW *H = F + m0 * m1 * m2;
+    TW *Tb = H + p.hcap;  // the tables of every level
     T *A = static_cast<T *>(p.A);
     const int tid = threadIdx.x, nt = blockDim.x;
 
+    // every level's tables (per active dim 2 nf weights, 5 nc stencil
+    // entries, 3 nc LU factors) and the array, all copies in flight at once
+    {
+        int toff = 0;
+        for (int i = 0; i < p.nlev; ++i) {
+            const int n[3] = {n0, n1, n2};
+            for (int d = 0; d < 3; ++d) {
+                if (n[d] <= 1) continue;
+                const int nf = (n[d] - 1) / (1 << i) + 1, nc = (nf - 1) / 2 + 1;
+                const TW *gw = static_cast<const TW *>(p.w[i][d]);
+                const TW *gk = static_cast<const TW *>(p.k[i][d]);
+                const TW *gf = static_cast<const TW *>(p.fac[i][d]);
+                for (int e = tid; e < 2 * nf; e += nt) cp_async_elem<TW>(Tb + toff + e, gw + e, true);
+                for (int e = tid; e < 5 * nc; e += nt) cp_async_elem<TW>(Tb + toff + 2 * nf + e, gk + e, true);
+                for (int e = tid; e < 3 * nc; e += nt) cp_async_elem<TW>(Tb + toff + 2 * nf + 5 * nc + e, gf + e, true);
+                toff += 2 * nf + 8 * nc;
+            }
+        }
+    }
+    cp_async_commit();
     for (int e = tid; e < N; e += nt) U[e] = static_cast<TW>(A[e]);
+    cp_async_wait<0>();
     __syncthreads();
+    int level_toff = 0;
+    int toffs[kSmallMaxLevels];
+    for (int i = 0; i < p.nlev; ++i) {
+        toffs[i] = level_toff;
+        const int n[3] = {n0, n1, n2};
+        for (int d = 0; d < 3; ++d) {
+            if (n[d] <= 1) continue;
+            const int nf = (n[d] - 1) / (1 << i) + 1, nc = (nf - 1) / 2 + 1;
+            level_toff += 2 * nf + 8 * nc;
+        }
+    }
 
     for (int it = 0; it < p.nlev; ++it) {
         const int i = (MODE == MODE_DEC) ? it : p.nlev - 1 - it;
@@ -205,14 +271,25 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(SmallParams p)
         SmallLevel<TW> L;
         const int n[3] = {n0, n1, n2};
         const int st[3] = {n1 * n2, n2, 1};
+        int toff = toffs[i];
         for (int d = 0; d < 3; ++d) {
             L.act[d] = n[d] > 1 ? 1 : 0;
             L.nf[d] = L.act[d] ? (n[d] - 1) / s + 1 : 1;
             L.nc[d] = L.act[d] ? (L.nf[d] - 1) / 2 + 1 : 1;
             L.st[d] = st[d] * s;
-            L.w[d] = static_cast<const TW *>(p.w[i][d]);
-            L.k[d] = static_cast<const TW *>(p.k[i][d]);
-            L.fac[d] = static_cast<const TW *>(p.fac[i][d]);
+            const TW *gw = static_cast<const TW *>(p.w[i][d]);
+            const TW *gk = static_cast<const TW *>(p.k[i][d]);
+            const TW *gf = static_cast<const TW *>(p.fac[i][d]);
+            if (L.act[d]) {
+                L.w[d] = Tb + toff;
+                L.k[d] = Tb + toff + 2 * L.nf[d];
+                L.fac[d] = Tb + toff + 2 * L.nf[d] + 5 * L.nc[d];
+                toff += 2 * L.nf[d] + 8 * L.nc[d];
+            } else {
+                L.w[d] = gw;
+                L.k[d] = gk;
+                L.fac[d] = gf;
+            }
         }
 
         if constexpr (MODE == MODE_DEC) {
@@ -241,6 +318,13 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small(SmallParams p)
     }
 
     for (int e = tid; e < N; e += nt) A[e] = static_cast<T>(U[e]);
+}
+
+template <typename T, typename TW, int MODE>
+__global__ void __launch_bounds__(kSmallThreads, 1) k_small(SmallParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    small_run<T, TW, MODE>(p, smem_raw);
 }
 
 }  // namespace mg

@@ -34,6 +34,21 @@ inline int64_t small_hplane(const int64_t *n)
     return n[1] * m2;
 }
 
+// Elements of the tables of nlev levels of an array of n nodes per dim:
+// 2 interpolation weights per fine node, 5 stencil entries and 3 LU factors
+// per coarse node, for every active dim of every level.
+inline int64_t small_tab_elems(const int64_t *n, int nlev)
+{
+    int64_t t = 0;
+    for (int i = 0; i < nlev; ++i)
+        for (int k = 0; k < 3; ++k)
+            if (n[k] > 1) {
+                const int64_t nf = (n[k] - 1) / (int64_t(1) << i) + 1;
+                t += 2 * nf + 8 * ((nf - 1) / 2 + 1);
+            }
+    return t;
+}
+
 // Largest dynamic shared memory the single-block kernel asks for, and the
 // longest dimension it takes (its solves run one thread per line).
 constexpr int64_t kSmallMaxBytes = 227 * 1024;

@@ -29,7 +29,11 @@ def test_batch_equals_single_fields_and_oracle(tmp_path):
         work = [f.clone() for f in fields]
         batch.decompose(work)
         torch.cuda.synchronize()
+    # a batch runs every field with the per-field kernels (no cooperative
+    # launch); the same plans with the cooperative kernel switched off give
+    # the same bits
     for p, s in zip(plans, single):
+        p.tune(0, 4, 1)
         p.decompose(s)
     torch.cuda.synchronize()
     for w, s, h in zip(work, single, host):

@@ -1,5 +1,7 @@
 """The single-block coarse-level kernel against the FP64 oracle and against
-the tiled per-level kernels (plan tuning parameter 3 switches between them).
+the tiled per-level kernels (plan tuning parameter 3 switches between them;
+parameter 4 keeps the cooperative kernel out, so that these plans take the
+single-block kernel wherever it applies).
 
 Shapes cover the three ways the kernel is entered: the whole field fits
 (it runs every level on the user array), the field is large and the kernel
@@ -62,6 +64,7 @@ def test_small_path_matches_oracle_and_tiled(shape, dtype, nonuniform):
     coords = _rand_coords(shape, 31) if nonuniform else None
     u = _field(shape, dtype, 30)
     plan = mg.Plan(shape, coords=coords, dtype=dtype)
+    plan.tune(0, 4, 1)
     tiled = mg.Plan(shape, coords=coords, dtype=dtype)
     tiled.tune(0, 3, 1)
     assert mg.mgard_plan_get_tune(plan.handle, 0, 3) == 0
@@ -89,6 +92,7 @@ def test_small_path_round_trip(shape, dtype):
     mg = _mg()
     u = _field(shape, dtype, 32)
     plan = mg.Plan(shape, dtype=dtype)
+    plan.tune(0, 4, 1)
     t = torch.from_numpy(u).cuda()
     plan.decompose(t)
     plan.recompose(t)
