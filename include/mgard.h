@@ -128,6 +128,11 @@ MGARD_API mgard_status mgard_recompose(const mgard_plan *plan, void *d_data, voi
  *            levels whose array fits one block's shared memory, at most
  *            227 KB, sides <= 257); 1 = always the single-block kernel.
  *   The forms of params 3 and 4 differ only in floating-point rounding order.
+ *   param 6  plan-wide: polls of a grid-barrier wait in the cooperative
+ *            kernel before the wait gives up and records it (0 = default,
+ *            2^22 polls of tens of nanoseconds each).  A wait runs out only
+ *            when the limit is far too small for the work between barriers;
+ *            the result is then wrong, and mgard_plan_check reports it.
  *   mgard_plan_get_tune also reports param 5: the first level the
  *   cooperative kernel runs (-1: none).
  * Returns MGARD_ERR_INVALID_ARG for an unknown parameter or value. */
@@ -135,6 +140,13 @@ MGARD_API mgard_status mgard_plan_tune(mgard_plan *plan, int level, int param, i
 
 /* Current value of a tuning parameter of level j (-1 on error). */
 MGARD_API int mgard_plan_get_tune(const mgard_plan *plan, int level, int param);
+
+/* Status of the last cooperative launch that used workspace d_ws (the
+ * plan's layout): synchronizes `stream`, then returns MGARD_ERR_TIMEOUT if a
+ * grid-barrier wait of that launch ran out (its results are not valid),
+ * else MGARD_OK (also when the plan has no cooperative kernel).  No paper
+ * counterpart: a safeguard of this implementation's bounded waits. */
+MGARD_API mgard_status mgard_plan_check(const mgard_plan *plan, const void *d_ws, void *stream);
 
 /* End-to-end forms with host buffers: copy h_in (host, prod(dims) elements,
  * pinned for overlap) into d_data, transform it in place, copy the result

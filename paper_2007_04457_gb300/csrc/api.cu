@@ -88,6 +88,7 @@ struct mgard_plan {
     // shared memory; coop_auto is the plan's choice, coop_off a tune switch
     int coop_j = 0, coop_auto = 0, coop_s = 0;
     bool coop_off = false;
+    int coop_spin = 0;                // barrier poll limit (0: default)
     int coop_grid = 0;
     size_t coop_smem = 0;
     int coop_hcap = 0;
@@ -368,7 +369,7 @@ cudaError_t run_multi(const mgard_plan *P, int mode, void *data, char *ws, cudaS
         }
     }
     mp.bar = reinterpret_cast<unsigned *>(ws + P->coop_bar_off);
-    mp.spin_limit = kMultiSpinLimit;
+    mp.spin_limit = P->coop_spin > 0 ? P->coop_spin : kMultiSpinLimit;
     cudaError_t err = cudaMemsetAsync(mp.bar, 0, kMultiBarrierWords * sizeof(unsigned), st);
     if (err != cudaSuccess) return err;
     return timed(P, KIND_MULTI, j0, st, [&] { return launch_multi<TX, TW>(mode, mp, P->coop_grid, P->coop_smem, st); });
@@ -1102,6 +1103,10 @@ mgard_status mgard_plan_tune(mgard_plan *P, int level, int param, int value)
         P->small_j = value ? P->L : P->small_auto;
         P->coop_j = (value || P->coop_off) ? P->L : P->coop_auto;
         return MGARD_OK;
+    case 6:
+        if (value < 0) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: barrier poll limit");
+        P->coop_spin = value;
+        return MGARD_OK;
     case 4:
         if (value != 0 && value != 1) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: cooperative switch");
         P->coop_off = value != 0;
@@ -1129,8 +1134,24 @@ int mgard_plan_get_tune(const mgard_plan *P, int level, int param)
     case 3: return P->small_j == P->L ? 1 : 0;
     case 4: return P->coop_off ? 1 : 0;
     case 5: return P->coop_j < P->L ? P->coop_j : -1;
+    case 6: return P->coop_spin;
     default: return -1;
     }
+}
+
+mgard_status mgard_plan_check(const mgard_plan *P, const void *d_ws, void *stream)
+{
+    if (!P) return fail(MGARD_ERR_INVALID_ARG, "plan_check: plan is NULL");
+    if (P->coop_auto >= P->L) return MGARD_OK;
+    if (!d_ws) return fail(MGARD_ERR_INVALID_ARG, "plan_check: d_ws is NULL");
+    unsigned word = 0;
+    const char *src = static_cast<const char *>(d_ws) + P->coop_bar_off + 2 * sizeof(unsigned);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t err = cudaMemcpyAsync(&word, src, sizeof(word), cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) return cuda_fail(err, "plan_check");
+    if (word != 0) return fail(MGARD_ERR_TIMEOUT, "a grid-barrier wait of the cooperative kernel ran out");
+    return MGARD_OK;
 }
 
 static mgard_status host_call(bool DEC, const mgard_plan *P, const void *h_in, void *h_out, void *d_data,

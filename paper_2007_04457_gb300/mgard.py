@@ -63,6 +63,7 @@ def _load() -> ctypes.CDLL:
                                 ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "mgard_plan_tune": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "mgard_plan_get_tune": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "mgard_plan_check": ([vp, vp, vp], ctypes.c_int),
         "mgard_batch_create": ([ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)],
                                ctypes.c_int),
         "mgard_batch_destroy": ([vp], ctypes.c_int),
@@ -177,6 +178,10 @@ def mgard_plan_get_tune(plan: int, level: int, param: int) -> int:
     return LIB.mgard_plan_get_tune(plan, level, param)
 
 
+def mgard_plan_check(plan: int, d_ws: int, stream: int) -> None:
+    _check(LIB.mgard_plan_check(plan, d_ws, stream), "mgard_plan_check")
+
+
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -272,6 +277,14 @@ class Plan:
     def tune(self, level: int, param: int, value: int) -> None:
         """Launch-shape tuning of one level (see mgard_plan_tune)."""
         mgard_plan_tune(self.handle, level, param, value)
+
+    def check(self, workspace=None, stream=None) -> None:
+        """Raise MgardError (MGARD_ERR_TIMEOUT) if a grid-barrier wait of the
+        last cooperative launch on this workspace ran out (mgard_plan_check)."""
+        torch = _torch()
+        ws = workspace if workspace is not None else self.workspace()
+        s = stream if stream is not None else torch.cuda.current_stream(ws.device)
+        mgard_plan_check(self.handle, ws.data_ptr(), s.cuda_stream)
 
     def close(self):
         if getattr(self, "handle", None):

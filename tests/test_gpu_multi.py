@@ -130,3 +130,30 @@ def test_multi_switch():
     assert mg.mgard_plan_get_tune(plan.handle, 0, 5) == 0
     with pytest.raises(mg.MgardError):
         plan.tune(0, 4, 2)
+
+
+def test_multi_barrier_wait_limit_is_reported():
+    """A poll limit far too small for the work between barriers makes waits
+    run out: the kernel finishes (every access stays within the level arrays
+    whatever the timing), records it, and mgard_plan_check reports it; the
+    default limit gives a clean record and the right result."""
+    mg = _mg()
+    shape = (129, 129, 129)
+    u = _field(shape, "f32", 53)
+    plan = mg.Plan(shape, dtype="f32")
+    ws = plan.workspace("cuda")
+    t = torch.from_numpy(u).cuda()
+    plan.tune(0, 6, 1)
+    assert mg.mgard_plan_get_tune(plan.handle, 0, 6) == 1
+    plan.decompose(t, ws)
+    with pytest.raises(mg.MgardError) as info:
+        plan.check(ws)
+    assert info.value.status == 5  # MGARD_ERR_TIMEOUT
+    plan.tune(0, 6, 0)
+    t = torch.from_numpy(u).cuda()
+    plan.decompose(t, ws)
+    plan.check(ws)
+    want = oracle.decompose(u.astype(np.float64))
+    assert _relerr(t.cpu().numpy().astype(np.float64), want) <= TOL["f32"]
+    with pytest.raises(mg.MgardError):
+        plan.tune(0, 6, -1)
