@@ -114,7 +114,10 @@ MGARD_API mgard_status mgard_recompose(const mgard_plan *plan, void *d_data, voi
 
 /* Launch-shape tuning of one level (step j = 0 is the finest level L).
  * Params 0-2 change only tile shapes and kernel variants, not the result.
- *   param 0  restriction tile: 0 = 8 x 64, 1 = 4 x 64, 2 = 16 x 64 coarse nodes
+ *   param 0  restriction tile: 0 = 8 x 64, 1 = 4 x 64, 2 = 16 x 64 coarse nodes per
+ *            block, 3 = 8 x 30 (FP64: 4 x 30) per warp (levels with at least
+ *            30 coarse columns and one strip of rows; the default where it
+ *            applies)
  *   param 1  warps (chunks) per line in the correction solves, 1..32, or
  *            0 = automatic (about 16 nodes per chunk)
  *   param 2  coarse planes per restriction work item (0 = automatic)

@@ -19,7 +19,9 @@ import json
 import math
 import os
 
-CONFIGS = (0, 1, 2)                 # load-vector tile configurations
+CONFIGS = (0, 1, 2)                 # load-vector tile configurations the model ranks
+DEFAULT = -1                        # each level keeps the plan's own choice (warp
+                                    # strips where they apply), always timed
 TILE_COLS = 64                      # coarse columns per tile
 SOLVE_WARPS = (0, 8, 16)            # 0 = automatic
 SECTOR = 32
@@ -98,13 +100,15 @@ def cache_key(gpu: str, shape, dtype: str) -> str:
 
 def apply(plan, cfg: int, warps: int) -> None:
     """Set the tile configuration and solve warps on every level of a plan
-    (a configuration the device cannot run is skipped for that level)."""
+    (a configuration the device cannot run is skipped for that level;
+    cfg = DEFAULT keeps each level's own choice)."""
     from .mgard import MgardError
     for level in range(plan.levels):
-        try:
-            plan.tune(level, 0, cfg)
-        except MgardError:
-            pass
+        if cfg != DEFAULT:
+            try:
+                plan.tune(level, 0, cfg)
+            except MgardError:
+                pass
         plan.tune(level, 1, warps)
 
 
@@ -127,7 +131,8 @@ def _time(plan, field, ws, reps: int) -> float:
 
 def tune(plan, field=None, top: int = 3, reps: int = 3, cache: bool = True, cache_path=None) -> dict:
     """Pick (tile config, solve warps) for ``plan`` by the model-pruned search
-    and apply it.  ``field`` is a scratch tensor of the plan's shape and dtype
+    (the plan's own per-level choice plus the ``top`` configurations of the
+    byte model) and apply it.  ``field`` is a scratch tensor of the plan's shape and dtype
     (its contents are transformed back and forth); one is made if omitted.
     Returns {"cfg", "warps", "ms", "timed"}."""
     import torch
@@ -143,7 +148,7 @@ def tune(plan, field=None, top: int = 3, reps: int = 3, cache: bool = True, cach
     ws = plan.workspace(field.device)
     elem = 8 if plan.dtype == "f64" else 4
     timed = []
-    for cfg in ranked_configs(plan.shape, elem, top):
+    for cfg in [DEFAULT] + ranked_configs(plan.shape, elem, top):
         for warps in SOLVE_WARPS:
             try:
                 apply(plan, cfg, warps)

@@ -61,6 +61,7 @@ struct mgard_level {
     int zreq;            // requested coarse planes per restriction item (0 = automatic)
     int zchunk, nzc, tiles_y, tiles_x;
     int rgrid_dec, rgrid_rec;
+    int kuni32[3], kuni64[3];  // 1: the interior rows of K (float / double table) are all equal
 };
 
 struct mgard_plan {
@@ -231,6 +232,7 @@ cudaError_t run_restrict_level(const mgard_plan *P, int j, int mode, void *A, ch
     p.zchunk = L.zchunk;
     p.nzc = L.nzc;
     p.nitems = L.tiles_y * L.tiles_x * L.nzc;
+    p.kuni1 = (sizeof(T) == 4) ? L.kuni32[1] : L.kuni64[1];
     const int grid = (mode == MODE_DEC) ? L.rgrid_dec : L.rgrid_rec;
     return timed(P, mode == MODE_DEC ? KIND_RESTRICT_DEC : KIND_RESTRICT_REC, j, st,
                  [&] { return launch_restrict<T, TW>(P->act, mode, L.rcfg, p, grid, st); });
@@ -551,10 +553,18 @@ cudaError_t configure_restrict(const mgard_plan *P, mgard_level &L, bool finest,
     cudaError_t err = finest ? restrict_shape<TU, TW>(P->act, MODE_DEC, L.rcfg, &sh)
                              : restrict_shape<TW, TW>(P->act, MODE_DEC, L.rcfg, &sh);
     if (err != cudaSuccess) return err;
-    // tiles of ty x tx coarse nodes; the last tile of a dimension also takes
-    // the final node, so there are ceil((m-1)/t) tiles
-    L.tiles_y = (P->act == ACT_1D) ? 1 : (int)std::max<int64_t>(1, (L.m[1] - 1 + sh.ty - 1) / sh.ty);
-    L.tiles_x = (int)std::max<int64_t>(1, (L.m[2] - 1 + sh.tx - 1) / sh.tx);
+    if (L.rcfg == 3) {
+        // strips of tx x ty coarse nodes, the last one shifted back to end at
+        // the final node: ceil(m/t) of them; the level must hold one strip
+        if (L.m[2] < sh.tx || L.m[1] < sh.ty) return cudaErrorInvalidValue;
+        L.tiles_y = (int)((L.m[1] + sh.ty - 1) / sh.ty);
+        L.tiles_x = (int)((L.m[2] + sh.tx - 1) / sh.tx);
+    } else {
+        // tiles of ty x tx coarse nodes; the last tile of a dimension also
+        // takes the final node, so there are ceil((m-1)/t) tiles
+        L.tiles_y = (P->act == ACT_1D) ? 1 : (int)std::max<int64_t>(1, (L.m[1] - 1 + sh.ty - 1) / sh.ty);
+        L.tiles_x = (int)std::max<int64_t>(1, (L.m[2] - 1 + sh.tx - 1) / sh.tx);
+    }
     const int64_t tiles = (int64_t)L.tiles_y * L.tiles_x;
     const int64_t ipb = std::max(1, sh.items_per_block);
     const int64_t slots = (int64_t)std::max(1, sh.blocks_per_sm) * P->num_sms * ipb;  // resident items
@@ -594,8 +604,13 @@ cudaError_t configure_level(mgard_plan *P, mgard_level &L, bool finest)
     if (L.rcfg_user || P->act == ACT_1D) return configure_restrict<TU, TW>(P, L, finest, &items, &slots);
     int best = 0;
     int64_t best_items = -1;
-    static const int order[kRestrictConfigs] = {2, 0, 1};  // 16, 8, 4 coarse rows
-    for (int cfg : order) {
+    // warp strips first for 4-byte level arrays (FP64 arithmetic is slow
+    // enough on this GPU that the strips' recomputed halo rows cost more than
+    // the tiles' staging); then tiles of 16, 8, 4 coarse rows
+    static const int order4[kRestrictConfigs] = {3, 2, 0, 1};
+    static const int order8[kRestrictConfigs] = {2, 0, 1, 3};
+    const bool elem4 = (finest ? P->elem_user : P->elem_ws) == 4;
+    for (int cfg : (elem4 ? order4 : order8)) {
         L.rcfg = cfg;
         cudaError_t err = configure_restrict<TU, TW>(P, L, finest, &items, &slots);
         if (err != cudaSuccess) {  // e.g. more shared memory than the device has
@@ -725,6 +740,7 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
             lv.n[q] = 1;
             lv.m[q] = 1;
             lv.w_off[q] = lv.k_off[q] = lv.t_off[q] = 0;
+            lv.kuni32[q] = lv.kuni64[q] = 0;
         }
         for (int k = 0; k < nd; ++k) {
             const int q = 3 - nd + k;
@@ -734,6 +750,14 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
             lv.n[q] = nf;
             lv.m[q] = (nf - 1) / 2 + 1;
             build_dim_tables(xf, tab, &lv.w_off[q], &lv.k_off[q], &lv.t_off[q]);
+            // interior K rows all equal (bitwise, in each table precision)
+            lv.kuni32[q] = lv.kuni64[q] = 1;
+            for (int64_t I = 2; I + 1 < lv.m[q]; ++I)
+                for (int t = 0; t < 5; ++t) {
+                    const double a = tab[lv.k_off[q] + 5 * I + t], b = tab[lv.k_off[q] + 5 + t];
+                    if (a != b) lv.kuni64[q] = 0;
+                    if ((float)a != (float)b) lv.kuni32[q] = 0;
+                }
         }
         const size_t mbytes = (size_t)count(lv.m) * P->elem_ws;
         lv.v_off = ws;

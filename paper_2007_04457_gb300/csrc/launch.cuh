@@ -12,8 +12,10 @@ namespace mg {
 
 // Tile shapes of the load-vector kernel selectable per level (coarse nodes in
 // dims 1 x 2; a last tile absorbs the final node of a dimension):
-//   2D/3D: cfg 0 = 8 x 64, cfg 1 = 4 x 64, cfg 2 = 16 x 64;  1D: 256 per block
-constexpr int kRestrictConfigs = 3;
+//   2D/3D: cfg 0 = 8 x 64, cfg 1 = 4 x 64, cfg 2 = 16 x 64 (a block per tile),
+//   cfg 3 = 8 x 30 (FP64: 4 x 30) per warp, for levels with m2 >= 30 and
+//   m1 >= the strip rows;  1D: 256 per block
+constexpr int kRestrictConfigs = 4;
 
 struct RestrictShape {
     int ty, tx;            // coarse nodes per tile in dims 1 and 2

@@ -9,6 +9,7 @@
 #include "launch.cuh"
 #include "multi.cuh"
 #include "restrict.cuh"
+#include "restrict_strip.cuh"
 #include "small.cuh"
 #include "sweep.cuh"
 #include "solve.cuh"
@@ -21,26 +22,31 @@ struct RestrictEntry {
     void (*fn)(RestrictParams);
     int ty, tx;          // coarse rows / columns per tile (1D: coarse nodes per block)
     size_t smem;         // dynamic shared memory bytes
+    int ipb;             // work items a block runs at once
 };
 
 template <typename T, typename TW, int ACT, int TY>
 RestrictEntry restrict_entry()
 {
     using G = RestrictGeom<T, ACT, TY>;
-    return {k_restrict<T, TW, ACT, TY>, G::TY, kRestrictTX, sizeof(T) * (size_t)G::TOTAL};
+    return {k_restrict<T, TW, ACT, TY>, G::TY, kRestrictTX, sizeof(T) * (size_t)G::TOTAL, 1};
 }
 
-// Tile configuration 0 / 1 / 2 = 8 / 4 / 16 coarse rows.  Both directions
-// read a level array that holds coefficients on N_l \ N_{l-1} (the
-// decomposition writes them before its restriction), so one kernel serves
-// both.
+// Tile configuration 0 / 1 / 2 = 8 / 4 / 16 coarse rows; 3 = one warp per
+// strip of 30 coarse columns (k_restrict_strip, 2D/3D only).  Both
+// directions read a level array that holds coefficients on N_l \ N_{l-1}
+// (the decomposition writes them before its restriction), so one kernel
+// serves both.
 template <typename T, typename TW, int ACT>
 RestrictEntry restrict_pick_cfg(int cfg)
 {
     if constexpr (ACT == ACT_1D) {
-        return {k_restrict1d<T, TW>, 1, 256, 0};
+        return {k_restrict1d<T, TW>, 1, 256, 0, 1};
     } else {
         switch (cfg) {
+        case 3:
+            return {k_restrict_strip<T, TW, ACT == ACT_3D>, StripRows<T>::value, kStripCols, 0,
+                    kStripThreads / 32};
         case 1: return restrict_entry<T, TW, ACT, 4>();
         case 2: return restrict_entry<T, TW, ACT, 16>();
         default: return restrict_entry<T, TW, ACT, 8>();
@@ -52,6 +58,7 @@ template <typename T, typename TW>
 bool restrict_pick(int act, int cfg, RestrictEntry *e)
 {
     if (cfg < 0 || cfg >= kRestrictConfigs) return false;
+    if (cfg == 3 && act == ACT_1D) return false;
     switch (act) {
     case ACT_1D: *e = restrict_pick_cfg<T, TW, ACT_1D>(cfg); return true;
     case ACT_2D: *e = restrict_pick_cfg<T, TW, ACT_2D>(cfg); return true;
@@ -85,7 +92,7 @@ cudaError_t restrict_shape(int act, int mode, int cfg, RestrictShape *out)
     out->tx = e.tx;
     out->smem = e.smem;
     out->blocks_per_sm = bps;
-    out->items_per_block = 1;
+    out->items_per_block = e.ipb;
     return cudaSuccess;
 }
 

@@ -27,6 +27,7 @@ struct RestrictParams {
     int tiles_y, tiles_x;    // tile grid over (dim 1, dim 2) in coarse nodes
     int zchunk, nzc;         // coarse planes per work item, number of chunks
     int nitems;              // tiles_y * tiles_x * nzc
+    int kuni1;               // 1: the interior rows of k1 are all equal
 };
 
 // Tridiagonal solves along one dimension of a compact coarse array, with the
