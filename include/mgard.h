@@ -118,8 +118,11 @@ MGARD_API mgard_status mgard_recompose(const mgard_plan *plan, void *d_data, voi
  *            block, 3 = 8 x 30 (FP64: 4 x 30) per warp (levels with at least
  *            30 coarse columns and one strip of rows; the default where it
  *            applies)
- *   param 1  warps (chunks) per line in the correction solves, 1..32, or
- *            0 = automatic (about 16 nodes per chunk)
+ *   param 1  correction solves: 0 = automatic (one thread per line along a
+ *            dimension whose stride exceeds its length when the level has at
+ *            least 256 such lines per SM, else chunks of about 16 nodes per
+ *            warp), -1 = one thread per line, 1..32 = that many warps
+ *            (chunks) per line in the shared-memory panel kernel
  *   param 2  coarse planes per restriction work item (0 = automatic)
  *   param 3  plan-wide (any valid level): 0 = run the coarse end of the
  *            hierarchy in a single launch per direction (default); 1 = run

@@ -1115,7 +1115,7 @@ mgard_status mgard_plan_tune(mgard_plan *P, int level, int param, int value)
         L.rcfg_user = true;
         break;
     case 1:
-        if (value < 0 || value > 32) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: solve warps");
+        if (value < -1 || value > 32) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: solve warps");
         L.svar = value;
         return MGARD_OK;
     case 2:

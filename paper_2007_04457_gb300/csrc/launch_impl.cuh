@@ -130,14 +130,40 @@ cudaError_t launch_solve_chunks(const SolveParams &p, int num_sms, cudaStream_t 
     return cudaGetLastError();
 }
 
-// nw_req = 0: k_solve_chunks for lines up to 576 nodes (and shared memory
-// for the contiguous case); otherwise (or nw_req > 0) the shared-memory
-// panel kernel with nw_req warps (0: about 16 nodes per chunk).
+// k_solve_lines: one thread per line, the factors of the line in shared memory.
+template <typename TW>
+cudaError_t launch_solve_lines(const SolveParams &p, int num_sms, cudaStream_t st)
+{
+    const size_t smem = (size_t)3 * p.m * sizeof(TW);
+    cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(k_solve_lines<TW>),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int bps = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_solve_lines<TW>, kSolveLineThreads, smem);
+    if (err != cudaSuccess) return err;
+    const int64_t blocks = (p.nlines + kSolveLineThreads - 1) / kSolveLineThreads;
+    const int64_t grid = std::min<int64_t>(blocks, (int64_t)std::max(1, bps) * num_sms);
+    k_solve_lines<TW><<<(unsigned)grid, kSolveLineThreads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+// nw_req = -1, or 0 for a dimension whose stride exceeds its length (in a
+// cube the slowest one) with enough lines for every SM: k_solve_lines
+// (measured slower than the chunks along the other dimensions, several times
+// along the contiguous one, where its stores evict the lines its loads still
+// need); nw_req = 0 otherwise: k_solve_chunks for lines up to 576
+// nodes (and shared memory for the contiguous case); else (or nw_req > 0)
+// the shared-memory panel kernel with nw_req warps (0: about 16 nodes per
+// chunk).
 template <typename TW>
 cudaError_t launch_solve(const SolveParams &p_in, int nw_req, int num_sms, cudaStream_t st)
 {
     SolveParams p = p_in;
     if (p.nlines <= 0) return cudaSuccess;
+    const bool lines_fit = (size_t)3 * p.m * sizeof(TW) <= 100 * 1024;
+    if (lines_fit && (nw_req == -1 || (nw_req == 0 && p.inner > p.m && p.nlines >= (int64_t)kSolveLinesPerSm * num_sms)))
+        return launch_solve_lines<TW>(p, num_sms, st);
+    if (nw_req < 0) nw_req = 0;
     if (nw_req == 0 && p.m <= 32 * kSolveChunkWarps && (int64_t)p.m * p.stride < (int64_t(1) << 31)) {
         const int ch = (p.m <= 16 * kSolveChunkWarps) ? 16 : 32;
         const int nw = (p.m + ch - 1) / ch;

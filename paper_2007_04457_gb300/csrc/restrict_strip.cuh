@@ -36,48 +36,73 @@ struct StripRows {
     static constexpr int value = sizeof(T) == 4 ? 8 : 4;  // coarse rows per strip
 };
 
+// Fine columns lo, lo + 1 of a row (0 outside the grid or for an invalid
+// row).  Two scalar loads: measured faster here than one paired load.
+template <typename T>
+__device__ __forceinline__ void strip_load2(const T *row, int lo, int n2, bool yok, T &a, T &b)
+{
+    a = (yok && lo >= 0 && lo < n2) ? row[lo] : T(0);
+    b = (yok && lo + 1 >= 0 && lo + 1 < n2) ? row[lo + 1] : T(0);
+}
+
 // The dim-2 and dim-1 restriction of fine plane z into g[0..TY): ODD = the
 // plane index is odd (every node of it is a coefficient node).  Gathers the
 // coarse values of owned nodes into V when `gather`.  UNI: every coarse row
 // of the strip has the dim-1 stencil ku (kept in registers); else the rows
-// are read from the table k1.
+// are read from the table k1.  Each lane reads the pair (2X, 2X+1) of a row
+// whose plane and row indices have an even sum, else (2X-1, 2X) (these are
+// the pairs that start on a two-element boundary, since n1 n2 and n2 are
+// odd); the other three values of its five come from the neighbour lanes.
 template <typename T, typename TW, int TY, bool ODD, bool UNI>
 __device__ __forceinline__ void strip_plane(const T *__restrict__ plane, int n1, int n2, int Y0, int cx,
-                                            bool ok0, bool ok1, const T (&kx)[5], const T (&ku)[5],
-                                            const T *__restrict__ k1, T (&g)[TY], bool gather,
-                                            TW *__restrict__ vplane, int yown, int m2, int X, bool xown)
+                                            const T (&kx)[5], const T (&ku)[5], const T *__restrict__ k1,
+                                            T (&g)[TY], bool gather, TW *__restrict__ vplane, int yown, int m2,
+                                            int X, bool xown)
 {
 #pragma unroll
     for (int j = 0; j < TY; ++j) g[j] = T(0);
     constexpr int R = 2 * TY + 3;
-    T c0[R], c1[R];
+    T a[R], b[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {  // every load of the plane first
         const int y = 2 * Y0 - 2 + r;
         const bool yok = y >= 0 && y < n1;
-        const T *row = plane + (int64_t)(yok ? y : 0) * n2 + cx;
-        c0[r] = (yok && ok0) ? row[0] : T(0);
-        c1[r] = (yok && ok1) ? row[1] : T(0);
+        const T *row = plane + (int64_t)(yok ? y : 0) * n2;
+        const bool aligned = ((ODD ? 1 : 0) + r) % 2 == 0;  // fine row y has the parity of r
+        strip_load2<T>(row, aligned ? cx : cx - 1, n2, yok, a[r], b[r]);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
+        const bool aligned = ((ODD ? 1 : 0) + r) % 2 == 0;
+        // the five fine columns 2X-2 .. 2X+2 of row r
+        T c0r, c1r, cm1, cm2, cp2;
+        if (aligned) {  // a = col 2X, b = col 2X+1
+            c0r = a[r];
+            c1r = b[r];
+            cm2 = __shfl_up_sync(0xffffffffu, a[r], 1);
+            cm1 = __shfl_up_sync(0xffffffffu, b[r], 1);
+            cp2 = __shfl_down_sync(0xffffffffu, a[r], 1);
+        } else {  // a = col 2X-1, b = col 2X
+            cm1 = a[r];
+            c0r = b[r];
+            c1r = __shfl_down_sync(0xffffffffu, a[r], 1);
+            cp2 = __shfl_down_sync(0xffffffffu, b[r], 1);
+            cm2 = __shfl_up_sync(0xffffffffu, b[r], 1);
+        }
         const bool rodd = ODD || (r & 1);  // fine row 2 Y0 - 2 + r has the parity of r
         if (!ODD && !(r & 1) && gather) {
             // coarse values of the owned coarse rows
             const int Yr = Y0 - 1 + r / 2;
-            if (Yr >= yown && Yr < Y0 + TY && xown) vplane[(int64_t)Yr * m2 + X] = static_cast<TW>(c0[r]);
+            if (Yr >= yown && Yr < Y0 + TY && xown) vplane[(int64_t)Yr * m2 + X] = static_cast<TW>(c0r);
         }
-        const T cm2 = __shfl_up_sync(0xffffffffu, c0[r], 1);
-        const T cm1 = __shfl_up_sync(0xffffffffu, c1[r], 1);
-        const T cp2 = __shfl_down_sync(0xffffffffu, c0[r], 1);
         T h;
         if (rodd) {
             h = fma_rn(kx[0], cm2, mul_rn(kx[1], cm1));
-            h = fma_rn(kx[2], c0[r], h);
-            h = fma_rn(kx[3], c1[r], h);
+            h = fma_rn(kx[2], c0r, h);
+            h = fma_rn(kx[3], c1r, h);
             h = fma_rn(kx[4], cp2, h);
         } else {  // even columns of a coarse row are coarse nodes: C = 0
-            h = fma_rn(kx[1], cm1, mul_rn(kx[3], c1[r]));
+            h = fma_rn(kx[1], cm1, mul_rn(kx[3], c1r));
         }
         // fine row 2 Y0 - 2 + r feeds coarse row Y0 + j with tap r - 2 j
 #pragma unroll
@@ -114,7 +139,6 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_restrict_strip(RestrictPar
         const bool active = lane >= 1 && lane <= kStripCols;
         const bool xown = active && X >= xown0;
         const int cx = 2 * X;
-        const bool ok0 = cx >= 0 && cx < n2, ok1 = cx + 1 >= 0 && cx + 1 < n2;
         T kx[5], ku[5];
 #pragma unroll
         for (int t = 0; t < 5; ++t) kx[t] = active ? k2[5 * X + t] : T(0);
@@ -151,10 +175,10 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_restrict_strip(RestrictPar
                 if (has_odd) {
                     const T *po = A + (int64_t)(2 * Z - 1) * plane_sz;
                     if (uni)
-                        strip_plane<T, TW, TY, true, true>(po, n1, n2, Y0, cx, ok0, ok1, kx, ku, k1, g, false, V,
+                        strip_plane<T, TW, TY, true, true>(po, n1, n2, Y0, cx, kx, ku, k1, g, false, V,
                                                            yown, m2, X, xown);
                     else
-                        strip_plane<T, TW, TY, true, false>(po, n1, n2, Y0, cx, ok0, ok1, kx, ku, k1, g, false, V,
+                        strip_plane<T, TW, TY, true, false>(po, n1, n2, Y0, cx, kx, ku, k1, g, false, V,
                                                             yown, m2, X, xown);
                     const T kzP3 = __ldg(k0 + 5 * (Z - 1) + 3), kzC1 = __ldg(k0 + 5 * Z + 1);
 #pragma unroll
@@ -168,10 +192,10 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_restrict_strip(RestrictPar
             const T *pe = A + (int64_t)(HZ ? 2 * Z : 0) * plane_sz;
             TW *vpe = V + (int64_t)(HZ ? Z : 0) * cplane;
             if (uni)
-                strip_plane<T, TW, TY, false, true>(pe, n1, n2, Y0, cx, ok0, ok1, kx, ku, k1, g, own_even, vpe, yown,
+                strip_plane<T, TW, TY, false, true>(pe, n1, n2, Y0, cx, kx, ku, k1, g, own_even, vpe, yown,
                                                     m2, X, xown);
             else
-                strip_plane<T, TW, TY, false, false>(pe, n1, n2, Y0, cx, ok0, ok1, kx, ku, k1, g, own_even, vpe,
+                strip_plane<T, TW, TY, false, false>(pe, n1, n2, Y0, cx, kx, ku, k1, g, own_even, vpe,
                                                      yown, m2, X, xown);
             if constexpr (HZ) {
                 const T kzP4 = (Z >= 1) ? __ldg(k0 + 5 * (Z - 1) + 4) : T(0);

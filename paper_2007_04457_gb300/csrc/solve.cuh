@@ -398,4 +398,101 @@ __global__ void __launch_bounds__(32 * kSolveChunkWarps) k_solve_chunks(SolvePar
     cp_async_wait<0>();
 }
 
+// One thread per line: the Thomas recurrences of the tabulated LU factors
+// (forward y_i = f_i - a_i y_{i-1}, backward z_i = inv_i y_i - q_i z_{i+1}),
+// U nodes at a time with the next U prefetched into registers before the
+// current ones are stored, so a thread always has loads in flight.  Threads
+// of a warp take consecutive lines: along a strided dimension their loads
+// are coalesced, along the contiguous one each load instruction touches one
+// 32-byte sector per lane that the next loads of the thread hit in L1.  The
+// factors sit in shared memory as (a, inv, q) per node, read by every lane
+// of the warp at the same address.  vmode as in SolveParams; the forward
+// pass reads src when given and writes y into F, the backward pass writes z
+// into F or V +- z into V.
+constexpr int kSolveLineThreads = 256;
+constexpr int kSolveLinesPerSm = 256;  // lines per SM from which one thread per line pays
+
+template <typename TW>
+struct LineUnroll {
+    static constexpr int value = sizeof(TW) == 4 ? 8 : 4;
+};
+
+template <typename TW>
+__global__ void __launch_bounds__(kSolveLineThreads) k_solve_lines(SolveParams p)
+{
+    constexpr int U = LineUnroll<TW>::value;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TW *tab = reinterpret_cast<TW *>(smem_raw);
+    const int m = p.m;
+    const TW *fac = static_cast<const TW *>(p.fac);
+    for (int e = threadIdx.x; e < 3 * m; e += blockDim.x) tab[e] = fac[e];
+    __syncthreads();
+    TW *F = static_cast<TW *>(p.F);
+    TW *V = static_cast<TW *>(p.V);
+    const TW *src = p.src ? static_cast<const TW *>(p.src) : F;
+    const int64_t inner = p.inner, stride = p.stride;
+    const int nch = (m + U - 1) / U;
+    const TW sg = (p.vmode == 2) ? TW(-1) : TW(1);
+    for (int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; line < p.nlines;
+         line += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t base = (line / inner) * (inner * m) + line % inner;
+        const TW *s_in = src + base;
+        TW *f = F + base;
+        // forward: y into F
+        TW cur[U], nxt[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) cur[u] = (u < m) ? s_in[(int64_t)u * stride] : TW(0);
+        TW t = TW(0);
+        for (int c = 0; c < nch; ++c) {
+            const int k0 = c * U;
+            if (c + 1 < nch) {
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    nxt[u] = (k0 + U + u < m) ? s_in[(int64_t)(k0 + U + u) * stride] : TW(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (k0 + u < m) {
+                    t = cur[u] - tab[3 * (k0 + u)] * t;
+                    f[(int64_t)(k0 + u) * stride] = t;
+                }
+#pragma unroll
+            for (int u = 0; u < U; ++u) cur[u] = nxt[u];
+        }
+        // backward: z into F, or V +- z
+        TW *dst = (p.vmode == 0) ? f : V + base;
+        TW vc[U], vn[U];
+        {
+            const int k0 = (nch - 1) * U;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                cur[u] = (k0 + u < m) ? f[(int64_t)(k0 + u) * stride] : TW(0);
+                vc[u] = (p.vmode != 0 && k0 + u < m) ? dst[(int64_t)(k0 + u) * stride] : TW(0);
+            }
+        }
+        t = TW(0);
+        for (int c = nch - 1; c >= 0; --c) {
+            const int k0 = c * U;
+            if (c > 0) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    nxt[u] = f[(int64_t)(k0 - U + u) * stride];
+                    vn[u] = (p.vmode != 0) ? dst[(int64_t)(k0 - U + u) * stride] : TW(0);
+                }
+            }
+#pragma unroll
+            for (int u = U - 1; u >= 0; --u)
+                if (k0 + u < m) {
+                    t = tab[3 * (k0 + u) + 1] * cur[u] - tab[3 * (k0 + u) + 2] * t;
+                    dst[(int64_t)(k0 + u) * stride] = (p.vmode == 0) ? t : vc[u] + sg * t;
+                }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                cur[u] = nxt[u];
+                vc[u] = vn[u];
+            }
+        }
+    }
+}
+
 }  // namespace mg

@@ -37,14 +37,22 @@ struct SweepRows {
     static constexpr int value = (ACT & 2) ? 8 : 1;
 };
 
-// resident blocks the registers are sized for (8-byte elements need more)
+// 4-byte elements: the next step's loads are issued before this step's
+// stores (registers for two steps); resident blocks the registers are sized
+// for, as measured at 513^3: 5 (decomposition) and 4 (recomposition) with
+// that prefetch, 4 for 8-byte elements without it
 template <int ELEM>
+struct SweepPipe {
+    static constexpr bool value = ELEM == 4;
+};
+template <int ELEM, int MODE>
 struct SweepMinBlocks {
-    static constexpr int value = ELEM == 4 ? 6 : 4;
+    static constexpr int value = ELEM == 4 ? (MODE == MODE_DEC ? 5 : 4) : 4;
 };
 
 template <typename T, typename TW, int ACT, int MODE>
-__global__ void __launch_bounds__(32 * kSweepWarps, SweepMinBlocks<(int)sizeof(T)>::value) k_sweep(PlaceParams p)
+__global__ void __launch_bounds__(32 * kSweepWarps, (SweepMinBlocks<(int)sizeof(T), MODE>::value))
+k_sweep(PlaceParams p)
 {
     constexpr bool HZ = (ACT & 4) != 0, HY = (ACT & 2) != 0;
     constexpr bool DEC = (MODE == MODE_DEC);
@@ -85,15 +93,14 @@ __global__ void __launch_bounds__(32 * kSweepWarps, SweepMinBlocks<(int)sizeof(T
 #pragma unroll
         for (int r = 0; r < R; ++r) I2p[r] = I2c[r] = T(0);
 
-        for (int64_t z = z0; z <= zlast; z += (HZ ? 2 : 1)) {
+        // Loads of the step at even plane z (and the odd plane z - 1 before
+        // it); with PIPE the next step's loads are issued before this step's
+        // stores, which go to other planes.
+        auto load_step = [&](int64_t z, T (&ue)[RE], T (&va)[RE], T (&vb)[RE], T (&uo)[R], T (&uz)[R]) {
             const bool own = z < z1;
-            const bool odd_plane = HZ && z > z0;  // the odd plane z - 1 is processed with this one
-            // the tile's first row at column x, in this plane and the odd one
-            T *plane = A + (z * n1 + y0) * n2 + (xv ? x : 0);
-            T *oplane = A + ((odd_plane ? z - 1 : z) * n1 + y0) * n2 + (xv ? x : 0);
-            // ---- every load of the step first (the stores below go to the same
-            // array, so loads issued after them could not be moved ahead)
-            T ue[RE], va[RE], vb[RE], uo[R], uz[R];
+            const bool odd_plane = HZ && z > z0;
+            const T *plane = A + (z * n1 + y0) * n2 + (xv ? x : 0);
+            const T *oplane = A + ((odd_plane ? z - 1 : z) * n1 + y0) * n2 + (xv ? x : 0);
 #pragma unroll
             for (int e = 0; e < RE; ++e) {
                 const int r = 2 * e;
@@ -106,10 +113,13 @@ __global__ void __launch_bounds__(32 * kSweepWarps, SweepMinBlocks<(int)sizeof(T
                     // (even columns) are read: the others belong to another tile
                     if (live && xv && (mine || !(x & 1))) ue[e] = row[0];
                 } else {
+                    // V(x/2) for every lane (pairs of lanes share it); the odd
+                    // lanes' right neighbour V(x/2 + 1) comes from the next lane,
+                    // and lane 31's from one more load
                     if (live) {
                         const TW *vrow = V + ((z >> (HZ ? 1 : 0)) * m1 + ((y0 + r) >> 1)) * m2;
                         if (xv) va[e] = static_cast<T>(vrow[x >> 1]);
-                        if (xo) vb[e] = static_cast<T>(vrow[(x >> 1) + 1]);
+                        if (L == 31 && xo) vb[e] = static_cast<T>(vrow[(x >> 1) + 1]);
                     }
                     if (live && mine && xo) ue[e] = row[0];
                 }
@@ -120,6 +130,30 @@ __global__ void __launch_bounds__(32 * kSweepWarps, SweepMinBlocks<(int)sizeof(T
                 if (r >= nrow) continue;
                 if (HY && (r & 1) && own && xv) uo[r] = plane[r * sn2];
                 if (odd_plane && xv) uz[r] = oplane[r * sn2];
+            }
+        };
+
+        constexpr bool PIPE = SweepPipe<(int)sizeof(T)>::value;
+        T ue[RE], va[RE], vb[RE], uo[R], uz[R];
+        T ue2[RE], va2[RE], vb2[RE], uo2[R], uz2[R];
+        if (PIPE) load_step(z0, ue, va, vb, uo, uz);
+        for (int64_t z = z0; z <= zlast; z += (HZ ? 2 : 1)) {
+            const bool own = z < z1;
+            const bool odd_plane = HZ && z > z0;  // the odd plane z - 1 is processed with this one
+            T *plane = A + (z * n1 + y0) * n2 + (xv ? x : 0);
+            T *oplane = A + ((odd_plane ? z - 1 : z) * n1 + y0) * n2 + (xv ? x : 0);
+            const int64_t zn = z + (HZ ? 2 : 1);
+            if constexpr (PIPE) {
+                if (zn <= zlast) load_step(zn, ue2, va2, vb2, uo2, uz2);
+            } else {
+                load_step(z, ue, va, vb, uo, uz);
+            }
+            if constexpr (!DEC) {
+#pragma unroll
+                for (int e = 0; e < RE; ++e) {
+                    const T vn = __shfl_down_sync(0xffffffffu, va[e], 1);
+                    if (L != 31) vb[e] = vn;
+                }
             }
             // ---- dim-2 interpolant of the even rows
             T Xe[RE];
@@ -174,6 +208,19 @@ __global__ void __launch_bounds__(32 * kSweepWarps, SweepMinBlocks<(int)sizeof(T
             }
 #pragma unroll
             for (int r = 0; r < R; ++r) I2p[r] = I2c[r];
+            if constexpr (PIPE) {
+#pragma unroll
+                for (int e = 0; e < RE; ++e) {
+                    ue[e] = ue2[e];
+                    va[e] = va2[e];
+                    vb[e] = vb2[e];
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    uo[r] = uo2[r];
+                    uz[r] = uz2[r];
+                }
+            }
         }
     }
 }

@@ -66,7 +66,7 @@ def test_autotune_keeps_results(tmp_path):
     shape = (65, 129, 65)
     plan = mg.Plan(shape, dtype="f32")
     best = autotune.tune(plan, top=2, reps=1, cache_path=str(tmp_path / "t.json"))
-    assert best["cfg"] in autotune.CONFIGS and best["warps"] in autotune.SOLVE_WARPS
+    assert best["cfg"] in (autotune.DEFAULT,) + autotune.CONFIGS and best["warps"] in autotune.SOLVE_WARPS
     u = synth.sinusoid_field(shape, 12, seed=41, dtype=np.float32)
     t = torch.from_numpy(u).cuda()
     plan.decompose(t)
