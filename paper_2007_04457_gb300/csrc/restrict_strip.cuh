@@ -37,23 +37,30 @@ struct StripRows {
 };
 
 // Fine columns lo, lo + 1 of a row (0 outside the grid or for an invalid
-// row).  Two scalar loads: measured faster here than one paired load.
-template <typename T>
+// row; INT: both inside).  Two scalar loads: measured faster here than one
+// paired load.
+template <typename T, bool INT>
 __device__ __forceinline__ void strip_load2(const T *row, int lo, int n2, bool yok, T &a, T &b)
 {
-    a = (yok && lo >= 0 && lo < n2) ? row[lo] : T(0);
-    b = (yok && lo + 1 >= 0 && lo + 1 < n2) ? row[lo + 1] : T(0);
+    if (INT) {
+        a = row[lo];
+        b = row[lo + 1];
+    } else {
+        a = (yok && lo >= 0 && lo < n2) ? row[lo] : T(0);
+        b = (yok && lo + 1 >= 0 && lo + 1 < n2) ? row[lo + 1] : T(0);
+    }
 }
 
 // The dim-2 and dim-1 restriction of fine plane z into g[0..TY): ODD = the
 // plane index is odd (every node of it is a coefficient node).  Gathers the
-// coarse values of owned nodes into V when `gather`.  UNI: every coarse row
-// of the strip has the dim-1 stencil ku (kept in registers); else the rows
-// are read from the table k1.  Each lane reads the pair (2X, 2X+1) of a row
+// coarse values of owned nodes into V when `gather`.  FAST: every coarse row
+// of the strip has the dim-1 stencil ku (kept in registers) and every row
+// and column the strip reads lies inside the grid; else the rows are read
+// from the table k1 and every load is checked.  Each lane reads the pair (2X, 2X+1) of a row
 // whose plane and row indices have an even sum, else (2X-1, 2X) (these are
 // the pairs that start on a two-element boundary, since n1 n2 and n2 are
 // odd); the other three values of its five come from the neighbour lanes.
-template <typename T, typename TW, int TY, bool ODD, bool UNI>
+template <typename T, typename TW, int TY, bool ODD, bool FAST>
 __device__ __forceinline__ void strip_plane(const T *__restrict__ plane, int n1, int n2, int Y0, int cx,
                                             const T (&kx)[5], const T (&ku)[5], const T *__restrict__ k1,
                                             T (&g)[TY], bool gather, TW *__restrict__ vplane, int yown, int m2,
@@ -66,10 +73,10 @@ __device__ __forceinline__ void strip_plane(const T *__restrict__ plane, int n1,
 #pragma unroll
     for (int r = 0; r < R; ++r) {  // every load of the plane first
         const int y = 2 * Y0 - 2 + r;
-        const bool yok = y >= 0 && y < n1;
+        const bool yok = FAST || (y >= 0 && y < n1);
         const T *row = plane + (int64_t)(yok ? y : 0) * n2;
         const bool aligned = ((ODD ? 1 : 0) + r) % 2 == 0;  // fine row y has the parity of r
-        strip_load2<T>(row, aligned ? cx : cx - 1, n2, yok, a[r], b[r]);
+        strip_load2<T, FAST>(row, aligned ? cx : cx - 1, n2, yok, a[r], b[r]);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -108,7 +115,7 @@ __device__ __forceinline__ void strip_plane(const T *__restrict__ plane, int n1,
 #pragma unroll
         for (int j = 0; j < TY; ++j) {
             const int bb = r - 2 * j;
-            if (bb >= 0 && bb <= 4) g[j] = fma_rn(UNI ? ku[bb] : __ldg(k1 + 5 * (Y0 + j) + bb), h, g[j]);
+            if (bb >= 0 && bb <= 4) g[j] = fma_rn(FAST ? ku[bb] : __ldg(k1 + 5 * (Y0 + j) + bb), h, g[j]);
         }
     }
 }
@@ -142,9 +149,12 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_restrict_strip(RestrictPar
         T kx[5], ku[5];
 #pragma unroll
         for (int t = 0; t < 5; ++t) kx[t] = active ? k2[5 * X + t] : T(0);
-        // the strip's coarse rows share one dim-1 stencil when the level's
-        // interior rows are all equal and the strip holds no boundary row
-        const bool uni = p.kuni1 && Y0 >= 1 && Y0 + TY <= m1 - 1;
+        // fast path: the strip's coarse rows share one dim-1 stencil (the
+        // level's interior rows are all equal and the strip holds no boundary
+        // row), and its fine rows 2 Y0 - 2 .. 2 Y0 + 2 TY and columns
+        // 2 X0 - 3 .. 2 X0 + 61 are inside the grid
+        const bool uni = p.kuni1 && Y0 >= 1 && Y0 + TY <= m1 - 1 && 2 * (Y0 + TY) < n1 && X0 >= 2 &&
+                         X0 + 31 < m2;
 #pragma unroll
         for (int t = 0; t < 5; ++t) ku[t] = uni ? __ldg(k1 + 5 * Y0 + t) : T(0);
 
