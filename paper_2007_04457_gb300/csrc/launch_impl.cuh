@@ -232,9 +232,34 @@ inline void sweep_chunks(PlaceParams &p, int act, int64_t R, int num_sms)
     p.nzc = (p.n0 + p.zchunk - 1) / p.zchunk;
 }
 
+// k_sweep2 (recomposition, 4-byte 2D/3D levels): tiles of 64 columns.
+template <typename T, typename TW>
+cudaError_t launch_sweep2(int act, PlaceParams p, int num_sms, cudaStream_t st)
+{
+    constexpr int64_t R = 8;
+    const int64_t tiles = ((p.m2 + 31) / 32) * ((p.n1 + R - 1) / R);
+    if (!(act & 4)) {
+        p.zchunk = 1;
+        p.nzc = 1;
+    } else {
+        const int64_t want = (int64_t)num_sms * 32;
+        const int64_t nz = std::max<int64_t>(1, std::min<int64_t>((want + tiles - 1) / tiles, (p.n0 - 1) / 2));
+        int64_t zc = (p.n0 + nz - 1) / nz;
+        zc += zc & 1;
+        p.zchunk = std::max<int64_t>(2, zc);
+        p.nzc = (p.n0 + p.zchunk - 1) / p.zchunk;
+    }
+    const int64_t items = tiles * p.nzc;
+    const int64_t blocks = std::min<int64_t>((items + kSweepWarps - 1) / kSweepWarps, 1 << 30);
+    if (act == ACT_3D) k_sweep2<T, TW, ACT_3D><<<(unsigned)blocks, 32 * kSweepWarps, 0, st>>>(p);
+    else k_sweep2<T, TW, ACT_2D><<<(unsigned)blocks, 32 * kSweepWarps, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
 template <typename T, typename TW, int MODE>
 cudaError_t launch_sweep(int act, PlaceParams p, int num_sms, cudaStream_t st)
 {
+    if (MODE == MODE_REC && sizeof(T) == 4 && act != ACT_1D) return launch_sweep2<T, TW>(act, p, num_sms, st);
     const int64_t R = sweep_rows(act, sizeof(T));
     sweep_chunks(p, act, R, num_sms);
     const int64_t items = ((p.n2 + 31) / 32) * ((act & 2) ? (p.n1 + R - 1) / R : 1) * p.nzc;

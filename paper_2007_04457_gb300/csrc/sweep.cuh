@@ -225,4 +225,164 @@ k_sweep(PlaceParams p)
     }
 }
 
+// k_sweep2 (recomposition, 2D/3D): as k_sweep<MODE_REC>, with two columns per
+// lane.  Warp item: 64 columns (lane L: coarse column X = 32 tx + L, fine
+// columns 2X, 2X+1) x R rows x a chunk of planes.  Per even row the lane
+// reads V(X) once (the warp's 32 reads are consecutive) and the neighbour
+// V(X+1) by shuffle (lane 31: one more read); the interpolants of odd rows
+// and of the odd plane before come from registers.  The next step's loads
+// are issued before this step's stores.
+constexpr bool kSweep2Pipe = true;  // prefetch the next step's loads
+constexpr int kSweep2Blocks = 3;     // resident blocks the registers are sized for (4 spills)
+
+template <typename T, typename TW, int ACT>
+__global__ void __launch_bounds__(32 * kSweepWarps, kSweep2Blocks) k_sweep2(PlaceParams p)
+{
+    constexpr bool HZ = (ACT & 4) != 0;
+    constexpr int R = 8;           // fine rows per item
+    constexpr int RE = R / 2 + 1;  // even rows with the halo row
+    T *__restrict__ A = static_cast<T *>(p.A);
+    const TW *__restrict__ V = static_cast<const TW *>(p.V);
+    const T *__restrict__ w0 = static_cast<const T *>(p.w0);
+    const T *__restrict__ w1 = static_cast<const T *>(p.w1);
+    const T *__restrict__ w2 = static_cast<const T *>(p.w2);
+    const int64_t n0 = p.n0, n1 = p.n1, n2 = p.n2, m1 = p.m1, m2 = p.m2;
+    const int sn2 = (int)n2;
+    const int L = threadIdx.x & 31;
+    const int64_t warp0 = (int64_t)blockIdx.x * kSweepWarps + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * kSweepWarps;
+    const int64_t tiles_x = (m2 + 31) / 32;
+    const int64_t tiles_y = (n1 + R - 1) / R;
+    const int64_t zc = p.zchunk;
+    const int64_t items = tiles_x * tiles_y * p.nzc;
+
+    for (int64_t item = warp0; item < items; item += nwarps) {
+        const int64_t tx = item % tiles_x;
+        const int64_t rest = item / tiles_x;
+        const int64_t ty = rest % tiles_y;
+        const int64_t tz = rest / tiles_y;
+        const int64_t X = tx * 32 + L;
+        const bool v0 = X < m2, v1 = X + 1 < m2;  // fine columns 2X, 2X+1 exist
+        const int64_t c0 = 2 * X;
+        const T wl2 = v1 ? w2[2 * (c0 + 1)] : T(0), wr2 = v1 ? w2[2 * (c0 + 1) + 1] : T(0);
+        const int64_t y0 = ty * R;
+        const int nrow = (int)min64(R, n1 - y0);
+        const bool hrow = y0 + R < n1;
+        T wy[R / 2][2];  // weights of the odd rows
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            const int64_t y = y0 + 2 * k + 1;
+            wy[k][0] = (2 * k + 1 < nrow) ? w1[2 * y] : T(0);
+            wy[k][1] = (2 * k + 1 < nrow) ? w1[2 * y + 1] : T(0);
+        }
+        const int64_t z0 = HZ ? tz * zc : 0;
+        const int64_t z1 = HZ ? min64(z0 + zc, n0) : 1;
+        const int64_t zlast = (HZ && z1 < n0) ? z1 : z1 - 1;
+
+        // loads of the step at even plane z: V of its even rows (and the
+        // right neighbour for lane 31), the coefficients of its own rows and
+        // of the odd plane z - 1
+        auto load_step = [&](int64_t z, T (&vv)[RE], T (&vr)[RE], T (&ce)[R][2], T (&co)[R][2]) {
+            const bool own = z < z1;
+            const bool odd_plane = HZ && z > z0;
+            const TW *vpl = V + (z >> (HZ ? 1 : 0)) * m1 * m2 + (y0 >> 1) * m2 + X;
+            const T *pl = A + (z * n1 + y0) * n2 + c0;
+            const T *ol = A + ((odd_plane ? z - 1 : z) * n1 + y0) * n2 + c0;
+#pragma unroll
+            for (int e = 0; e < RE; ++e) {
+                const int r = 2 * e;
+                const bool live = r < nrow || (r == R && hrow);
+                vv[e] = (live && v0) ? static_cast<T>(vpl[(int64_t)e * m2]) : T(0);
+                vr[e] = (live && L == 31 && v1) ? static_cast<T>(vpl[(int64_t)e * m2 + 1]) : T(0);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const bool mine = own && r < nrow;
+                ce[r][0] = (mine && (r & 1) && v0) ? pl[r * sn2] : T(0);
+                ce[r][1] = (mine && v1) ? pl[r * sn2 + 1] : T(0);
+                const bool om = odd_plane && r < nrow;
+                co[r][0] = (om && v0) ? ol[r * sn2] : T(0);
+                co[r][1] = (om && v1) ? ol[r * sn2 + 1] : T(0);
+            }
+        };
+
+        T I2p[R][2], I2c[R][2];
+#pragma unroll
+        for (int r = 0; r < R; ++r) I2p[r][0] = I2p[r][1] = I2c[r][0] = I2c[r][1] = T(0);
+        T vv[RE], vr[RE], ce[R][2], co[R][2];
+        T vv2[RE], vr2[RE], ce2[R][2], co2[R][2];
+        if (kSweep2Pipe) load_step(z0, vv, vr, ce, co);
+        for (int64_t z = z0; z <= zlast; z += (HZ ? 2 : 1)) {
+            const bool own = z < z1;
+            const bool odd_plane = HZ && z > z0;
+            T *pl = A + (z * n1 + y0) * n2 + c0;
+            T *ol = A + ((odd_plane ? z - 1 : z) * n1 + y0) * n2 + c0;
+            const int64_t zn = z + (HZ ? 2 : 1);
+            if constexpr (kSweep2Pipe) {
+                if (zn <= zlast) load_step(zn, vv2, vr2, ce2, co2);
+            } else {
+                load_step(z, vv, vr, ce, co);
+            }
+            // the plane's interpolant: even rows from V (dim 2), odd rows dim 1
+            T Xe[RE][2];
+#pragma unroll
+            for (int e = 0; e < RE; ++e) {
+                T vn = __shfl_down_sync(0xffffffffu, vv[e], 1);
+                if (L == 31) vn = vr[e];
+                Xe[e][0] = vv[e];
+                Xe[e][1] = lerp2(wl2, vv[e], wr2, vn);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r & 1) {
+                    const int k = r / 2;
+                    I2c[r][0] = lerp2(wy[k][0], Xe[k][0], wy[k][1], Xe[k + 1][0]);
+                    I2c[r][1] = lerp2(wy[k][0], Xe[k][1], wy[k][1], Xe[k + 1][1]);
+                } else {
+                    I2c[r][0] = Xe[r / 2][0];
+                    I2c[r][1] = Xe[r / 2][1];
+                }
+            }
+            // stores: the even plane (coarse nodes take V), then the odd one
+            if (own) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (r >= nrow) break;
+                    if (v0) pl[r * sn2] = (r & 1) ? add_rn(ce[r][0], I2c[r][0]) : I2c[r][0];
+                    if (v1) pl[r * sn2 + 1] = add_rn(ce[r][1], I2c[r][1]);
+                }
+            }
+            if (odd_plane) {
+                const int64_t zo = z - 1;
+                const T wzl = w0[2 * zo], wzr = w0[2 * zo + 1];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (r >= nrow) break;
+                    if (v0) ol[r * sn2] = add_rn(co[r][0], lerp2(wzl, I2p[r][0], wzr, I2c[r][0]));
+                    if (v1) ol[r * sn2 + 1] = add_rn(co[r][1], lerp2(wzl, I2p[r][1], wzr, I2c[r][1]));
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                I2p[r][0] = I2c[r][0];
+                I2p[r][1] = I2c[r][1];
+            }
+            if constexpr (kSweep2Pipe) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    ce[r][0] = ce2[r][0];
+                    ce[r][1] = ce2[r][1];
+                    co[r][0] = co2[r][0];
+                    co[r][1] = co2[r][1];
+                }
+#pragma unroll
+                for (int e = 0; e < RE; ++e) {
+                    vv[e] = vv2[e];
+                    vr[e] = vr2[e];
+                }
+            }
+        }
+    }
+}
+
 }  // namespace mg
