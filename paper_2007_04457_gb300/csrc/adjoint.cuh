@@ -161,4 +161,113 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_even(AdjParams p)
     }
 }
 
+// k_adj_odd2 (2D/3D): the same map as k_adj_odd, separably.  A warp item is a
+// pair of fine planes (2Zp, 2Zp + 1) x a pair of fine rows (2Yp, 2Yp + 1);
+// the K^T stencils of dims 0 and 1 reach the same 3 x 3 coarse rows
+// (Iz, Iy in {Zp-1, Zp, Zp+1} x {Yp-1, Yp, Yp+1}) from all four fine rows,
+// so the warp folds them per coarse column into four rows R in shared memory
+// (one per fine row, with that row's dim-0 and dim-1 weights) and then
+// applies the dim-2 stencil per fine column: about one coarse load per fine
+// node instead of up to 27.
+constexpr int kAdj2Warps = 4;
+
+template <typename TW>
+__device__ __forceinline__ void kt_pair(int64_t P, int64_t m, const TW *k, TW (&w)[2][3])
+{
+    // fine 2P (even): coarse P-1 (tap 4), P (tap 2), P+1 (tap 0);
+    // fine 2P+1 (odd): coarse P (tap 3), P+1 (tap 1); slot a <-> coarse P-1+a
+    w[0][0] = (P - 1 >= 0) ? k[5 * (P - 1) + 4] : TW(0);
+    w[0][1] = k[5 * P + 2];
+    w[0][2] = (P + 1 < m) ? k[5 * (P + 1)] : TW(0);
+    w[1][0] = TW(0);
+    w[1][1] = k[5 * P + 3];
+    w[1][2] = (P + 1 < m) ? k[5 * (P + 1) + 1] : TW(0);
+}
+
+template <typename T, typename TW, int ACT>
+__global__ void __launch_bounds__(32 * kAdj2Warps) k_adj_odd2(AdjParams p)
+{
+    constexpr bool HZ = (ACT & 4) != 0;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *__restrict__ A = static_cast<T *>(p.A);
+    const TW *__restrict__ Zc = static_cast<const TW *>(p.Z);
+    const TW *k0 = static_cast<const TW *>(p.k0);
+    const TW *k1 = static_cast<const TW *>(p.k1);
+    const TW *k2 = static_cast<const TW *>(p.k2);
+    const int64_t n0 = p.n0, n1 = p.n1, n2 = p.n2, m0 = p.m0, m1 = p.m1, m2 = p.m2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    TW *R = reinterpret_cast<TW *>(smem_raw) + (size_t)warp * 4 * m2;  // R[pz][py][X]
+    const int64_t zp_n = HZ ? (n0 + 1) / 2 : 1, yp_n = (n1 + 1) / 2;
+    const int64_t items = zp_n * yp_n;
+    for (int64_t item = (int64_t)blockIdx.x * kAdj2Warps + warp; item < items;
+         item += (int64_t)gridDim.x * kAdj2Warps) {
+        const int64_t Yp = item % yp_n, Zp = item / yp_n;
+        TW wz[2][3], wy[2][3];
+        if (HZ) {
+            kt_pair<TW>(Zp, m0, k0, wz);
+        } else {
+            wz[0][0] = wz[0][2] = wz[1][0] = wz[1][1] = wz[1][2] = TW(0);
+            wz[0][1] = TW(1);
+        }
+        kt_pair<TW>(Yp, m1, k1, wy);
+        // coarse rows (Zp-1+a, Yp-1+b), present when inside the coarse grid
+        for (int64_t X = lane; X < m2; X += 32) {
+            TW acc[2][2] = {{TW(0), TW(0)}, {TW(0), TW(0)}};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int64_t Iz = HZ ? Zp - 1 + a : 0;
+                if (HZ ? (Iz < 0 || Iz >= m0) : a != 1) continue;
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const int64_t Iy = Yp - 1 + b;
+                    if (Iy < 0 || Iy >= m1) continue;
+                    const TW v = Zc[(Iz * m1 + Iy) * m2 + X];
+#pragma unroll
+                    for (int pz = 0; pz < 2; ++pz)
+#pragma unroll
+                        for (int py = 0; py < 2; ++py) acc[pz][py] += wz[pz][a] * wy[py][b] * v;
+                }
+            }
+#pragma unroll
+            for (int pz = 0; pz < 2; ++pz)
+#pragma unroll
+                for (int py = 0; py < 2; ++py) R[(pz * 2 + py) * m2 + X] = acc[pz][py];
+        }
+        __syncwarp();
+        for (int64_t x = lane; x < n2; x += 32) {
+            // dim-2 stencil weights of fine column x over R
+            const int64_t Xh = x >> 1;
+            TW wx[3];
+            if (!(x & 1)) {
+                wx[0] = (Xh - 1 >= 0) ? k2[5 * (Xh - 1) + 4] : TW(0);
+                wx[1] = k2[5 * Xh + 2];
+                wx[2] = (Xh + 1 < m2) ? k2[5 * (Xh + 1)] : TW(0);
+            } else {
+                wx[0] = TW(0);
+                wx[1] = k2[5 * Xh + 3];
+                wx[2] = (Xh + 1 < m2) ? k2[5 * (Xh + 1) + 1] : TW(0);
+            }
+#pragma unroll
+            for (int pz = 0; pz < 2; ++pz) {
+                const int64_t z = HZ ? 2 * Zp + pz : 0;
+                if (HZ ? z >= n0 : pz != 0) continue;
+#pragma unroll
+                for (int py = 0; py < 2; ++py) {
+                    const int64_t y = 2 * Yp + py;
+                    if (y >= n1) continue;
+                    if (!((x & 1) || py || pz)) continue;  // a node of N_{l-1}
+                    const TW *r = R + (pz * 2 + py) * m2;
+                    TW g = wx[1] * r[Xh];
+                    if (Xh - 1 >= 0) g += wx[0] * r[Xh - 1];
+                    if (Xh + 1 < m2) g += wx[2] * r[Xh + 1];
+                    T *pa = A + (z * n1 + y) * n2 + x;
+                    const TW av = static_cast<TW>(*pa);
+                    *pa = static_cast<T>(p.sign > 0 ? av + g : av - g);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
 }  // namespace mg

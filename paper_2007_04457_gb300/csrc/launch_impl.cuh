@@ -322,6 +322,17 @@ cudaError_t launch_gather(int act, const PlaceParams &p, cudaStream_t st)
 template <typename T, typename TW>
 cudaError_t launch_adj_odd(int act, const AdjParams &p, cudaStream_t st)
 {
+    const size_t smem2 = (size_t)kAdj2Warps * 4 * p.m2 * sizeof(TW);
+    if (act != ACT_1D && smem2 <= 96 * 1024) {
+        void (*fn)(AdjParams) = (act == ACT_3D) ? k_adj_odd2<T, TW, ACT_3D> : k_adj_odd2<T, TW, ACT_2D>;
+        cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        if (err != cudaSuccess) return err;
+        const int64_t items = ((act == ACT_3D) ? (p.n0 + 1) / 2 : 1) * ((p.n1 + 1) / 2);
+        const int64_t blocks = std::min<int64_t>((items + kAdj2Warps - 1) / kAdj2Warps, int64_t(1) << 30);
+        fn<<<(unsigned)blocks, 32 * kAdj2Warps, smem2, st>>>(p);
+        return cudaGetLastError();
+    }
     dim3 g, b;
     detail::node_grid(p.n2, p.n1, p.n0, &g, &b);
     MG_ACT_SWITCH(k_adj_odd, g, b, p)
