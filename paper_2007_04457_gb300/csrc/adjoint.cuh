@@ -270,4 +270,78 @@ __global__ void __launch_bounds__(32 * kAdj2Warps) k_adj_odd2(AdjParams p)
     }
 }
 
+// k_adj_even2 (2D/3D): the same map as k_adj_even, separably.  The sum of
+// Pi^T over the 3 x 3 x 3 fine box of a coarse node reads only nodes of
+// N_l \ N_{l-1} besides the node itself, whose weight is 1, so
+//   s = sum_{a,b,c} wz_a wy_b wx_c A(box) - A(node).
+// A warp takes one coarse row (Zc, Yc): per fine column it folds the nine
+// fine rows (2Zc-1.., 2Yc-1..) with wz wy (two fine columns per lane,
+// 2X and 2X+1), and the dim-2 weights combine column 2X-1 (the previous
+// lane's, carried across chunks by lane 31), 2X and 2X+1.
+template <typename T, typename TW, int ACT>
+__global__ void __launch_bounds__(32 * kAdj2Warps) k_adj_even2(AdjParams p)
+{
+    constexpr bool HZ = (ACT & 4) != 0;
+    T *__restrict__ A = static_cast<T *>(p.A);
+    const TW *__restrict__ B = static_cast<const TW *>(p.Z);  // compact base, or null: A itself
+    const T *w0 = static_cast<const T *>(p.w0);
+    const T *w1 = static_cast<const T *>(p.w1);
+    const T *w2 = static_cast<const T *>(p.w2);
+    const int64_t n0 = p.n0, n1 = p.n1, n2 = p.n2, m0 = p.m0, m1 = p.m1, m2 = p.m2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t items = m0 * m1;
+    for (int64_t item = (int64_t)blockIdx.x * kAdj2Warps + warp; item < items;
+         item += (int64_t)gridDim.x * kAdj2Warps) {
+        const int64_t Yc = item % m1, Zc = item / m1;
+        // weights of the fine planes / rows 2E-1, 2E, 2E+1 of coarse index E
+        TW wz[3], wy[3];
+        if (HZ) {
+            wz[0] = (Zc >= 1) ? static_cast<TW>(w0[2 * (2 * Zc - 1) + 1]) : TW(0);
+            wz[1] = TW(1);
+            wz[2] = (Zc <= m0 - 2) ? static_cast<TW>(w0[2 * (2 * Zc + 1)]) : TW(0);
+        } else {
+            wz[0] = wz[2] = TW(0);
+            wz[1] = TW(1);
+        }
+        wy[0] = (Yc >= 1) ? static_cast<TW>(w1[2 * (2 * Yc - 1) + 1]) : TW(0);
+        wy[1] = TW(1);
+        wy[2] = (Yc <= m1 - 2) ? static_cast<TW>(w1[2 * (2 * Yc + 1)]) : TW(0);
+        const int64_t ze = HZ ? 2 * Zc : 0, ye = 2 * Yc;
+        TW carry = TW(0);  // folded value of fine column 2 X0 - 1
+        for (int64_t X0 = 0; X0 < m2; X0 += 32) {
+            const int64_t X = X0 + lane;
+            const bool v0 = X < m2, v1 = X + 1 < m2;  // fine columns 2X, 2X+1
+            TW r0 = TW(0), r1 = TW(0), self = TW(0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (wz[a] == TW(0)) continue;
+                const int64_t z = ze - 1 + a;
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    if (wy[b] == TW(0)) continue;
+                    const int64_t y = ye - 1 + b;
+                    const T *row = A + (z * n1 + y) * n2 + 2 * X;
+                    const TW wab = wz[a] * wy[b];
+                    const TW a0 = v0 ? static_cast<TW>(row[0]) : TW(0);
+                    const TW a1 = v1 ? static_cast<TW>(row[1]) : TW(0);
+                    r0 += wab * a0;
+                    r1 += wab * a1;
+                    if (a == 1 && b == 1) self = a0;
+                }
+            }
+            TW rm = __shfl_up_sync(0xffffffffu, r1, 1);  // fine column 2X - 1
+            if (lane == 0) rm = carry;
+            carry = __shfl_sync(0xffffffffu, r1, 31);
+            if (v0) {
+                const TW wr = (X >= 1) ? static_cast<TW>(w2[2 * (2 * X - 1) + 1]) : TW(0);
+                const TW wl = v1 ? static_cast<TW>(w2[2 * (2 * X + 1)]) : TW(0);
+                const TW s2 = wr * rm + r0 + wl * r1 - self;
+                T *pe = A + (ze * n1 + ye) * n2 + 2 * X;
+                const TW base = B ? B[(Zc * m1 + Yc) * m2 + X] : self;
+                *pe = static_cast<T>(p.sign > 0 ? base + s2 : base - s2);
+            }
+        }
+    }
+}
+
 }  // namespace mg

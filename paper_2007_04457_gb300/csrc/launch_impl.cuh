@@ -342,6 +342,13 @@ cudaError_t launch_adj_odd(int act, const AdjParams &p, cudaStream_t st)
 template <typename T, typename TW>
 cudaError_t launch_adj_even(int act, const AdjParams &p, cudaStream_t st)
 {
+    if (act != ACT_1D) {
+        const int64_t items = p.m0 * p.m1;
+        const int64_t blocks = std::min<int64_t>((items + kAdj2Warps - 1) / kAdj2Warps, int64_t(1) << 30);
+        if (act == ACT_3D) k_adj_even2<T, TW, ACT_3D><<<(unsigned)blocks, 32 * kAdj2Warps, 0, st>>>(p);
+        else k_adj_even2<T, TW, ACT_2D><<<(unsigned)blocks, 32 * kAdj2Warps, 0, st>>>(p);
+        return cudaGetLastError();
+    }
     dim3 g, b;
     detail::node_grid(p.m2, p.m1, p.m0, &g, &b);
     MG_ACT_SWITCH(k_adj_even, g, b, p)
