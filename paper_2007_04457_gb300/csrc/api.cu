@@ -84,6 +84,11 @@ struct mgard_plan {
     int small_auto = 0;    // the finest level whose array fits the kernel
     size_t small_smem = 0;
     int small_hcap = 0;
+    // the adjoints run levels adj_j .. L-1 in one block (adj_j = L: none): the
+    // single-block transposed maps are not separable, so they start only on
+    // arrays of at most kAdjSmallNodes nodes
+    int adj_j = 0;
+    size_t adj_smem = 0;
     // levels coop_j .. L-1 in one cooperative launch (coop_j = L: none):
     // coop_j .. coop_s-1 by the whole grid, coop_s .. L-1 by block 0 in
     // shared memory; coop_auto is the plan's choice, coop_off a tune switch
@@ -184,6 +189,27 @@ template <>
 const double *tab_ptr<double>(const mgard_plan *P, int64_t off) { return P->tab64 + off; }
 
 int act_of(int ndim) { return ndim == 1 ? ACT_1D : (ndim == 2 ? ACT_2D : ACT_3D); }
+
+constexpr int64_t kAdjSmallNodes = 5000;
+
+// First level of the single-block transposed maps: from small_j on, the
+// first array of at most kAdjSmallNodes nodes; its shared memory holds the
+// array, the first level's coarse grid and the tables of its levels.
+void adj_select(mgard_plan *P)
+{
+    P->adj_j = P->L;
+    P->adj_smem = 0;
+    for (int j = P->small_j; j < P->L; ++j) {
+        const int64_t *nj = (j == 0) ? P->n : P->lv[j - 1].m;
+        if (nj[0] * nj[1] * nj[2] > kAdjSmallNodes) continue;
+        int64_t m[3];
+        for (int k = 0; k < 3; ++k) m[k] = (nj[k] > 1) ? (nj[k] - 1) / 2 + 1 : 1;
+        P->adj_j = j;
+        P->adj_smem = (size_t)((nj[0] * nj[1] * nj[2] + m[0] * m[1] * m[2] + small_tab_elems(nj, P->L - j)) *
+                               (int64_t)P->elem_ws);
+        return;
+    }
+}
 
 enum { KIND_RESTRICT_DEC = 0, KIND_RESTRICT_REC = 1, KIND_SOLVE = 2, KIND_SOLVE_FUSED = 3,
        KIND_PLACE = 4, KIND_INTERP = 5, KIND_PLACE_EVEN = 6, KIND_ADJ = 7, KIND_SMALL = 8,
@@ -309,9 +335,9 @@ cudaError_t run_interp_level(const mgard_plan *P, int j, void *A, char *ws, cuda
 // Levels small_j .. L-1 in one block, on the array of level small_j (the
 // user array when small_j = 0, else V_{small_j - 1}).
 template <typename T, typename TW>
-cudaError_t run_small(const mgard_plan *P, int mode, void *A, cudaStream_t st)
+cudaError_t run_small(const mgard_plan *P, int mode, void *A, cudaStream_t st, int adjoint = -1)
 {
-    const int j0 = P->small_j;
+    const int j0 = (adjoint >= 0) ? P->adj_j : P->small_j;
     const int64_t *n = (j0 == 0) ? P->n : P->lv[j0 - 1].m;
     SmallParams sp;
     sp.A = A;
@@ -326,6 +352,8 @@ cudaError_t run_small(const mgard_plan *P, int mode, void *A, cudaStream_t st)
             sp.fac[i][d] = tab_ptr<TW>(P, L.t_off[d]);
         }
     }
+    if (adjoint >= 0)  // transposed maps: adjoint 0 = decomposition, 1 = recomposition
+        return timed(P, KIND_ADJ, j0, st, [&] { return launch_small_adj<T, TW>(adjoint, sp, P->adj_smem, st); });
     return timed(P, KIND_SMALL, j0, st, [&] { return launch_small<T, TW>(mode, sp, P->small_smem, st); });
 }
 
@@ -493,12 +521,20 @@ template <typename TU, typename TW>
 mgard_status exec_decompose_adjoint(const mgard_plan *P, void *data, char *ws, cudaStream_t st)
 {
     cudaError_t err;
-    for (int j = 0; j < P->L; ++j) {
+    // levels from adj_j on: one block, coarsest first, on the array of
+    // level adj_j (its gathers are identities there)
+    const int J = P->adj_j;
+    for (int j = 0; j < J; ++j) {
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
         err = (j == 0) ? run_gather<TU, TW>(P, j, A, ws, st) : run_gather<TW, TW>(P, j, A, ws, st);
         if (err != cudaSuccess) return cuda_fail(err, "decompose_adjoint: gather kernel");
     }
-    for (int j = P->L - 1; j >= 0; --j) {
+    if (J < P->L) {
+        void *A = (J == 0) ? data : (void *)(ws + P->lv[J - 1].v_off);
+        err = (J == 0) ? run_small<TU, TW>(P, MODE_DEC, A, st, 0) : run_small<TW, TW>(P, MODE_DEC, A, st, 0);
+        if (err != cudaSuccess) return cuda_fail(err, "decompose_adjoint: single-block kernel");
+    }
+    for (int j = J - 1; j >= 0; --j) {
         const mgard_level &L = P->lv[j];
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
         err = run_solves<TW>(P, j, 0, ws, st, ws + L.v_off);
@@ -520,7 +556,8 @@ template <typename TU, typename TW>
 mgard_status exec_recompose_adjoint(const mgard_plan *P, void *data, char *ws, cudaStream_t st)
 {
     cudaError_t err;
-    for (int j = 0; j < P->L; ++j) {
+    const int J = P->adj_j;  // levels from adj_j on: one block, finest first
+    for (int j = 0; j < J; ++j) {
         const mgard_level &L = P->lv[j];
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
         err = (j == 0) ? run_adj_even<TU, TW>(P, j, A, nullptr, +1, st)
@@ -534,7 +571,12 @@ mgard_status exec_recompose_adjoint(const mgard_plan *P, void *data, char *ws, c
                        : run_adj_odd<TW, TW>(P, j, A, ws + L.f_off, -1, st);
         if (err != cudaSuccess) return cuda_fail(err, "recompose_adjoint: odd-node kernel");
     }
-    for (int j = P->L - 1; j >= 0; --j) {
+    if (J < P->L) {
+        void *A = (J == 0) ? data : (void *)(ws + P->lv[J - 1].v_off);
+        err = (J == 0) ? run_small<TU, TW>(P, MODE_REC, A, st, 1) : run_small<TW, TW>(P, MODE_REC, A, st, 1);
+        if (err != cudaSuccess) return cuda_fail(err, "recompose_adjoint: single-block kernel");
+    }
+    for (int j = J - 1; j >= 0; --j) {
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
         const PlaceParams p = (j == 0) ? place_params<TU>(P, j, A, ws) : place_params<TW>(P, j, A, ws);
         err = (j == 0) ? launch_scatter<TU, TW>(P->act, p, st) : launch_scatter<TW, TW>(P->act, p, st);
@@ -795,6 +837,7 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
         }
     }
     P->small_j = P->small_auto;
+    adj_select(P);
 
     // the cooperative kernel: from the first level whose coarse lines fit one
     // thread's registers, the grid runs every level until the array is small
@@ -1126,6 +1169,7 @@ mgard_status mgard_plan_tune(mgard_plan *P, int level, int param, int value)
         if (value != 0 && value != 1) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: single-block switch");
         P->small_j = value ? P->L : P->small_auto;
         P->coop_j = (value || P->coop_off) ? P->L : P->coop_auto;
+        adj_select(P);
         return MGARD_OK;
     case 6:
         if (value < 0) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: barrier poll limit");

@@ -67,6 +67,11 @@ cudaError_t multi_occupancy(int mode, size_t smem, int *blocks_per_sm);
 template <typename TX, typename TW>
 cudaError_t launch_multi(int mode, const MultiParams &p, int grid, size_t smem, cudaStream_t st);
 
+// Transposed maps of all remaining levels of a small array in one block
+// (small.cuh): dir 0 = decomposition, 1 = recomposition; smem as launch_small.
+template <typename T, typename TW>
+cudaError_t launch_small_adj(int dir, const SmallParams &p, size_t smem, cudaStream_t st);
+
 // Transposed level maps (adjoint.cuh).
 template <typename T, typename TW>
 cudaError_t launch_gather(int act, const PlaceParams &p, cudaStream_t st);

@@ -366,6 +366,17 @@ cudaError_t launch_small(int mode, const SmallParams &p, size_t smem, cudaStream
     return cudaGetLastError();
 }
 
+template <typename T, typename TW>
+cudaError_t launch_small_adj(int dir, const SmallParams &p, size_t smem, cudaStream_t st)
+{
+    void (*fn)(SmallParams) = (dir == 0) ? k_small_adj<T, TW, 0> : k_small_adj<T, TW, 1>;
+    cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    fn<<<1, kSmallThreads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
 template <typename TX, typename TW>
 cudaError_t multi_occupancy(int mode, size_t smem, int *blocks_per_sm)
 {
@@ -408,6 +419,7 @@ cudaError_t launch_multi(int mode, const MultiParams &p, int grid, size_t smem, 
     template cudaError_t launch_adj_odd<T, TW>(int, const AdjParams &, cudaStream_t);          \
     template cudaError_t launch_adj_even<T, TW>(int, const AdjParams &, cudaStream_t);          \
     template cudaError_t launch_small<T, TW>(int, const SmallParams &, size_t, cudaStream_t);    \
+    template cudaError_t launch_small_adj<T, TW>(int, const SmallParams &, size_t, cudaStream_t); \
     template cudaError_t multi_occupancy<T, TW>(int, size_t, int *);                             \
     template cudaError_t launch_multi<T, TW>(int, const MultiParams &, int, size_t, cudaStream_t);
 

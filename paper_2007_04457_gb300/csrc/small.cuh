@@ -320,6 +320,200 @@ __device__ void small_run(const SmallParams &p, unsigned char *smem_raw)
     for (int e = tid; e < N; e += nt) A[e] = static_cast<T>(U[e]);
 }
 
+// Transposed level maps of every remaining level in shared memory (the
+// adjoints of k_small's decomposition and recomposition, Section II-A
+// transposed).  In the strided in-place layout the gather of a level's
+// coarse nodes into V and their placement back are identities, so per level
+// (o = N_l \ N_{l-1}, e = N_{l-1}):
+//   decomposition transpose, coarsest level first:
+//     F = M_{l-1}^{-1} U(e);  U(o) += K^T F;  U(e) -= Pi^T U(o)
+//   recomposition transpose, finest level first:
+//     U(e) += Pi^T U(o);  F = M_{l-1}^{-1} U(e);  U(o) -= K^T F
+// Shared memory: U, then F (the first level's coarse grid), then the tables.
+
+// F <- U at the coarse nodes of level L (compact).
+template <typename TW>
+__device__ void small_gather_f(const TW *U, TW *F, const SmallLevel<TW> &L)
+{
+    const int nc1 = L.nc[1], nc2 = L.nc[2];
+    const float rc1 = 1.0f / (float)nc1, rc2 = 1.0f / (float)nc2;
+    for (int e = threadIdx.x; e < L.nc[0] * nc1 * nc2; e += blockDim.x) {
+        const int r = small_div(e, rc2), X = e - r * nc2;
+        const int Z = small_div(r, rc1), Y = r - Z * nc1;
+        F[e] = U[2 * (Z * L.st[0] + Y * L.st[1] + X * L.st[2])];
+    }
+}
+
+// Coarse neighbours of fine index j of a dimension with their K^T weights.
+template <typename TW>
+__device__ __forceinline__ int small_kt(int j, int m, const TW *k, int (&I)[3], TW (&w)[3])
+{
+    int c = 0;
+    const int I0 = j >> 1;
+    if (!(j & 1)) {
+        if (I0 - 1 >= 0) { I[c] = I0 - 1; w[c] = k[5 * (I0 - 1) + 4]; ++c; }
+        I[c] = I0; w[c] = k[5 * I0 + 2]; ++c;
+        if (I0 + 1 < m) { I[c] = I0 + 1; w[c] = k[5 * (I0 + 1)]; ++c; }
+    } else {
+        I[c] = I0; w[c] = k[5 * I0 + 3]; ++c;
+        if (I0 + 1 < m) { I[c] = I0 + 1; w[c] = k[5 * (I0 + 1) + 1]; ++c; }
+    }
+    return c;
+}
+
+// U(o) += sg (K^T F)(o) at every node of N_l \ N_{l-1} of level L.
+template <typename TW>
+__device__ void small_adj_odd(TW *U, const TW *F, const SmallLevel<TW> &L, TW sg)
+{
+    const int nf1 = L.nf[1], nf2 = L.nf[2], nc1 = L.nc[1], nc2 = L.nc[2];
+    const float r1 = 1.0f / (float)nf1, r2 = 1.0f / (float)nf2;
+    for (int e = threadIdx.x; e < L.nf[0] * nf1 * nf2; e += blockDim.x) {
+        const int row = small_div(e, r2), i2 = e - row * nf2;
+        const int i0 = small_div(row, r1), i1 = row - i0 * nf1;
+        if (!(((L.act[0] & i0) | (L.act[1] & i1) | (L.act[2] & i2)) & 1)) continue;  // a node of N_{l-1}
+        int I0[3] = {0, 0, 0}, I1[3] = {0, 0, 0}, I2[3] = {0, 0, 0};
+        TW w0[3] = {TW(1), TW(0), TW(0)}, w1[3] = {TW(1), TW(0), TW(0)}, w2[3] = {TW(1), TW(0), TW(0)};
+        const int c0 = L.act[0] ? small_kt<TW>(i0, L.nc[0], L.k[0], I0, w0) : 1;
+        const int c1 = L.act[1] ? small_kt<TW>(i1, nc1, L.k[1], I1, w1) : 1;
+        const int c2 = L.act[2] ? small_kt<TW>(i2, nc2, L.k[2], I2, w2) : 1;
+        TW g = TW(0);
+        for (int a = 0; a < c0; ++a) {
+            TW gy = TW(0);
+            for (int b = 0; b < c1; ++b) {
+                const TW *fr = F + (I0[a] * nc1 + I1[b]) * nc2;
+                TW gx = TW(0);
+                for (int c = 0; c < c2; ++c) gx += w2[c] * fr[I2[c]];
+                gy += w1[b] * gx;
+            }
+            g += w0[a] * gy;
+        }
+        U[i0 * L.st[0] + i1 * L.st[1] + i2 * L.st[2]] += sg * g;
+    }
+}
+
+// Fine neighbours of coarse index E of a dimension with their Pi^T weights.
+template <typename TW>
+__device__ __forceinline__ int small_pt(int E, int n, const TW *w, int (&j)[3], TW (&wt)[3])
+{
+    int c = 0;
+    const int f = 2 * E;
+    if (f - 1 >= 1) { j[c] = f - 1; wt[c] = w[2 * (f - 1) + 1]; ++c; }
+    j[c] = f; wt[c] = TW(1); ++c;
+    if (f + 1 <= n - 2) { j[c] = f + 1; wt[c] = w[2 * (f + 1)]; ++c; }
+    return c;
+}
+
+// U(e) += sg (Pi^T U|_o)(e) at every node of N_{l-1} of level L (reads only
+// nodes of N_l \ N_{l-1}).
+template <typename TW>
+__device__ void small_adj_even(TW *U, const SmallLevel<TW> &L, TW sg)
+{
+    const int nc1 = L.nc[1], nc2 = L.nc[2];
+    const float rc1 = 1.0f / (float)nc1, rc2 = 1.0f / (float)nc2;
+    for (int e = threadIdx.x; e < L.nc[0] * nc1 * nc2; e += blockDim.x) {
+        const int r = small_div(e, rc2), E2 = e - r * nc2;
+        const int E0 = small_div(r, rc1), E1 = r - E0 * nc1;
+        int j0[3] = {0, 0, 0}, j1[3] = {0, 0, 0}, j2[3] = {0, 0, 0};
+        TW w0[3] = {TW(1), TW(0), TW(0)}, w1[3] = {TW(1), TW(0), TW(0)}, w2[3] = {TW(1), TW(0), TW(0)};
+        const int c0 = L.act[0] ? small_pt<TW>(E0, L.nf[0], L.w[0], j0, w0) : 1;
+        const int c1 = L.act[1] ? small_pt<TW>(E1, L.nf[1], L.w[1], j1, w1) : 1;
+        const int c2 = L.act[2] ? small_pt<TW>(E2, L.nf[2], L.w[2], j2, w2) : 1;
+        const int f0 = L.act[0] ? 2 * E0 : 0, f1 = L.act[1] ? 2 * E1 : 0, f2 = L.act[2] ? 2 * E2 : 0;
+        TW sum = TW(0);
+        for (int a = 0; a < c0; ++a)
+            for (int b = 0; b < c1; ++b)
+                for (int c = 0; c < c2; ++c) {
+                    if (j0[a] == f0 && j1[b] == f1 && j2[c] == f2) continue;  // the node itself
+                    sum += w0[a] * w1[b] * w2[c] * U[j0[a] * L.st[0] + j1[b] * L.st[1] + j2[c] * L.st[2]];
+                }
+        U[f0 * L.st[0] + f1 * L.st[1] + f2 * L.st[2]] += sg * sum;
+    }
+}
+
+// DIR 0: transpose of the decomposition; 1: of the recomposition.
+template <typename T, typename TW, int DIR>
+__device__ void small_adj_run(const SmallParams &p, unsigned char *smem_raw)
+{
+    TW *U = reinterpret_cast<TW *>(smem_raw);
+    const int n0 = p.n[0], n1 = p.n[1], n2 = p.n[2];
+    const int N = n0 * n1 * n2;
+    const int m0 = (n0 > 1) ? (n0 - 1) / 2 + 1 : 1;
+    const int m1 = (n1 > 1) ? (n1 - 1) / 2 + 1 : 1;
+    const int m2 = (n2 > 1) ? (n2 - 1) / 2 + 1 : 1;
+    TW *F = U + N;
+    TW *Tb = F + m0 * m1 * m2;
+    T *A = static_cast<T *>(p.A);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    int toffs[kSmallMaxLevels];
+    {
+        int toff = 0;
+        for (int i = 0; i < p.nlev; ++i) {
+            toffs[i] = toff;
+            const int n[3] = {n0, n1, n2};
+            for (int d = 0; d < 3; ++d) {
+                if (n[d] <= 1) continue;
+                const int nf = (n[d] - 1) / (1 << i) + 1, nc = (nf - 1) / 2 + 1;
+                const TW *gw = static_cast<const TW *>(p.w[i][d]);
+                const TW *gk = static_cast<const TW *>(p.k[i][d]);
+                const TW *gf = static_cast<const TW *>(p.fac[i][d]);
+                for (int e = tid; e < 2 * nf; e += nt) cp_async_elem<TW>(Tb + toff + e, gw + e, true);
+                for (int e = tid; e < 5 * nc; e += nt) cp_async_elem<TW>(Tb + toff + 2 * nf + e, gk + e, true);
+                for (int e = tid; e < 3 * nc; e += nt) cp_async_elem<TW>(Tb + toff + 2 * nf + 5 * nc + e, gf + e, true);
+                toff += 2 * nf + 8 * nc;
+            }
+        }
+    }
+    cp_async_commit();
+    for (int e = tid; e < N; e += nt) U[e] = static_cast<TW>(A[e]);
+    cp_async_wait<0>();
+    __syncthreads();
+
+    for (int it = 0; it < p.nlev; ++it) {
+        const int i = (DIR == 0) ? p.nlev - 1 - it : it;
+        const int s = 1 << i;
+        SmallLevel<TW> L;
+        const int n[3] = {n0, n1, n2};
+        const int st[3] = {n1 * n2, n2, 1};
+        int toff = toffs[i];
+        for (int d = 0; d < 3; ++d) {
+            L.act[d] = n[d] > 1 ? 1 : 0;
+            L.nf[d] = L.act[d] ? (n[d] - 1) / s + 1 : 1;
+            L.nc[d] = L.act[d] ? (L.nf[d] - 1) / 2 + 1 : 1;
+            L.st[d] = st[d] * s;
+            if (L.act[d]) {
+                L.w[d] = Tb + toff;
+                L.k[d] = Tb + toff + 2 * L.nf[d];
+                L.fac[d] = Tb + toff + 2 * L.nf[d] + 5 * L.nc[d];
+                toff += 2 * L.nf[d] + 8 * L.nc[d];
+            } else {
+                L.w[d] = L.k[d] = L.fac[d] = Tb;
+            }
+        }
+        if constexpr (DIR == 1) {
+            small_adj_even<TW>(U, L, TW(1));
+            __syncthreads();
+        }
+        small_gather_f<TW>(U, F, L);
+        __syncthreads();
+        small_solves<TW>(F, L);
+        small_adj_odd<TW>(U, F, L, DIR == 0 ? TW(1) : TW(-1));
+        __syncthreads();
+        if constexpr (DIR == 0) {
+            small_adj_even<TW>(U, L, TW(-1));
+            __syncthreads();
+        }
+    }
+
+    for (int e = tid; e < N; e += nt) A[e] = static_cast<T>(U[e]);
+}
+
+template <typename T, typename TW, int DIR>
+__global__ void __launch_bounds__(kSmallThreads, 1) k_small_adj(SmallParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    small_adj_run<T, TW, DIR>(p, smem_raw);
+}
+
 template <typename T, typename TW, int MODE>
 __global__ void __launch_bounds__(kSmallThreads, 1) k_small(SmallParams p)
 {

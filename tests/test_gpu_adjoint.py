@@ -45,6 +45,7 @@ def _relerr(got, want):
 
 CASES = [
     ((129, 129), "f64", -1, False),
+    ((129, 65, 65), "f32", -1, True),   # tiled finest level, then one block
     ((65,), "f32", -1, True),
     ((33, 65), "f32", -1, False),
     ((17, 33, 17), "f64", -1, True),
@@ -57,11 +58,16 @@ CASES = [
 
 @pytest.mark.parametrize("shape,dtype,nlevels,nonuniform", CASES)
 @pytest.mark.parametrize("which", ["decompose", "recompose"])
-def test_adjoint_matches_oracle(shape, dtype, nlevels, nonuniform, which):
+@pytest.mark.parametrize("tiled", [False, True])
+def test_adjoint_matches_oracle(shape, dtype, nlevels, nonuniform, which, tiled):
+    """tiled: every level with the per-level adjoint kernels (tuning parameter
+    3); else the levels that fit one block's shared memory run in one launch."""
     mg = _mg()
     coords = _rand_coords(shape, 21) if nonuniform else None
     y = np.random.default_rng(22).standard_normal(shape).astype(_np_dtype(dtype))
     plan = mg.Plan(shape, nlevels=nlevels, coords=coords, dtype=dtype)
+    if tiled:
+        plan.tune(0, 3, 1)
     t = torch.from_numpy(y).cuda()
     getattr(plan, f"{which}_adjoint")(t)
     torch.cuda.synchronize()
