@@ -7,6 +7,7 @@ from .oracle import (  # noqa: F401
     build,
     decompose,
     recompose,
+    recompose_classes,
     decompose_adjoint,
     recompose_adjoint,
     line_mass,

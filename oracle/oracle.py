@@ -102,6 +102,25 @@ def recompose(u, nlevels=None, coords=None):
     return _run("orc_recompose", u, nlevels, coords)
 
 
+def recompose_classes(u, nclasses, nlevels=None, coords=None):
+    """Recomposition from the first ``nclasses`` coefficient classes
+    (Section I, Fig. 1: an approximation is rebuilt from a chosen number of
+    classes; Section II-A, overall process: the omitted coefficients are left
+    out of the recomposition).  Class 0 is the coarsest nodal values on N_0,
+    class l the level-l coefficients on N_l \\ N_{l-1}.  Leaving a class out
+    means its coefficients are zero: every node outside N_{nclasses-1} is set
+    to zero and the full recomposition runs.  1 <= nclasses <= L + 1."""
+    u = np.array(u, dtype=np.float64, order="C", copy=True)
+    L = max_levels(u.shape) if nlevels is None or nlevels < 0 else int(nlevels)
+    if not 1 <= int(nclasses) <= L + 1:
+        raise ValueError(f"nclasses must be in 1..{L + 1}")
+    stride = 1 << (L - (int(nclasses) - 1))
+    kept = np.zeros(u.shape, dtype=bool)
+    kept[np.ix_(*[np.arange(0, n, stride) for n in u.shape])] = True
+    u[~kept] = 0.0
+    return recompose(u, L, coords)
+
+
 def decompose_adjoint(u, nlevels=None, coords=None):
     """Transpose of the linear map ``decompose``."""
     return _run("orc_decompose_adjoint", u, nlevels, coords)

@@ -306,3 +306,74 @@ def test_thomas_matches_dense_solve(n):
     M = _line_matrix(oracle.line_mass, n, n, x)
     z = oracle.line_mass_solve(x, f)
     np.testing.assert_allclose(z, np.linalg.solve(M, f), rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------- coefficient classes
+
+def _on_finest(q, coords, L, k):
+    """Finest-grid nodal values of the V_k function with nodal values q on N_k
+    (tensor product of 1D hat-function evaluations)."""
+    B = np.ones((1, 1))
+    for x in coords:
+        B = np.kron(B, dense.hat_values(x, x[dense.level_index(len(x), L, k)]))
+    return (B @ q.reshape(-1)).reshape([len(x) for x in coords])
+
+
+@pytest.mark.parametrize("shape", [(33,), (17, 9), (9, 9, 9), (5, 9, 17)])
+@pytest.mark.parametrize("uniform", [True, False])
+def test_classes_give_projections(shape, uniform):
+    """Keeping the first k+1 classes rebuilds Q_k u, the L2 projection onto
+    V_k (u = Q_0 u + sum_l (Q_l - Q_{l-1}) u, each class one term), from
+    dense Gram systems; all L+1 classes give u back."""
+    rng = np.random.default_rng(21)
+    coords = ([oracle.uniform_coords(n) for n in shape] if uniform
+              else _rand_coords(rng, shape))
+    L = oracle.max_levels(shape)
+    u = rng.standard_normal(shape)
+    dec = oracle.decompose(u, coords=coords)
+    for nc in range(1, L + 2):
+        got = oracle.recompose_classes(dec, nc, coords=coords)
+        want = _on_finest(dense.projection(u, coords, L, nc - 1), coords, L, nc - 1)
+        assert _relmax(got, want) < 1e-11, nc
+
+
+@pytest.mark.parametrize("shape,k", [((33,), 2), ((17, 9), 1), ((9, 9, 17), 2), ((17, 17, 9), 0)])
+def test_classes_reproduce_level_k_functions(shape, k):
+    """A function of V_k is its own projection: its first k+1 classes
+    rebuild it, non-uniform spacing included."""
+    rng = np.random.default_rng(5)
+    coords = _rand_coords(rng, shape)
+    L = oracle.max_levels(shape)
+    q = rng.standard_normal([len(dense.level_index(n, L, k)) for n in shape])
+    u = _on_finest(q, coords, L, k)
+    got = oracle.recompose_classes(oracle.decompose(u, coords=coords), k + 1, coords=coords)
+    assert _relmax(got, u) < 1e-12
+
+
+def test_classes_error_is_monotone():
+    """V_0 in V_1 in ... in V_L, and Q_k is the best approximation in V_k
+    in the L2 norm, so the L2 error of the rebuilt field never grows with
+    the number of classes kept and reaches zero with all of them."""
+    rng = np.random.default_rng(8)
+    shape = (9, 17, 9)
+    coords = _rand_coords(rng, shape)
+    L = oracle.max_levels(shape)
+    G = np.ones((1, 1))
+    for x in coords:
+        G = np.kron(G, dense.gram_1d(x))
+    u = rng.standard_normal(shape)
+    dec = oracle.decompose(u, coords=coords)
+    errs = []
+    for nc in range(1, L + 2):
+        e = (u - oracle.recompose_classes(dec, nc, coords=coords)).reshape(-1)
+        errs.append(float(e @ G @ e))
+    assert all(b <= a * (1 + 1e-12) + 1e-24 for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-24 and errs[0] > 1e-3
+
+
+def test_classes_argument_range():
+    u = np.zeros((9, 9))
+    with pytest.raises(ValueError):
+        oracle.recompose_classes(u, 0)
+    with pytest.raises(ValueError):
+        oracle.recompose_classes(u, oracle.max_levels(u.shape) + 2)
