@@ -39,7 +39,7 @@ N_MODES = 12
 E2E_LANES = 3  # fields in flight in the end-to-end leg (2: 394, 3: 440, 4: 449 GB/s measured)
 SEED = 2
 KIND_NAMES = {0: "restrict_dec", 1: "restrict_rec", 2: "solve", 3: "solve_fused", 8: "small", 9: "multi",
-              4: "coef", 5: "interp", 6: "scatter"}
+              4: "coef", 5: "interp", 6: "scatter", 7: "adjoint", 10: "prolong"}
 
 
 def level_nodes(shape, L):
@@ -317,6 +317,57 @@ def run_adjoint(torch, mgard, synth, dev, stream, rank):
     return out
 
 
+def run_progressive(torch, mgard, plan, u, ws, stream, peak):
+    """Recomposition of the 513^3 FP32 field from its first L and L-1
+    coefficient classes (the finest one or two classes left out) against the
+    full recomposition.  Every call starts from the decomposed field,
+    restored by a device copy outside the call's events (median of 7).  The
+    kernel that writes the finest grid (k_prolong) is timed by the plan's
+    event pairs against the HBM roofline: it writes every finest node and
+    reads the level-k values once."""
+    import numpy as np
+
+    L, S = plan.levels, 4
+    plan.decompose(u, ws, stream)
+    coef = u.clone()
+
+    def median_call(fn, reps=7):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            u.copy_(coef)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sorted(a.elapsed_time(b) for a, b in ev)[reps // 2]
+
+    for _ in range(3):
+        u.copy_(coef)
+        plan.recompose_classes(u, L, ws, stream)
+    full = median_call(lambda: plan.recompose(u, ws, stream))
+    rows = []
+    for nc in (L, L - 1):
+        ms = median_call(lambda: plan.recompose_classes(u, nc, ws, stream))
+        mgard.mgard_profile_enable(plan.handle, 1)
+        mgard.mgard_profile_read(plan.handle)
+        median_call(lambda: plan.recompose_classes(u, nc, ws, stream), 3)
+        prof = mgard.mgard_profile_read(plan.handle)
+        mgard.mgard_profile_enable(plan.handle, 0)
+        c, t = [(c, t) for k, lv, c, t in prof if k == 10][0]
+        D = L + 1 - nc
+        kb = int(np.prod(SHAPE)) * S + level_nodes(SHAPE, L)[D] * S
+        per = t / c
+        rows.append({"nclasses": nc, "dropped_levels": D, "ms": ms, "speedup_vs_full_recompose": full / ms,
+                     "prolong_ms": per, "prolong_bytes": kb, "prolong_gbs": kb / (per / 1e3) / 1e9,
+                     "prolong_frac_of_measured_hbm": kb / (per / 1e3) / 1e9 / peak})
+    u.copy_(coef)
+    plan.recompose(u, ws, stream)
+    torch.cuda.synchronize()
+    del coef
+    return {"workload": "513^3 FP32 recomposition from the first L and L-1 of L+1 coefficient classes",
+            "full_recompose_ms": full, "runs": rows}
+
+
 def run_mixed(torch, mgard, synth, dev, stream, rank, max_over_ranks):
     """1025 x 1025 x 513 FP32 field (12 modes + Gaussian blob), FP64 solves and
     coarse-level accumulation, 9 levels."""
@@ -349,6 +400,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-progressive", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -535,6 +587,7 @@ def main():
                     "pass_model_peak_gbs": peak / 8.43,
                     "decompose_frac_of_pass_model": in_bytes / (t_dec / 1e3) / 1e9 / (peak / 8.43)}
 
+    progressive = None if args.no_progressive else run_progressive(torch, mgard, plan, u, ws, stream, peak)
     batched = None if args.no_batch else run_batched(torch, mgard, synth, dev, stream, rank)
     mixed = None if args.no_mixed else run_mixed(torch, mgard, synth, dev, stream, rank, max_over_ranks)
     adjoint = None if args.no_adjoint else run_adjoint(torch, mgard, synth, dev, stream, rank)
@@ -561,6 +614,7 @@ def main():
             "mixed": mixed,
             "batched": batched,
             "adjoint": adjoint,
+            "progressive": progressive,
             "paper_metric": paper_metric,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -112,6 +112,20 @@ MGARD_API mgard_status mgard_decompose(const mgard_plan *plan, void *d_data, voi
 MGARD_API mgard_status mgard_recompose(const mgard_plan *plan, void *d_data, void *d_ws,
                              size_t ws_bytes, void *stream);
 
+/* Recomposition from the first `nclasses` coefficient classes, in place
+ * (Section I, Fig. 1: a field is rebuilt to a chosen fidelity from a number
+ * of coefficient classes; Section II-A, overall process: the omitted
+ * coefficients are left out of the recomposition).  Class 0 is the coarsest
+ * values on N_0, class l the level-l coefficients on N_l \ N_{l-1}; the
+ * classes l >= nclasses are treated as zero (what their nodes of d_data
+ * hold does not affect the result).  On return every node of d_data holds the rebuilt field, which is
+ * the L2 projection Q_k u of the decomposed field onto V_k, k = nclasses-1,
+ * evaluated on the finest grid; nclasses = L + 1 is mgard_recompose.
+ *   nclasses  1 .. L + 1 (MGARD_ERR_INVALID_ARG otherwise)
+ *   d_data, d_ws, ws_bytes, stream as for mgard_decompose. */
+MGARD_API mgard_status mgard_recompose_classes(const mgard_plan *plan, int nclasses, void *d_data,
+                                               void *d_ws, size_t ws_bytes, void *stream);
+
 /* Launch-shape tuning of one level (step j = 0 is the finest level L).
  * Params 0-2 change only tile shapes and kernel variants, not the result.
  *   param 0  restriction tile: 0 = 8 x 64, 1 = 4 x 64, 2 = 16 x 64 coarse nodes per

@@ -3,6 +3,7 @@
 // layout and the level loops of decomposition and recomposition
 // (Section II-A, Eq. 1-2; Section III-B, program structure).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -100,6 +101,10 @@ struct mgard_plan {
     int coop_hcap = 0;
     size_t coop_bar_off = 0;
     std::vector<size_t> coop_g_off;   // per grid level: G (n0 x m1 x m2)
+    // recomposition from the first coefficient classes: per count D = 1..L of
+    // dropped levels (index D - 1) and dim, the table of the weight of every
+    // finest node's right N_{L-D} neighbour
+    std::vector<std::array<int64_t, 3>> pro_off;
     // kernel timing (measurement support): event pairs around the launches of
     // the prof_levels finest levels
     struct ProfRec {
@@ -213,7 +218,7 @@ void adj_select(mgard_plan *P)
 
 enum { KIND_RESTRICT_DEC = 0, KIND_RESTRICT_REC = 1, KIND_SOLVE = 2, KIND_SOLVE_FUSED = 3,
        KIND_PLACE = 4, KIND_INTERP = 5, KIND_PLACE_EVEN = 6, KIND_ADJ = 7, KIND_SMALL = 8,
-       KIND_MULTI = 9 };
+       KIND_MULTI = 9, KIND_PROLONG = 10 };
 
 cudaEvent_t prof_event(const mgard_plan *P)
 {
@@ -333,11 +338,13 @@ cudaError_t run_interp_level(const mgard_plan *P, int j, void *A, char *ws, cuda
 }
 
 // Levels small_j .. L-1 in one block, on the array of level small_j (the
-// user array when small_j = 0, else V_{small_j - 1}).
+// user array when small_j = 0, else V_{small_j - 1}); `first` > small_j
+// starts at a smaller array, which the shared memory sized for level
+// small_j also holds.
 template <typename T, typename TW>
-cudaError_t run_small(const mgard_plan *P, int mode, void *A, cudaStream_t st, int adjoint = -1)
+cudaError_t run_small(const mgard_plan *P, int mode, void *A, cudaStream_t st, int adjoint = -1, int first = -1)
 {
-    const int j0 = (adjoint >= 0) ? P->adj_j : P->small_j;
+    const int j0 = (adjoint >= 0) ? P->adj_j : (first >= 0 ? first : P->small_j);
     const int64_t *n = (j0 == 0) ? P->n : P->lv[j0 - 1].m;
     SmallParams sp;
     sp.A = A;
@@ -447,14 +454,16 @@ mgard_status exec_decompose(const mgard_plan *P, void *data, char *ws, cudaStrea
 
 // Recomposition, levels 1..L: first every level's load vector F_j and the
 // gathered coarse array V_j (both depend only on stored coefficients), then
-// coarsest first: correction solve with V_j -= z, then interpolation.
+// coarsest first: correction solve with V_j -= z, then interpolation.  With
+// D > 0 only steps D .. L-1 run, on the level array V_{D-1} (already
+// gathered), which ends up holding the recomposed level-(L-D) values.
 template <typename TU, typename TW>
-mgard_status exec_recompose(const mgard_plan *P, void *data, char *ws, cudaStream_t st, bool allow_coop)
+mgard_status exec_recompose(const mgard_plan *P, void *data, char *ws, cudaStream_t st, bool allow_coop, int D = 0)
 {
     cudaError_t err;
-    const bool coop = allow_coop && P->coop_j < P->L;
-    const int J = coop ? P->coop_j : P->small_j;
-    for (int j = 0; j < J; ++j) {
+    const bool coop = allow_coop && P->coop_j < P->L && D <= P->coop_j;
+    const int J = coop ? P->coop_j : std::max(P->small_j, D);
+    for (int j = D; j < J; ++j) {
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
         err = (j == 0) ? run_restrict_level<TU, TW>(P, j, MODE_REC, A, ws, st)
                        : run_restrict_level<TW, TW>(P, j, MODE_REC, A, ws, st);
@@ -465,16 +474,60 @@ mgard_status exec_recompose(const mgard_plan *P, void *data, char *ws, cudaStrea
         if (err != cudaSuccess) return cuda_fail(err, "recompose: cooperative coarse-level kernel");
     } else if (J < P->L) {
         void *A = (J == 0) ? data : (void *)(ws + P->lv[J - 1].v_off);
-        err = (J == 0) ? run_small<TU, TW>(P, MODE_REC, A, st) : run_small<TW, TW>(P, MODE_REC, A, st);
+        err = (J == 0) ? run_small<TU, TW>(P, MODE_REC, A, st, -1, J) : run_small<TW, TW>(P, MODE_REC, A, st, -1, J);
         if (err != cudaSuccess) return cuda_fail(err, "recompose: single-block coarse-level kernel");
     }
-    for (int j = J - 1; j >= 0; --j) {
+    for (int j = J - 1; j >= D; --j) {
         err = run_solves<TW>(P, j, -1, ws, st);
         if (err != cudaSuccess) return cuda_fail(err, "recompose: correction solve kernel");
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
         err = (j == 0) ? run_interp_level<TU, TW>(P, j, A, ws, st) : run_interp_level<TW, TW>(P, j, A, ws, st);
         if (err != cudaSuccess) return cuda_fail(err, "recompose: interpolation kernel");
     }
+    return MGARD_OK;
+}
+
+template <typename TU, typename TW>
+cudaError_t run_prolong(const mgard_plan *P, int D, void *data, char *ws, cudaStream_t st)
+{
+    const int64_t *m = P->lv[D - 1].m;
+    ProlongParams p;
+    p.out = data;
+    p.V = ws + P->lv[D - 1].v_off;
+    p.w0 = tab_ptr<TW>(P, P->pro_off[D - 1][0]);
+    p.w1 = tab_ptr<TW>(P, P->pro_off[D - 1][1]);
+    p.w2 = tab_ptr<TW>(P, P->pro_off[D - 1][2]);
+    p.n0 = (int)P->n[0]; p.n1 = (int)P->n[1]; p.n2 = (int)P->n[2];
+    p.m0 = (int)m[0]; p.m1 = (int)m[1]; p.m2 = (int)m[2];
+    p.shift = D;
+    p.seg = 0;
+    return timed(P, KIND_PROLONG, 0, st, [&] { return launch_prolong<TU, TW>(p, P->num_sms, st); });
+}
+
+template <typename T, typename TW>
+cudaError_t run_gather(const mgard_plan *P, int j, void *A, char *ws, cudaStream_t st);
+
+// Recomposition from the first L + 1 - D coefficient classes (Section I,
+// Fig. 1; Section II-A, overall process): the classes of the D finest levels
+// are left out, i.e. their coefficients are zero.  The coarse nodes are
+// gathered down to N_{L-D} (the dropped coefficients are never read), levels
+// 1 .. L-D recompose as usual into V_{D-1}, and with zero coefficients the
+// remaining D steps are pure interpolation, done in one pass onto the
+// finest array.
+template <typename TU, typename TW>
+mgard_status exec_recompose_classes(const mgard_plan *P, void *data, char *ws, cudaStream_t st, int D)
+{
+    if (D == 0) return exec_recompose<TU, TW>(P, data, ws, st, true);
+    cudaError_t err;
+    for (int j = 0; j < D; ++j) {
+        void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
+        err = (j == 0) ? run_gather<TU, TW>(P, j, A, ws, st) : run_gather<TW, TW>(P, j, A, ws, st);
+        if (err != cudaSuccess) return cuda_fail(err, "recompose_classes: gather kernel");
+    }
+    const mgard_status s = exec_recompose<TU, TW>(P, data, ws, st, true, D);
+    if (s != MGARD_OK) return s;
+    err = run_prolong<TU, TW>(P, D, data, ws, st);
+    if (err != cudaSuccess) return cuda_fail(err, "recompose_classes: interpolation kernel");
     return MGARD_OK;
 }
 
@@ -820,6 +873,20 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
     }
     P->ws_bytes = ws;
 
+    // weight of the right N_{L-D} neighbour of every finest node (0 on
+    // N_{L-D} itself), D = 1..L, from the coordinates
+    P->pro_off.assign(L, std::array<int64_t, 3>{0, 0, 0});
+    for (int D = 1; D <= L; ++D) {
+        const int64_t s = int64_t(1) << D;
+        for (int k = 0; k < nd; ++k) {
+            P->pro_off[D - 1][3 - nd + k] = (int64_t)tab.size();
+            for (int64_t i = 0; i < n[k]; ++i) {
+                const int64_t a = i / s * s;
+                tab.push_back(i == a ? 0.0 : (x[k][i] - x[k][a]) / (x[k][a + s] - x[k][a]));
+            }
+        }
+    }
+
     // the finest level whose array the single-block kernel takes
     P->small_auto = L;
     for (int j = 0; j < L; ++j) {
@@ -1109,6 +1176,23 @@ mgard_status mgard_decompose(const mgard_plan *P, void *d_data, void *d_ws, size
 mgard_status mgard_recompose(const mgard_plan *P, void *d_data, void *d_ws, size_t ws_bytes, void *stream)
 {
     return mg_transform(P, 1, d_data, d_ws, ws_bytes, static_cast<cudaStream_t>(stream), true);
+}
+
+mgard_status mgard_recompose_classes(const mgard_plan *P, int nclasses, void *d_data, void *d_ws, size_t ws_bytes,
+                                     void *stream)
+{
+    mgard_status s = check_call(P, d_data, d_ws, ws_bytes);
+    if (s != MGARD_OK) return s;
+    if (nclasses < 1 || nclasses > P->L + 1)
+        return fail(MGARD_ERR_INVALID_ARG, "recompose_classes: nclasses must be in 1.." + std::to_string(P->L + 1));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(d_ws);
+    const int D = P->L + 1 - nclasses;
+    switch (P->dtype) {
+    case MGARD_F32: return exec_recompose_classes<float, float>(P, d_data, ws, st, D);
+    case MGARD_F64: return exec_recompose_classes<double, double>(P, d_data, ws, st, D);
+    default: return exec_recompose_classes<float, double>(P, d_data, ws, st, D);
+    }
 }
 
 mgard_status mgard_decompose_adjoint(const mgard_plan *P, void *d_data, void *d_ws, size_t ws_bytes, void *stream)

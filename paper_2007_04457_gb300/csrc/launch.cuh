@@ -82,4 +82,9 @@ cudaError_t launch_adj_odd(int act, const AdjParams &p, cudaStream_t st);
 template <typename T, typename TW>
 cudaError_t launch_adj_even(int act, const AdjParams &p, cudaStream_t st);
 
+// Finest-grid values of a level-k function from its compact values
+// (prolong.cuh); p.shift >= 1, p.seg is set here.
+template <typename T, typename TW>
+cudaError_t launch_prolong(const ProlongParams &p, int num_sms, cudaStream_t st);
+
 }  // namespace mg

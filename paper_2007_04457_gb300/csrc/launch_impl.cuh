@@ -8,6 +8,7 @@
 #include "interp.cuh"
 #include "launch.cuh"
 #include "multi.cuh"
+#include "prolong.cuh"
 #include "restrict.cuh"
 #include "restrict_strip.cuh"
 #include "small.cuh"
@@ -408,6 +409,22 @@ cudaError_t launch_multi(int mode, const MultiParams &p, int grid, size_t smem, 
     return cudaLaunchKernelEx(&cfg, fn, p);
 }
 
+template <typename T, typename TW>
+cudaError_t launch_prolong(const ProlongParams &p, int num_sms, cudaStream_t st)
+{
+    if (p.shift < 1 || p.n0 < 1 || p.n1 < 1 || p.n2 < 1) return cudaErrorInvalidValue;
+    ProlongParams q = p;
+    const int64_t rows = (int64_t)p.n0 * p.n1;
+    const int64_t warps = (int64_t)num_sms * kProlongBlocksPerSm * (kProlongThreads / 32);
+    // whole rows per work item when there are enough rows, else 256 nodes
+    q.seg = (rows >= 4 * warps) ? (p.n2 + 31) / 32 * 32 : 256;
+    const int64_t items = rows * ((p.n2 + q.seg - 1) / q.seg);
+    const int64_t need = (items + kProlongThreads / 32 - 1) / (kProlongThreads / 32);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms * kProlongBlocksPerSm));
+    k_prolong<T, TW><<<(unsigned)grid, kProlongThreads, 0, st>>>(q);
+    return cudaGetLastError();
+}
+
 #define MG_INSTANTIATE_LEVEL(T, TW)                                                              \
     template cudaError_t restrict_shape<T, TW>(int, int, int, RestrictShape *);                  \
     template cudaError_t launch_restrict<T, TW>(int, int, int, const RestrictParams &, int,     \
@@ -421,7 +438,8 @@ cudaError_t launch_multi(int mode, const MultiParams &p, int grid, size_t smem, 
     template cudaError_t launch_small<T, TW>(int, const SmallParams &, size_t, cudaStream_t);    \
     template cudaError_t launch_small_adj<T, TW>(int, const SmallParams &, size_t, cudaStream_t); \
     template cudaError_t multi_occupancy<T, TW>(int, size_t, int *);                             \
-    template cudaError_t launch_multi<T, TW>(int, const MultiParams &, int, size_t, cudaStream_t);
+    template cudaError_t launch_multi<T, TW>(int, const MultiParams &, int, size_t, cudaStream_t); \
+    template cudaError_t launch_prolong<T, TW>(const ProlongParams &, int, cudaStream_t);
 
 #define MG_INSTANTIATE_SOLVE(TW) \
     template cudaError_t launch_solve<TW>(const SolveParams &, int, int, cudaStream_t);

@@ -69,4 +69,15 @@ struct AdjParams {
     int sign;                // +1 or -1
 };
 
+// Finest-grid values of a level-k function (prolong.cuh): multilinear
+// interpolation of compact level-k values onto every node of the finest grid.
+struct ProlongParams {
+    void *out;               // finest array (type T), n0 x n1 x n2
+    const void *V;           // level-k values (type TW), m0 x m1 x m2
+    const void *w0, *w1, *w2;  // per finest node: weight of its right level-k neighbour (TW)
+    int n0, n1, n2, m0, m1, m2;
+    int shift;               // finest index >> shift = left level-k neighbour (>= 1)
+    int seg;                 // nodes of a row per work item (a multiple of 32)
+};
+
 }  // namespace mg

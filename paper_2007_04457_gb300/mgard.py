@@ -53,6 +53,7 @@ def _load() -> ctypes.CDLL:
         "mgard_plan_launches": ([vp, ctypes.c_int], ctypes.c_int),
         "mgard_decompose": ([vp, vp, vp, sz, vp], ctypes.c_int),
         "mgard_recompose": ([vp, vp, vp, sz, vp], ctypes.c_int),
+        "mgard_recompose_classes": ([vp, ctypes.c_int, vp, vp, sz, vp], ctypes.c_int),
         "mgard_decompose_adjoint": ([vp, vp, vp, sz, vp], ctypes.c_int),
         "mgard_recompose_adjoint": ([vp, vp, vp, sz, vp], ctypes.c_int),
         "mgard_decompose_host": ([vp, vp, vp, vp, vp, sz, vp], ctypes.c_int),
@@ -132,6 +133,12 @@ def mgard_decompose(plan: int, d_data: int, d_ws: int, ws_bytes: int, stream: in
 
 def mgard_recompose(plan: int, d_data: int, d_ws: int, ws_bytes: int, stream: int) -> None:
     _check(LIB.mgard_recompose(plan, d_data, d_ws, ws_bytes, stream), "mgard_recompose")
+
+
+def mgard_recompose_classes(plan: int, nclasses: int, d_data: int, d_ws: int, ws_bytes: int,
+                            stream: int) -> None:
+    _check(LIB.mgard_recompose_classes(plan, nclasses, d_data, d_ws, ws_bytes, stream),
+           "mgard_recompose_classes")
 
 
 def mgard_decompose_adjoint(plan: int, d_data: int, d_ws: int, ws_bytes: int, stream: int) -> None:
@@ -261,6 +268,12 @@ class Plan:
     def recompose(self, data, workspace=None, stream=None):
         """In-place recomposition of a CUDA tensor; returns it."""
         mgard_recompose(self.handle, *self._args(data, workspace, stream))
+        return data
+
+    def recompose_classes(self, data, nclasses: int, workspace=None, stream=None):
+        """In place: rebuild the field from its first `nclasses` coefficient
+        classes (1 .. levels + 1; the finer classes count as zero)."""
+        mgard_recompose_classes(self.handle, int(nclasses), *self._args(data, workspace, stream))
         return data
 
     def decompose_adjoint(self, data, workspace=None, stream=None):

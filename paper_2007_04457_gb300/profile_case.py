@@ -1,10 +1,11 @@
 """Run decompose + recompose on a synthetic n^3 field, for use under a profiler.
 
-    python -m paper_2007_04457_gb300.profile_case [n] [dtype] [reps] [ndim]
+    python -m paper_2007_04457_gb300.profile_case [n] [dtype] [reps] [ndim] [nclasses]
 
 n: nodes per side (default 257), dtype: f32 | f64 | f32_mixed, reps: number of
-decompose + recompose pairs, ndim: 1, 2 or 3 (default 3).  Prints one line and
-exits 0; no timing is done here.
+decompose + recompose pairs, ndim: 1, 2 or 3 (default 3), nclasses: when
+given, each recomposition rebuilds from the first nclasses coefficient
+classes only.  Prints one line and exits 0; no timing is done here.
 """
 import sys
 
@@ -18,6 +19,7 @@ def main(argv):
     dtype = argv[2] if len(argv) > 2 else "f32"
     reps = int(argv[3]) if len(argv) > 3 else 2
     ndim = int(argv[4]) if len(argv) > 4 else 3
+    nclasses = int(argv[5]) if len(argv) > 5 else 0
     shape = (n,) * ndim
     plan = mgard.Plan(shape, dtype=dtype)
     tdt = torch.float64 if dtype == "f64" else torch.float32
@@ -25,9 +27,13 @@ def main(argv):
     ws = plan.workspace(u.device)
     for _ in range(reps):
         plan.decompose(u, ws)
-        plan.recompose(u, ws)
+        if nclasses > 0:
+            plan.recompose_classes(u, nclasses, ws)
+        else:
+            plan.recompose(u, ws)
     torch.cuda.synchronize()
-    print(f"profile_case ok: shape={shape} dtype={dtype} levels={plan.levels} reps={reps}")
+    print(f"profile_case ok: shape={shape} dtype={dtype} levels={plan.levels} reps={reps}"
+          + (f" nclasses={nclasses}" if nclasses > 0 else ""))
 
 
 if __name__ == "__main__":
