@@ -413,14 +413,20 @@ template <typename T, typename TW>
 cudaError_t launch_prolong(const ProlongParams &p, int num_sms, cudaStream_t st)
 {
     if (p.shift < 1 || p.n0 < 1 || p.n1 < 1 || p.n2 < 1) return cudaErrorInvalidValue;
+    // one wave of resident blocks (the grid-stride loop covers the rest)
+    int per_sm = 0;
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prolong<T, TW>, kProlongThreads, 0);
+    if (err != cudaSuccess) return err;
+    per_sm = std::max(1, std::min(per_sm, kProlongBlocksPerSm));
     ProlongParams q = p;
     const int64_t rows = (int64_t)p.n0 * p.n1;
-    const int64_t warps = (int64_t)num_sms * kProlongBlocksPerSm * (kProlongThreads / 32);
+    const int64_t warps = (int64_t)num_sms * per_sm * (kProlongThreads / 32);
     // whole rows per work item when there are enough rows, else 256 nodes
     q.seg = (rows >= 4 * warps) ? (p.n2 + 31) / 32 * 32 : 256;
     const int64_t items = rows * ((p.n2 + q.seg - 1) / q.seg);
+    if (items >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
     const int64_t need = (items + kProlongThreads / 32 - 1) / (kProlongThreads / 32);
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms * kProlongBlocksPerSm));
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms * per_sm));
     k_prolong<T, TW><<<(unsigned)grid, kProlongThreads, 0, st>>>(q);
     return cudaGetLastError();
 }
