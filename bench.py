@@ -84,10 +84,24 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+# Headers that hold nothing but the device code of other kernels: a change
+# there cannot alter the code, launch or memory traffic of a kernel defined
+# elsewhere.  Keys: the kernel names recorded in profiles/traffic.txt.
+_OWN_HEADER = {"coef": "sweep.cuh", "interp": "sweep.cuh", "prolong": "prolong.cuh"}
+_DEVICE_ONLY_HEADERS = ("adjoint.cuh", "multi.cuh", "prolong.cuh", "restrict.cuh", "restrict_strip.cuh",
+                        "small.cuh", "solve.cuh", "sweep.cuh")
+
+
+def kernel_source_hash(kernel=None):
+    """Hash of the library sources (all of them), or of those that define
+    one kernel: every source except the device-code headers of other
+    kernels."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2007_04457_gb300", "csrc")
+    own = _OWN_HEADER.get(kernel)
     for f in sorted(os.listdir(csrc)):
+        if kernel is not None and f in _DEVICE_ONLY_HEADERS and f != own:
+            continue
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
@@ -96,11 +110,11 @@ def kernel_source_hash():
 
 def recorded_traffic(kernel_name):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+    on the current sources of that kernel (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel_name not in _OWN_HEADER:
         return None
-    cur = kernel_source_hash()
+    cur = kernel_source_hash(kernel_name)
     for line in open(path):
         parts = line.split()
         if len(parts) >= 3 and parts[0] == kernel_name and parts[1] == cur:
