@@ -19,28 +19,22 @@ namespace mg {
 
 constexpr int kProlongThreads = 256;
 constexpr int kProlongBlocksPerSm = 8;
+constexpr int kProlongRows = 64;   // finest rows (dim 1) per work item
 
-// Work item = p.seg consecutive nodes of one finest row (i0, i1), handled by
-// one warp 32 nodes per step, two steps per iteration with the loads of both
-// issued first.  Per step every lane forms one coarse column of the row's
-// interpolant in dims 0 and 1 (four loads of V, which stays in L2: each
-// level-k row serves up to (2^(D+1) - 1)^2 finest rows, visited close
-// together), then takes the two columns that bracket its node from their
-// lanes by shuffles: with D >= 1, 32 consecutive nodes span at most 17
-// coarse columns.  A node on N_k gets weight 0 on its right neighbour, so
-// its value is copied exactly.
-template <typename TW>
-__device__ __forceinline__ TW prolong_col(const TW *r00, const TW *r01, const TW *r10, const TW *r11, int c,
-                                          TW a0, TW a1)
-{
-    const TW v00 = r00[c], v01 = r01[c], v10 = r10[c], v11 = r11[c];
-    const TW t0 = v00 + a1 * (v01 - v00);
-    const TW t1 = v10 + a1 * (v11 - v10);
-    return t0 + a0 * (t1 - t0);
-}
-
+// Work item = a strip of 32 finest columns x kProlongRows finest rows of one
+// plane i0, handled by one warp walking down the rows.  Lane L loads, per
+// level-k row, the dim-0 interpolant of coarse column (first column of the
+// strip >> D) + L (two loads of V; with D >= 1 a strip spans at most 17
+// coarse columns); the warp keeps the two level-k rows that bracket its
+// current row in registers and prefetches the next one, so a finest row
+// costs one interpolation in dim 1, two shuffles (the coarse columns left and
+// right of the lane's node), one in dim 2 and a store.  Consecutive warps
+// take neighbouring strips of the same rows, sharing their coarse rows in L1.
+// A node on N_k gets weight 0 on every right neighbour, so its value is
+// copied exactly.  The launch (launch_impl.cuh) sizes the grid to one wave
+// of resident blocks; the loop below covers every item whatever the grid.
 template <typename T, typename TW>
-__global__ void __launch_bounds__(kProlongThreads) k_prolong(ProlongParams p)
+__global__ void __launch_bounds__(kProlongThreads, sizeof(TW) == 4 ? kProlongBlocksPerSm : 5) k_prolong(ProlongParams p)
 {
     T *__restrict__ out = static_cast<T *>(p.out);
     const TW *__restrict__ V = static_cast<const TW *>(p.V);
@@ -48,39 +42,52 @@ __global__ void __launch_bounds__(kProlongThreads) k_prolong(ProlongParams p)
     const TW *__restrict__ w1 = static_cast<const TW *>(p.w1);
     const TW *__restrict__ w2 = static_cast<const TW *>(p.w2);
     const int lane = threadIdx.x & 31;
-    const int sh = p.shift, n2 = p.n2, m2 = p.m2;
-    const unsigned nseg = (unsigned)((n2 + p.seg - 1) / p.seg);
-    const unsigned items = (unsigned)p.n0 * (unsigned)p.n1 * nseg;  // < 2^31 (host check)
-    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (unsigned it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
-        const unsigned r = it / nseg;
-        const int xs = (int)(it - r * nseg) * p.seg;
-        const int xe = min(xs + p.seg, n2);
-        const int i0 = (int)(r / (unsigned)p.n1), i1 = (int)(r - (unsigned)i0 * (unsigned)p.n1);
-        const int c0 = i0 >> sh, c1 = i1 >> sh;
-        const int c0b = min(c0 + 1, p.m0 - 1), c1b = min(c1 + 1, p.m1 - 1);
-        const TW a0 = w0[i0], a1 = w1[i1];
-        const TW *r00 = V + ((int64_t)c0 * p.m1 + c1) * m2;
-        const TW *r01 = V + ((int64_t)c0 * p.m1 + c1b) * m2;
-        const TW *r10 = V + ((int64_t)c0b * p.m1 + c1) * m2;
-        const TW *r11 = V + ((int64_t)c0b * p.m1 + c1b) * m2;
-        T *orow = out + (int64_t)r * n2;
-        for (int x0 = xs; x0 < xe; x0 += 64) {
-            // second step of the pair: when it lies past the segment, its
-            // indexes collapse onto the last node (in bounds, not stored)
-            const int y0 = min(x0 + 32, n2 - 1);
-            const int cbA = x0 >> sh, cbB = y0 >> sh;
-            const int i2A = min(x0 + lane, n2 - 1), i2B = min(y0 + lane, n2 - 1);
-            const TW colA = prolong_col(r00, r01, r10, r11, min(cbA + lane, m2 - 1), a0, a1);
-            const TW colB = prolong_col(r00, r01, r10, r11, min(cbB + lane, m2 - 1), a0, a1);
-            const TW a2A = w2[i2A], a2B = w2[i2B];
-            const int clA = i2A >> sh, clB = i2B >> sh;
-            const TW lA = __shfl_sync(0xffffffffu, colA, clA - cbA);
-            const TW rA = __shfl_sync(0xffffffffu, colA, min(clA + 1, m2 - 1) - cbA);
-            const TW lB = __shfl_sync(0xffffffffu, colB, clB - cbB);
-            const TW rB = __shfl_sync(0xffffffffu, colB, min(clB + 1, m2 - 1) - cbB);
-            if (x0 + lane < xe) orow[i2A] = static_cast<T>(lA + a2A * (rA - lA));
-            if (x0 + 32 + lane < xe) orow[i2B] = static_cast<T>(lB + a2B * (rB - lB));
+    const int sh = p.shift, n1 = p.n1, n2 = p.n2, m1 = p.m1, m2 = p.m2;
+    const int64_t nstrip = (n2 + 31) / 32;
+    const int64_t per_plane = nstrip * ((n1 + kProlongRows - 1) / kProlongRows);
+    const int64_t items = (int64_t)p.n0 * per_plane;
+    const int64_t plane_m = (int64_t)m1 * m2;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
+        const int i0 = (int)(it / per_plane);
+        const int64_t rem = it - (int64_t)i0 * per_plane;
+        const int ch = (int)(rem / nstrip);
+        const int xs = (int)(rem - (int64_t)ch * nstrip) * 32;
+        const int x = xs + lane;
+        const int xc = min(x, n2 - 1);
+        const int cb = xs >> sh;
+        const int sl = (xc >> sh) - cb;                          // 0 .. 15
+        const int sr = min((xc >> sh) + 1, m2 - 1) - cb;         // 0 .. 16
+        const TW a2 = w2[xc];
+        const int c0 = i0 >> sh, c0b = min(c0 + 1, p.m0 - 1);
+        const TW a0 = w0[i0];
+        const int cc = min(cb + lane, m2 - 1);
+        const TW *P0 = V + (int64_t)c0 * plane_m + cc;
+        const TW *P1 = V + (int64_t)c0b * plane_m + cc;
+        const int ys = ch * kProlongRows, ye = min(ys + kProlongRows, n1);
+        int c1 = ys >> sh;
+        int cn = min(c1 + 1, m1 - 1);
+        const TW l0 = P0[(int64_t)c1 * m2], l1 = P1[(int64_t)c1 * m2];
+        const TW h0 = P0[(int64_t)cn * m2], h1 = P1[(int64_t)cn * m2];
+        cn = min(c1 + 2, m1 - 1);
+        TW q0 = P0[(int64_t)cn * m2], q1 = P1[(int64_t)cn * m2];   // the level-k row after `hi`
+        TW lo = l0 + a0 * (l1 - l0);
+        TW hi = h0 + a0 * (h1 - h0);
+        int64_t idx = ((int64_t)i0 * n1 + ys) * n2 + x;
+        for (int y = ys; y < ye; ++y, idx += n2) {
+            if ((y >> sh) != c1) {  // the warp moves on to the next level-k row
+                c1 = y >> sh;
+                lo = hi;
+                hi = q0 + a0 * (q1 - q0);
+                cn = min(c1 + 2, m1 - 1);
+                q0 = P0[(int64_t)cn * m2];
+                q1 = P1[(int64_t)cn * m2];
+            }
+            const TW a1 = w1[y];
+            const TW t = lo + a1 * (hi - lo);
+            const TW vl = __shfl_sync(0xffffffffu, t, sl);
+            const TW vr = __shfl_sync(0xffffffffu, t, sr);
+            if (x < n2) out[idx] = static_cast<T>(vl + a2 * (vr - vl));
         }
     }
 }
