@@ -74,6 +74,8 @@ def test_plan_create_rejects_bad_coordinates(lib):
 def test_null_arguments(lib):
     lib.mgard_decompose.restype = ctypes.c_int
     assert lib.mgard_decompose(None, None, None, 0, None) == 1
+    lib.mgard_recompose_classes.restype = ctypes.c_int
+    assert lib.mgard_recompose_classes(None, 1, None, None, 0, None) == 1
     lib.mgard_plan_destroy.restype = ctypes.c_int
     assert lib.mgard_plan_destroy(None) == 0
     lib.mgard_workspace_bytes.restype = ctypes.c_size_t
