@@ -183,6 +183,32 @@ def dist_setup():
     return world, rank, local
 
 
+def dist_barrier(world):
+    """Barrier over the ranks (no-op for one process)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def dist_max(x, world, device):
+    """Largest value of x over the ranks: the job's time is its slowest rank's.
+    `device` is where the reduction tensor lives (the GPU for NCCL, the CPU
+    for gloo)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbs(bytes_per_rank_step, steps, world, ms_max):
+    """Whole-job GB/s: every rank moves the same bytes per step on its own
+    field (weak scaling), in the time of the slowest rank."""
+    return world * bytes_per_rank_step * steps / (ms_max / 1e3) / 1e9
+
+
 def run_reference(args):
     """The oracle (plain FP64 CPU code) on the host cores, same metric."""
     world, rank, _ = dist_setup()
@@ -382,9 +408,9 @@ def run_progressive(torch, mgard, plan, u, ws, stream, peak):
             "full_recompose_ms": full, "runs": rows}
 
 
-def run_mixed(torch, mgard, synth, dev, stream, rank, max_over_ranks):
-    """1025 x 1025 x 513 FP32 field (12 modes + Gaussian blob), FP64 solves and
-    coarse-level accumulation, 9 levels."""
+def run_mixed(torch, mgard, synth, dev, stream, rank, world, max_over_ranks):
+    """1025 x 1025 x 513 FP32 field (12 modes + Gaussian blob) per rank, FP64
+    solves and coarse-level accumulation, 9 levels; whole-job GB/s."""
     shape = (1025, 1025, 513)
     plan = mgard.Plan(shape, dtype="f32_mixed")
     u = synth.sinusoid_field_torch(shape, 12, 3 + rank, dev, torch.float32, blob=True)
@@ -394,7 +420,7 @@ def run_mixed(torch, mgard, synth, dev, stream, rank, max_over_ranks):
         step()
     ms = max_over_ranks(_timed(torch, stream, step, 5))
     d, r = algorithmic_bytes(shape, plan.levels, 4)
-    out = {"value": (d + r) / (ms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": ms, "levels": plan.levels,
+    out = {"value": job_gbs(d + r, 1, world, ms), "unit": "GB/s", "ms_per_step": ms, "levels": plan.levels,
            "workload": "1025x1025x513 FP32 field, FP64 solves and coarse arrays"}
     del u, ws
     plan.close()
@@ -431,15 +457,10 @@ def main():
     dev = torch.device("cuda", local)
 
     def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+        dist_barrier(world)
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return dist_max(x, world, dev)
 
     plan = mgard.Plan(SHAPE, dtype="f32")
     L = plan.levels
@@ -476,7 +497,7 @@ def main():
     prof = [(KIND_NAMES[k], k, lv, c, t) for k, lv, c, t in mgard.mgard_profile_read(plan.handle)]
     mgard.mgard_profile_enable(plan.handle, 0)
 
-    value = world * (dec_b + rec_b) * args.steps / (ms / 1e3) / 1e9
+    value = job_gbs(dec_b + rec_b, args.steps, world, ms)
     peak, peak_src = measured_peak()
     top = max(prof, key=lambda r: r[4]) if prof else None
     roof = None
@@ -514,7 +535,7 @@ def main():
         torch.cuda.synchronize()
         ms64 = max_over_ranks(e0.elapsed_time(e1))
         d64, r64 = algorithmic_bytes(SHAPE, L, 8)
-        fp64 = {"value": world * (d64 + r64) * k64 / (ms64 / 1e3) / 1e9, "unit": "GB/s",
+        fp64 = {"value": job_gbs(d64 + r64, k64, world, ms64), "unit": "GB/s",
                 "ms_per_step": ms64 / k64, "steps": k64}
         del u64, ws64, plan64
         torch.cuda.empty_cache()
@@ -572,7 +593,7 @@ def main():
         torch.cuda.synchronize()
         mse = max_over_ranks(e0.elapsed_time(e1))
         err = float((lanes[(ke - 1) % E2E_LANES]["out"] - h_in).abs().max() / h_in.abs().max())
-        e2e = {"value": world * (dec_b + rec_b) * ke / (mse / 1e3) / 1e9, "unit": "GB/s",
+        e2e = {"value": job_gbs(dec_b + rec_b, ke, world, mse), "unit": "GB/s",
                "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes,
                "ms_per_step": mse / ke, "steps": ke, "fields_in_flight": E2E_LANES, "round_trip_rel_err": err}
 
@@ -603,7 +624,7 @@ def main():
 
     progressive = None if args.no_progressive else run_progressive(torch, mgard, plan, u, ws, stream, peak)
     batched = None if args.no_batch else run_batched(torch, mgard, synth, dev, stream, rank)
-    mixed = None if args.no_mixed else run_mixed(torch, mgard, synth, dev, stream, rank, max_over_ranks)
+    mixed = None if args.no_mixed else run_mixed(torch, mgard, synth, dev, stream, rank, world, max_over_ranks)
     adjoint = None if args.no_adjoint else run_adjoint(torch, mgard, synth, dev, stream, rank)
 
     cpu = None
