@@ -16,4 +16,9 @@ from .oracle import (  # noqa: F401
     line_mass_solve,
     uniform_coords,
     max_levels,
+    dim_levels,
+    decompose_per_dim,
+    recompose_per_dim,
+    decompose_adjoint_per_dim,
+    recompose_adjoint_per_dim,
 )

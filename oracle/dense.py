@@ -13,6 +13,9 @@ level recursion, no tridiagonal solve, no stencils.  It states the method
   G_l q_l = B_l^T G_L u.
 * The level-l coefficients are (I - Pi_{l-1}) Q_l u on N_l \\ N_{l-1}
   (Eq. 1); the coarsest nodes keep Q_0 u (Fig. 3 in-place layout).
+* With a level count per dimension (``levels``), dimension k's node set
+  stops thinning after levels[k] steps from the finest level; the spaces
+  stay nested tensor products and everything above applies unchanged.
 
 Gram matrices come from 2-point Gauss-Legendre quadrature of products of hat
 functions on each element (exact for these quadratics); hat-function values
@@ -24,9 +27,16 @@ from __future__ import annotations
 import numpy as np
 
 
-def level_index(n: int, L: int, l: int) -> np.ndarray:
-    """Finest-grid indices of the level-l nodes of a dimension with n nodes."""
-    return np.arange(0, n, 1 << (L - l))
+def level_index(n: int, L: int, l: int, Lk: int | None = None) -> np.ndarray:
+    """Finest-grid indices of the level-l nodes of a dimension with n nodes
+    (with Lk: a dimension that stops coarsening after Lk steps)."""
+    step = L - l if Lk is None else min(L - l, Lk)
+    return np.arange(0, n, 1 << step)
+
+
+def _indices(coords, L, l, levels):
+    return [level_index(len(x), L, l, None if levels is None else levels[k])
+            for k, x in enumerate(coords)]
 
 
 def gram_1d(x: np.ndarray) -> np.ndarray:
@@ -61,10 +71,10 @@ def _kron(mats):
     return out
 
 
-def projection(u: np.ndarray, coords, L: int, l: int) -> np.ndarray:
+def projection(u: np.ndarray, coords, L: int, l: int, levels=None) -> np.ndarray:
     """Nodal values of Q_l u on N_l (array of the level-l shape)."""
     G_L = _kron([gram_1d(x) for x in coords])
-    idx = [level_index(len(x), L, l) for x in coords]
+    idx = _indices(coords, L, l, levels)
     B = _kron([hat_values(x, x[i]) for x, i in zip(coords, idx)])
     G_l = _kron([gram_1d(x[i]) for x, i in zip(coords, idx)])
     rhs = B.T @ (G_L @ u.reshape(-1))
@@ -72,31 +82,33 @@ def projection(u: np.ndarray, coords, L: int, l: int) -> np.ndarray:
     return q.reshape([len(i) for i in idx])
 
 
-def interpolate_from_coarse(q_l: np.ndarray, coords, L: int, l: int) -> np.ndarray:
+def interpolate_from_coarse(q_l: np.ndarray, coords, L: int, l: int, levels=None) -> np.ndarray:
     """Pi_{l-1} q_l on N_l: multilinear interpolant of the N_{l-1} values."""
-    idx_f = [level_index(len(x), L, l) for x in coords]
-    idx_c = [level_index(len(x), L, l - 1) for x in coords]
+    idx_f = _indices(coords, L, l, levels)
+    idx_c = _indices(coords, L, l - 1, levels)
     Bs = [hat_values(x[f], x[c]) for x, f, c in zip(coords, idx_f, idx_c)]
-    coarse = q_l[tuple(np.ix_(*[np.arange(0, len(f), 2) for f in idx_f]))]
+    coarse = q_l[tuple(np.ix_(*[np.searchsorted(f, c) for f, c in zip(idx_f, idx_c)]))]
     return (_kron(Bs) @ coarse.reshape(-1)).reshape(q_l.shape)
 
 
-def decompose(u: np.ndarray, coords, L: int) -> np.ndarray:
-    """Full in-place decomposition array built from global projections."""
+def decompose(u: np.ndarray, coords, L: int, levels=None) -> np.ndarray:
+    """Full in-place decomposition array built from global projections
+    (``levels``: per-dimension level counts, L their maximum)."""
     u = np.asarray(u, dtype=np.float64)
     out = np.zeros_like(u)
     for l in range(L, 0, -1):
-        q = projection(u, coords, L, l)
-        c = q - interpolate_from_coarse(q, coords, L, l)
-        idx = [level_index(len(x), L, l) for x in coords]
+        q = projection(u, coords, L, l, levels)
+        c = q - interpolate_from_coarse(q, coords, L, l, levels)
+        idx = _indices(coords, L, l, levels)
+        idx_c = _indices(coords, L, l - 1, levels)
         sub = out[np.ix_(*idx)]
         odd = np.zeros(q.shape, dtype=bool)
         for k in range(u.ndim):
             shp = [1] * u.ndim
             shp[k] = q.shape[k]
-            odd = odd | (np.arange(q.shape[k]) % 2 == 1).reshape(shp)
+            odd = odd | (~np.isin(idx[k], idx_c[k])).reshape(shp)
         sub[odd] = c[odd]
         out[np.ix_(*idx)] = sub
-    idx0 = [level_index(len(x), L, 0) for x in coords]
-    out[np.ix_(*idx0)] = projection(u, coords, L, 0)
+    idx0 = _indices(coords, L, 0, levels)
+    out[np.ix_(*idx0)] = projection(u, coords, L, 0, levels)
     return out

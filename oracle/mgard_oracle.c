@@ -30,6 +30,15 @@
  *   - Dimensions are processed fastest-varying first (Section II-A, the
  *     "prescribed order"; the result does not depend on it in exact
  *     arithmetic).
+ *   - Per-dimension level counts (the *_per_dim entry points; the paper runs
+ *     equal sides only, Section IV): dimension k coarsens in the first L_k
+ *     steps from the finest level and keeps all its nodes after that, so a
+ *     short side stops early while the others go on (L = max_k L_k levels).
+ *     A dimension that does not coarsen in a step has P = I there: its nodes
+ *     are all "coarse", its interpolation is the identity and its factor of
+ *     the load vector is M alone, which the tensor-product solve with the
+ *     same M then undoes (the spaces stay nested tensor products, so Eq. 1-2
+ *     hold unchanged).  With every L_k = L this is exactly the plain map.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -182,7 +191,8 @@ typedef struct {
     shape_t coarse;               /* level-(l-1) nodes N_{l-1}             */
     double *xf[ORC_MAXD];         /* coordinates of N_l per dimension      */
     double *xc[ORC_MAXD];         /* coordinates of N_{l-1} per dimension  */
-    long stride;                  /* index stride of N_l in the full array */
+    long stride[ORC_MAXD];        /* index stride of N_l in the full array */
+    int coarsen[ORC_MAXD];        /* 1: the dimension coarsens in this step */
 } level_t;
 
 static void level_free(level_t *lv)
@@ -190,22 +200,26 @@ static void level_free(level_t *lv)
     for (int k = 0; k < ORC_MAXD; ++k) { free(lv->xf[k]); free(lv->xc[k]); lv->xf[k] = lv->xc[k] = NULL; }
 }
 
-/* Build level l (1 <= l <= L) of a grid with full shape s and coordinates x. */
-static int level_make(const shape_t *s, const double *const *x, int L, int l, level_t *lv)
+/* Build level l (1 <= l <= L) of a grid with full shape s and coordinates x;
+ * dimension k coarsens in the first Lk[k] steps from the finest level. */
+static int level_make(const shape_t *s, const double *const *x, const int *Lk, int L, int l, level_t *lv)
 {
     memset(lv, 0, sizeof(*lv));
-    lv->stride = 1L << (L - l);
+    const int step = L - l;   /* steps taken from the finest level */
     lv->fine.d = lv->coarse.d = s->d;
     for (int k = 0; k < s->d; ++k) {
-        long nf = (s->n[k] - 1) / lv->stride + 1;
-        long nc = (nf - 1) / 2 + 1;
+        lv->coarsen[k] = step < Lk[k];
+        lv->stride[k] = 1L << (step < Lk[k] ? step : Lk[k]);
+        long nf = (s->n[k] - 1) / lv->stride[k] + 1;
+        long nc = lv->coarsen[k] ? (nf - 1) / 2 + 1 : nf;
+        long cs = lv->coarsen[k] ? 2 : 1;
         lv->fine.n[k] = nf;
         lv->coarse.n[k] = nc;
         lv->xf[k] = (double *)malloc(sizeof(double) * (size_t)nf);
         lv->xc[k] = (double *)malloc(sizeof(double) * (size_t)nc);
         if (!lv->xf[k] || !lv->xc[k]) { level_free(lv); return ORC_ENOMEM; }
-        for (long i = 0; i < nf; ++i) lv->xf[k][i] = x[k][i * lv->stride];
-        for (long i = 0; i < nc; ++i) lv->xc[k][i] = lv->xf[k][2 * i];
+        for (long i = 0; i < nf; ++i) lv->xf[k][i] = x[k][i * lv->stride[k]];
+        for (long i = 0; i < nc; ++i) lv->xc[k][i] = lv->xf[k][cs * i];
     }
     return ORC_OK;
 }
@@ -223,19 +237,34 @@ static long ravel(const shape_t *s, const long *ix)
     return idx;
 }
 
-static int all_even(const shape_t *s, const long *ix)
+/* Is level index i of dimension k on the coarse grid of the step? */
+static int coarse_in_dim(const level_t *lv, int k, long i)
 {
-    for (int k = 0; k < s->d; ++k) if (ix[k] % 2) return 0;
+    return !lv->coarsen[k] || i % 2 == 0;
+}
+
+/* Is the level-l node ix in N_{l-1}? */
+static int is_coarse(const level_t *lv, const long *ix)
+{
+    for (int k = 0; k < lv->fine.d; ++k) if (!coarse_in_dim(lv, k, ix[k])) return 0;
     return 1;
 }
 
-/* Copy the level-l nodes (index stride lv->stride) between u and v. */
+/* Index in the coarse array of a node of N_{l-1} given by its level index. */
+static long coarse_at(const level_t *lv, const long *ix)
+{
+    long cx[ORC_MAXD];
+    for (int k = 0; k < lv->fine.d; ++k) cx[k] = lv->coarsen[k] ? ix[k] / 2 : ix[k];
+    return ravel(&lv->coarse, cx);
+}
+
+/* Copy the level-l nodes (index strides lv->stride) between u and v. */
 static void level_gather(const shape_t *full, const level_t *lv, const double *u, double *v)
 {
     long m = shape_size(&lv->fine), ix[ORC_MAXD], gx[ORC_MAXD];
     for (long i = 0; i < m; ++i) {
         unravel(&lv->fine, i, ix);
-        for (int k = 0; k < full->d; ++k) gx[k] = ix[k] * lv->stride;
+        for (int k = 0; k < full->d; ++k) gx[k] = ix[k] * lv->stride[k];
         v[i] = u[ravel(full, gx)];
     }
 }
@@ -245,7 +274,7 @@ static void level_scatter(const shape_t *full, const level_t *lv, const double *
     long m = shape_size(&lv->fine), ix[ORC_MAXD], gx[ORC_MAXD];
     for (long i = 0; i < m; ++i) {
         unravel(&lv->fine, i, ix);
-        for (int k = 0; k < full->d; ++k) gx[k] = ix[k] * lv->stride;
+        for (int k = 0; k < full->d; ++k) gx[k] = ix[k] * lv->stride[k];
         u[ravel(full, gx)] = v[i];
     }
 }
@@ -263,7 +292,7 @@ static double interp_at(const level_t *lv, const double *v, const long *ix)
         int skip = 0;
         for (int k = 0; k < d; ++k) {
             int right = (combo >> k) & 1;
-            if (ix[k] % 2 == 0) {
+            if (coarse_in_dim(lv, k, ix[k])) {
                 if (right) { skip = 1; break; }   /* even dimension: one corner */
                 cx[k] = ix[k];
             } else {
@@ -293,7 +322,10 @@ static int load_vector(const level_t *lv, const double *C, double *f)
     for (int k = cur.d - 1; k >= 0 && rc == ORC_OK; --k) {
         rc = apply_along(&cur, k, cur.n[k], OP_MASS, lv->xf[k], a, b);
         if (rc != ORC_OK) break;
-        rc = apply_along(&cur, k, lv->coarse.n[k], OP_RESTRICT, lv->xf[k], b, a);
+        if (lv->coarsen[k])
+            rc = apply_along(&cur, k, lv->coarse.n[k], OP_RESTRICT, lv->xf[k], b, a);
+        else  /* P = I along a dimension that does not coarsen */
+            memcpy(a, b, sizeof(double) * (size_t)shape_size(&cur));
         cur.n[k] = lv->coarse.n[k];
     }
     if (rc == ORC_OK) memcpy(f, a, sizeof(double) * (size_t)shape_size(&lv->coarse));
@@ -329,7 +361,10 @@ static int mass_prolong(const level_t *lv, const double *z, double *C)
     memcpy(a, z, sizeof(double) * (size_t)shape_size(&lv->coarse));
     int rc = ORC_OK;
     for (int k = cur.d - 1; k >= 0 && rc == ORC_OK; --k) {
-        rc = apply_along(&cur, k, lv->fine.n[k], OP_PROLONG, lv->xf[k], a, b);
+        if (lv->coarsen[k])
+            rc = apply_along(&cur, k, lv->fine.n[k], OP_PROLONG, lv->xf[k], a, b);
+        else  /* P = I along a dimension that does not coarsen */
+            memcpy(b, a, sizeof(double) * (size_t)shape_size(&cur));
         cur.n[k] = lv->fine.n[k];
         if (rc != ORC_OK) break;
         rc = apply_along(&cur, k, cur.n[k], OP_MASS, lv->xf[k], b, a);
@@ -357,17 +392,15 @@ static int level_decompose(const level_t *lv, double *v)
     if (!C || !f) { free(C); free(f); return ORC_ENOMEM; }
     for (long i = 0; i < m; ++i) {
         unravel(&lv->fine, i, ix);
-        C[i] = all_even(&lv->fine, ix) ? 0.0 : v[i] - interp_at(lv, v, ix);
+        C[i] = is_coarse(lv, ix) ? 0.0 : v[i] - interp_at(lv, v, ix);
     }
     int rc = load_vector(lv, C, f);
     if (rc == ORC_OK) rc = coarse_solve(lv, f);
     if (rc == ORC_OK) {
         for (long i = 0; i < m; ++i) {
             unravel(&lv->fine, i, ix);
-            if (all_even(&lv->fine, ix)) {
-                long cx[ORC_MAXD];
-                for (int k = 0; k < lv->fine.d; ++k) cx[k] = ix[k] / 2;
-                v[i] += f[ravel(&lv->coarse, cx)];
+            if (is_coarse(lv, ix)) {
+                v[i] += f[coarse_at(lv, ix)];
             } else {
                 v[i] = C[i];
             }
@@ -388,7 +421,7 @@ static int level_recompose(const level_t *lv, double *v)
     if (!C || !f) { free(C); free(f); return ORC_ENOMEM; }
     for (long i = 0; i < m; ++i) {
         unravel(&lv->fine, i, ix);
-        C[i] = all_even(&lv->fine, ix) ? 0.0 : v[i];
+        C[i] = is_coarse(lv, ix) ? 0.0 : v[i];
     }
     int rc = load_vector(lv, C, f);
     if (rc == ORC_OK) rc = coarse_solve(lv, f);
@@ -396,16 +429,14 @@ static int level_recompose(const level_t *lv, double *v)
         /* coarse nodal values of Q_l u: Q_{l-1} u - z */
         for (long i = 0; i < m; ++i) {
             unravel(&lv->fine, i, ix);
-            if (all_even(&lv->fine, ix)) {
-                long cx[ORC_MAXD];
-                for (int k = 0; k < lv->fine.d; ++k) cx[k] = ix[k] / 2;
-                v[i] -= f[ravel(&lv->coarse, cx)];
+            if (is_coarse(lv, ix)) {
+                v[i] -= f[coarse_at(lv, ix)];
             }
         }
         /* new nodes: coefficient + interpolant of the corrected coarse values */
         for (long i = 0; i < m; ++i) {
             unravel(&lv->fine, i, ix);
-            if (!all_even(&lv->fine, ix)) v[i] = C[i] + interp_at(lv, v, ix);
+            if (!is_coarse(lv, ix)) v[i] = C[i] + interp_at(lv, v, ix);
         }
     }
     free(C);
@@ -427,10 +458,8 @@ static int level_decompose_adjoint(const level_t *lv, double *v)
     if (!z || !G || !w) { free(z); free(G); free(w); return ORC_ENOMEM; }
     for (long i = 0; i < m; ++i) {
         unravel(&lv->fine, i, ix);
-        if (all_even(&lv->fine, ix)) {
-            long cx[ORC_MAXD];
-            for (int k = 0; k < lv->fine.d; ++k) cx[k] = ix[k] / 2;
-            z[ravel(&lv->coarse, cx)] = v[i];
+        if (is_coarse(lv, ix)) {
+            z[coarse_at(lv, ix)] = v[i];
         }
     }
     int rc = coarse_solve(lv, z);
@@ -438,13 +467,13 @@ static int level_decompose_adjoint(const level_t *lv, double *v)
     if (rc == ORC_OK) {
         for (long i = 0; i < m; ++i) {
             unravel(&lv->fine, i, ix);
-            if (!all_even(&lv->fine, ix)) w[i] = v[i] + G[i];
+            if (!is_coarse(lv, ix)) w[i] = v[i] + G[i];
         }
         /* e_bar = e_bar' - Pi^T w : every odd node sends its interpolation
          * weights times w back to its corners */
         for (long i = 0; i < m; ++i) {
             unravel(&lv->fine, i, ix);
-            if (all_even(&lv->fine, ix)) continue;
+            if (is_coarse(lv, ix)) continue;
             int d = lv->fine.d;
             for (int combo = 0; combo < (1 << d); ++combo) {
                 long cx[ORC_MAXD];
@@ -452,7 +481,7 @@ static int level_decompose_adjoint(const level_t *lv, double *v)
                 int skip = 0;
                 for (int k = 0; k < d; ++k) {
                     int right = (combo >> k) & 1;
-                    if (ix[k] % 2 == 0) {
+                    if (coarse_in_dim(lv, k, ix[k])) {
                         if (right) { skip = 1; break; }
                         cx[k] = ix[k];
                     } else {
@@ -468,7 +497,7 @@ static int level_decompose_adjoint(const level_t *lv, double *v)
         }
         for (long i = 0; i < m; ++i) {
             unravel(&lv->fine, i, ix);
-            if (!all_even(&lv->fine, ix)) v[i] = w[i];
+            if (!is_coarse(lv, ix)) v[i] = w[i];
         }
     }
     free(z);
@@ -490,7 +519,7 @@ static int level_recompose_adjoint(const level_t *lv, double *v)
     /* e_tot = e_bar_new + Pi^T o_bar_new, accumulated on the even nodes of v */
     for (long i = 0; i < m; ++i) {
         unravel(&lv->fine, i, ix);
-        if (all_even(&lv->fine, ix)) continue;
+        if (is_coarse(lv, ix)) continue;
         int d = lv->fine.d;
         for (int combo = 0; combo < (1 << d); ++combo) {
             long cx[ORC_MAXD];
@@ -498,7 +527,7 @@ static int level_recompose_adjoint(const level_t *lv, double *v)
             int skip = 0;
             for (int k = 0; k < d; ++k) {
                 int right = (combo >> k) & 1;
-                if (ix[k] % 2 == 0) {
+                if (coarse_in_dim(lv, k, ix[k])) {
                     if (right) { skip = 1; break; }
                     cx[k] = ix[k];
                 } else {
@@ -514,10 +543,8 @@ static int level_recompose_adjoint(const level_t *lv, double *v)
     }
     for (long i = 0; i < m; ++i) {
         unravel(&lv->fine, i, ix);
-        if (all_even(&lv->fine, ix)) {
-            long cx[ORC_MAXD];
-            for (int k = 0; k < lv->fine.d; ++k) cx[k] = ix[k] / 2;
-            z[ravel(&lv->coarse, cx)] = v[i];
+        if (is_coarse(lv, ix)) {
+            z[coarse_at(lv, ix)] = v[i];
         }
     }
     int rc = coarse_solve(lv, z);
@@ -525,7 +552,7 @@ static int level_recompose_adjoint(const level_t *lv, double *v)
     if (rc == ORC_OK) {
         for (long i = 0; i < m; ++i) {
             unravel(&lv->fine, i, ix);
-            if (!all_even(&lv->fine, ix)) v[i] -= G[i];
+            if (!is_coarse(lv, ix)) v[i] -= G[i];
         }
     }
     free(z);
@@ -537,14 +564,14 @@ static int level_recompose_adjoint(const level_t *lv, double *v)
 /* Whole hierarchy                                                           */
 /* ------------------------------------------------------------------------ */
 
-static int check_args(int d, const long *n, const double *const *x, int L, shape_t *s)
+static int check_args(int d, const long *n, const double *const *x, const int *Lk, shape_t *s)
 {
-    if (d < 1 || d > ORC_MAXD || !n || !x || L < 0) return ORC_EINVAL;
+    if (d < 1 || d > ORC_MAXD || !n || !x || !Lk) return ORC_EINVAL;
     s->d = d;
     for (int k = 0; k < d; ++k) {
-        if (!x[k]) return ORC_EINVAL;
+        if (!x[k] || Lk[k] < 0 || Lk[k] > 30) return ORC_EINVAL;
         if (n[k] < 2) return ORC_EINVAL;
-        if ((n[k] - 1) % (1L << L) != 0) return ORC_EINVAL;
+        if ((n[k] - 1) % (1L << Lk[k]) != 0) return ORC_EINVAL;
         s->n[k] = n[k];
     }
     return ORC_OK;
@@ -552,17 +579,19 @@ static int check_args(int d, const long *n, const double *const *x, int L, shape
 
 enum { DIR_DEC, DIR_REC, DIR_DEC_ADJ, DIR_REC_ADJ };
 
-static int run(int d, const long *n, const double *const *x, int L, double *u, int dir)
+static int run(int d, const long *n, const double *const *x, const int *Lk, double *u, int dir)
 {
     shape_t s;
-    int rc = check_args(d, n, x, L, &s);
+    int rc = check_args(d, n, x, Lk, &s);
     if (rc != ORC_OK) return rc;
+    int L = 0;
+    for (int k = 0; k < d; ++k) if (Lk[k] > L) L = Lk[k];
     /* decompose and recompose-adjoint run finest first; the others coarsest first */
     int fine_first = (dir == DIR_DEC || dir == DIR_REC_ADJ);
     for (int step = 0; step < L && rc == ORC_OK; ++step) {
         int l = fine_first ? L - step : step + 1;
         level_t lv;
-        rc = level_make(&s, x, L, l, &lv);
+        rc = level_make(&s, x, Lk, L, l, &lv);
         if (rc != ORC_OK) break;
         double *v = (double *)malloc(sizeof(double) * (size_t)shape_size(&lv.fine));
         if (!v) { level_free(&lv); rc = ORC_ENOMEM; break; }
@@ -585,29 +614,59 @@ static int run(int d, const long *n, const double *const *x, int L, double *u, i
 /*   d      number of dimensions (1..3)                                     */
 /*   n      nodes per dimension, slowest first; (n[k]-1) % 2^L == 0         */
 /*   x      d coordinate arrays, x[k] of length n[k], strictly increasing   */
-/*   L      number of levels to process                                     */
+/*   L      number of levels to process (the *_per_dim forms: Lk, one       */
+/*          level count per dimension)                                      */
 /*   u      row-major array of prod(n) doubles, transformed in place        */
 /* Return 0 on success, 1 on invalid arguments, 2 on allocation failure.    */
 /* ------------------------------------------------------------------------ */
 
+static int run_all(int d, const long *n, const double *const *x, int L, double *u, int dir)
+{
+    if (L < 0) return ORC_EINVAL;
+    int Lk[ORC_MAXD] = {L, L, L};
+    return run(d, n, x, Lk, u, dir);
+}
+
 int orc_decompose(int d, const long *n, const double *const *x, int L, double *u)
 {
-    return run(d, n, x, L, u, DIR_DEC);
+    return run_all(d, n, x, L, u, DIR_DEC);
 }
 
 int orc_recompose(int d, const long *n, const double *const *x, int L, double *u)
 {
-    return run(d, n, x, L, u, DIR_REC);
+    return run_all(d, n, x, L, u, DIR_REC);
 }
 
 int orc_decompose_adjoint(int d, const long *n, const double *const *x, int L, double *u)
 {
-    return run(d, n, x, L, u, DIR_DEC_ADJ);
+    return run_all(d, n, x, L, u, DIR_DEC_ADJ);
 }
 
 int orc_recompose_adjoint(int d, const long *n, const double *const *x, int L, double *u)
 {
-    return run(d, n, x, L, u, DIR_REC_ADJ);
+    return run_all(d, n, x, L, u, DIR_REC_ADJ);
+}
+
+/* The same maps with a level count per dimension: Lk[k] levels along
+ * dimension k, (n[k]-1) % 2^Lk[k] == 0, L = max_k Lk[k] levels in all. */
+int orc_decompose_per_dim(int d, const long *n, const double *const *x, const int *Lk, double *u)
+{
+    return run(d, n, x, Lk, u, DIR_DEC);
+}
+
+int orc_recompose_per_dim(int d, const long *n, const double *const *x, const int *Lk, double *u)
+{
+    return run(d, n, x, Lk, u, DIR_REC);
+}
+
+int orc_decompose_adjoint_per_dim(int d, const long *n, const double *const *x, const int *Lk, double *u)
+{
+    return run(d, n, x, Lk, u, DIR_DEC_ADJ);
+}
+
+int orc_recompose_adjoint_per_dim(int d, const long *n, const double *const *x, const int *Lk, double *u)
+{
+    return run(d, n, x, Lk, u, DIR_REC_ADJ);
 }
 
 /* Single-line operators, exported so the tests can pin them one by one. */

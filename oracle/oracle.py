@@ -44,6 +44,11 @@ def _load():
             f = getattr(lib, name)
             f.argtypes = [ctypes.c_int, lp, ctypes.POINTER(dp), ctypes.c_int, dp]
             f.restype = ctypes.c_int
+        for name in ("orc_decompose_per_dim", "orc_recompose_per_dim",
+                     "orc_decompose_adjoint_per_dim", "orc_recompose_adjoint_per_dim"):
+            f = getattr(lib, name)
+            f.argtypes = [ctypes.c_int, lp, ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_int), dp]
+            f.restype = ctypes.c_int
         for name in ("orc_line_mass", "orc_line_prolong", "orc_line_restrict"):
             f = getattr(lib, name)
             f.argtypes = [ctypes.c_long, dp, dp, dp]
@@ -71,14 +76,32 @@ def max_levels(shape) -> int:
     return L
 
 
-def _run(fn_name: str, u: np.ndarray, nlevels: int | None, coords) -> np.ndarray:
+def dim_levels(shape) -> tuple:
+    """Per dimension, the largest L_k with (n_k - 1) divisible by 2^L_k."""
+    out = []
+    for n in shape:
+        L = 0
+        while (n - 1) % (1 << (L + 1)) == 0 and (n - 1) >= (1 << (L + 1)):
+            L += 1
+        out.append(L)
+    return tuple(out)
+
+
+def _run(fn_name: str, u: np.ndarray, nlevels, coords) -> np.ndarray:
     lib = _load()
     u = np.array(u, dtype=np.float64, order="C", copy=True)
     d = u.ndim
     if not 1 <= d <= 3:
         raise ValueError("oracle supports 1 to 3 dimensions")
     shape = u.shape
-    L = max_levels(shape) if nlevels is None or nlevels < 0 else int(nlevels)
+    per_dim = fn_name.endswith("_per_dim")
+    if per_dim:
+        Lk = dim_levels(shape) if nlevels is None else tuple(int(v) for v in nlevels)
+        if len(Lk) != d:
+            raise ValueError("one level count per dimension")
+        L = (ctypes.c_int * d)(*Lk)
+    else:
+        L = max_levels(shape) if nlevels is None or nlevels < 0 else int(nlevels)
     if coords is None:
         coords = [uniform_coords(n) for n in shape]
     xs = [np.ascontiguousarray(np.asarray(c, dtype=np.float64)) for c in coords]
@@ -88,7 +111,8 @@ def _run(fn_name: str, u: np.ndarray, nlevels: int | None, coords) -> np.ndarray
     x_arr = (ctypes.POINTER(ctypes.c_double) * d)(*[_dp(x) for x in xs])
     rc = getattr(lib, fn_name)(d, n_arr, x_arr, L, _dp(u))
     if rc != 0:
-        raise ValueError(f"{fn_name} failed with code {rc} (shape {shape}, L={L})")
+        raise ValueError(f"{fn_name} failed with code {rc} (shape {shape}, "
+                         f"L={list(L) if per_dim else L})")
     return u
 
 
@@ -119,6 +143,30 @@ def recompose_classes(u, nclasses, nlevels=None, coords=None):
     kept[np.ix_(*[np.arange(0, n, stride) for n in u.shape])] = True
     u[~kept] = 0.0
     return recompose(u, L, coords)
+
+
+def decompose_per_dim(u, levels=None, coords=None):
+    """Decomposition with a level count per dimension (default: each
+    dimension's own maximum, ``dim_levels``): dimension k coarsens in the
+    first levels[k] steps from the finest level and then keeps its nodes, so
+    short sides stop early (a generalisation of the equal sides of Section
+    IV; Eq. 1-2 unchanged on the nested tensor-product spaces)."""
+    return _run("orc_decompose_per_dim", u, levels, coords)
+
+
+def recompose_per_dim(u, levels=None, coords=None):
+    """Exact inverse of ``decompose_per_dim``."""
+    return _run("orc_recompose_per_dim", u, levels, coords)
+
+
+def decompose_adjoint_per_dim(u, levels=None, coords=None):
+    """Transpose of ``decompose_per_dim``."""
+    return _run("orc_decompose_adjoint_per_dim", u, levels, coords)
+
+
+def recompose_adjoint_per_dim(u, levels=None, coords=None):
+    """Transpose of ``recompose_per_dim``."""
+    return _run("orc_recompose_adjoint_per_dim", u, levels, coords)
 
 
 def decompose_adjoint(u, nlevels=None, coords=None):

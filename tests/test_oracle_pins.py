@@ -377,3 +377,102 @@ def test_classes_argument_range():
         oracle.recompose_classes(u, 0)
     with pytest.raises(ValueError):
         oracle.recompose_classes(u, oracle.max_levels(u.shape) + 2)
+
+
+# ---------------------------------------------------------------- per-dimension level counts
+
+PER_DIM = [((33, 5), (5, 2)), ((9, 33), (3, 5)), ((17, 5, 9), (4, 2, 3)),
+           ((5, 9, 17), (2, 3, 4)), ((9, 6), (3, 0)), ((13, 9), (2, 3))]
+
+
+def test_per_dim_default_levels():
+    assert oracle.dim_levels((1025, 1025, 513)) == (10, 10, 9)
+    assert oracle.dim_levels((17, 6)) == (4, 0)
+    assert oracle.dim_levels((13,)) == (2,)     # 12 = 3 * 4
+    assert oracle.dim_levels((2, 3)) == (0, 1)
+
+
+@pytest.mark.parametrize("shape", [(33,), (9, 17), (17, 9, 33)])
+def test_per_dim_equal_levels_is_the_plain_map(shape):
+    """Every dimension with the same count L: the plain maps, bit for bit."""
+    rng = np.random.default_rng(31)
+    coords = _rand_coords(rng, shape)
+    L = oracle.max_levels(shape)
+    u = rng.standard_normal(shape)
+    lv = (L,) * len(shape)
+    assert np.array_equal(oracle.decompose_per_dim(u, lv, coords), oracle.decompose(u, L, coords))
+    assert np.array_equal(oracle.recompose_per_dim(u, lv, coords), oracle.recompose(u, L, coords))
+    assert np.array_equal(oracle.decompose_adjoint_per_dim(u, lv, coords),
+                          oracle.decompose_adjoint(u, L, coords))
+
+
+@pytest.mark.parametrize("shape,levels", PER_DIM)
+@pytest.mark.parametrize("uniform", [True, False])
+def test_per_dim_matches_dense_projections(shape, levels, uniform):
+    """Unequal level counts against the global-projection statement on
+    per-dimension nested node sets (no recursion, no Thomas, no stencils)."""
+    rng = np.random.default_rng(12)
+    coords = ([oracle.uniform_coords(n) for n in shape] if uniform
+              else _rand_coords(rng, shape))
+    u = rng.standard_normal(shape)
+    got = oracle.decompose_per_dim(u, levels, coords)
+    want = dense.decompose(u, coords, max(levels), levels)
+    assert _relmax(got, want) < 1e-12
+
+
+@pytest.mark.parametrize("shape,levels,axis", [((17, 6), (4, 0), 1), ((6, 33), (0, 5), 0)])
+def test_per_dim_frozen_dimension_gives_independent_lines(shape, levels, axis):
+    """A dimension that never coarsens contributes the identity: every line
+    across it is decomposed on its own by the 1D map (mass matrix and its
+    inverse cancel along the frozen dimension)."""
+    rng = np.random.default_rng(4)
+    coords = _rand_coords(rng, shape)
+    u = rng.standard_normal(shape)
+    got = oracle.decompose_per_dim(u, levels, coords)
+    live = 1 - axis
+    for j in range(shape[axis]):
+        sl = (slice(None), j) if axis == 1 else (j, slice(None))
+        want = oracle.decompose(u[sl], levels[live], [coords[live]])
+        assert _relmax(got[sl], want) < 1e-12
+
+
+def test_per_dim_frozen_dimension_in_3d_gives_independent_planes():
+    shape, levels = (5, 6, 9), (2, 0, 3)
+    rng = np.random.default_rng(6)
+    coords = _rand_coords(rng, shape)
+    u = rng.standard_normal(shape)
+    got = oracle.decompose_per_dim(u, levels, coords)
+    for j in range(shape[1]):
+        want = dense.decompose(u[:, j, :], [coords[0], coords[2]], 3, (2, 3))
+        assert _relmax(got[:, j, :], want) < 1e-12
+
+
+@pytest.mark.parametrize("shape,levels", PER_DIM)
+def test_per_dim_round_trip(shape, levels):
+    rng = np.random.default_rng(13)
+    coords = _rand_coords(rng, shape)
+    u = rng.standard_normal(shape)
+    back = oracle.recompose_per_dim(oracle.decompose_per_dim(u, levels, coords), levels, coords)
+    assert _relmax(back, u) < 1e-13
+
+
+@pytest.mark.parametrize("shape,levels", PER_DIM[:4])
+def test_per_dim_adjoint_dot_products(shape, levels):
+    """<D x, y> = <x, D^T y> for both maps."""
+    rng = np.random.default_rng(14)
+    coords = _rand_coords(rng, shape)
+    x, y = rng.standard_normal(shape), rng.standard_normal(shape)
+    for fwd, adj in ((oracle.decompose_per_dim, oracle.decompose_adjoint_per_dim),
+                     (oracle.recompose_per_dim, oracle.recompose_adjoint_per_dim)):
+        dx = fwd(x, levels, coords)
+        lhs = float(np.sum(dx * y))
+        rhs = float(np.sum(x * adj(y, levels, coords)))
+        assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(dx) * np.linalg.norm(y)
+
+
+def test_per_dim_level_count_beyond_the_side_is_rejected():
+    u = np.zeros((9, 6))
+    with pytest.raises(ValueError):
+        oracle.decompose_per_dim(u, (3, 1))     # 5 is not divisible by 2
+    with pytest.raises(ValueError):
+        oracle.decompose_per_dim(u, (3,))
