@@ -371,6 +371,16 @@ def test_classes_error_is_monotone():
     assert errs[-1] < 1e-24 and errs[0] > 1e-3
 
 
+def test_classes_worked_example_1d():
+    """Fig. 2 example rebuilt from its first 1, 2 and 3 classes, worked by
+    hand (tests/golden/classes_1d.txt)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "classes_1d.txt"))
+            if l.strip() and not l.startswith("#")]
+    x, dec, *want = (np.array([float(v) for v in r]) for r in rows)
+    for nc, w in enumerate(want, start=1):
+        np.testing.assert_allclose(oracle.recompose_classes(dec, nc, coords=[x]), w, rtol=0, atol=1e-14)
+
+
 def test_classes_argument_range():
     u = np.zeros((9, 9))
     with pytest.raises(ValueError):
