@@ -1066,6 +1066,8 @@ extern "C" {
 mgard_status mgard_plan_create(int ndim, const int64_t *dims, int nlevels, const double *const *coords,
                                mgard_dtype dtype, mgard_plan **out)
 {
+    if (!out) return fail(MGARD_ERR_INVALID_ARG, "plan_create: out is NULL");
+    *out = nullptr;  // NULL on every failure path
     std::vector<double> tab;
     mgard_plan *P = nullptr;
     mgard_status s = build_plan_host(ndim, dims, nlevels, coords, dtype, &P, &tab);
