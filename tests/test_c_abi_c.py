@@ -28,6 +28,23 @@ int main(void)
     if (mgard_recompose_classes(NULL, 1, NULL, NULL, 0, NULL) != MGARD_ERR_INVALID_ARG) return 5;
     if (mgard_workspace_bytes(NULL) != 0 || mgard_plan_levels(NULL) != -1) return 6;
     if (mgard_plan_destroy(NULL) != MGARD_OK) return 7;
+    /* every entry point rejects a NULL plan or batch before touching a device */
+    if (mgard_recompose(NULL, NULL, NULL, 0, NULL) != MGARD_ERR_INVALID_ARG) return 9;
+    if (mgard_decompose_adjoint(NULL, NULL, NULL, 0, NULL) != MGARD_ERR_INVALID_ARG) return 10;
+    if (mgard_recompose_adjoint(NULL, NULL, NULL, 0, NULL) != MGARD_ERR_INVALID_ARG) return 11;
+    if (mgard_decompose_host(NULL, NULL, NULL, NULL, NULL, 0, NULL) != MGARD_ERR_INVALID_ARG) return 12;
+    if (mgard_plan_tune(NULL, 0, 0, 0) != MGARD_ERR_INVALID_ARG) return 13;
+    if (mgard_plan_get_tune(NULL, 0, 0) != -1 || mgard_plan_launches(NULL, 0) != -1) return 14;
+    if (mgard_plan_check(NULL, NULL, NULL) != MGARD_ERR_INVALID_ARG) return 15;
+    if (mgard_profile_enable(NULL, 1) != MGARD_ERR_INVALID_ARG) return 16;
+    if (mgard_profile_read(NULL, 0, NULL, NULL, NULL, NULL) != -1) return 17;
+    {
+        mgard_batch *b = (mgard_batch *)1;
+        if (mgard_batch_create(0, NULL, 1, &b) != MGARD_ERR_INVALID_ARG || b != NULL) return 18;
+        if (mgard_batch_decompose(NULL, NULL, NULL, 0, NULL) != MGARD_ERR_INVALID_ARG) return 19;
+        if (mgard_batch_workspace_bytes(NULL) != 0 || mgard_batch_destroy(NULL) != MGARD_OK) return 20;
+    }
+    if (mgard_decompose_noalloc(2, bad, 1, MGARD_F32, NULL, NULL) != MGARD_ERR_INVALID_ARG) return 21;
     printf("ok %d\n", (int)MGARD_NOALLOC_SCRATCH_BYTES);
     return 0;
 }
