@@ -77,7 +77,8 @@ struct ProlongParams {
     const void *w0, *w1, *w2;  // per finest node: weight of its right level-k neighbour (TW)
     int n0, n1, n2, m0, m1, m2;
     int shift;               // finest index >> shift = left level-k neighbour (>= 1)
-    int seg;                 // nodes of a row per work item (a multiple of 32)
+    int seg;                 // launcher only: row segment it sizes the grid by (the
+                             // kernel walks its own strips of 32 columns x 64 rows)
 };
 
 }  // namespace mg
