@@ -15,6 +15,7 @@ l, S = bytes per element).  The field (540 MB) is larger than the 129 MB L2,
 so no flush is needed between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       python bench.py --case SHAPE DTYPE REPS [NCLASSES] [TUNE]   (profiling case)
 Under torchrun each rank refactors its own field (independent partitions,
 weak scaling, no collective on the data path).
 """
@@ -454,7 +455,43 @@ def run_mixed(torch, mgard, synth, dev, stream, rank, world, max_over_ranks):
     return out
 
 
+def run_case(spec):
+    """One profiling case (no timing): --case SHAPE DTYPE REPS [NCLASSES] [TUNE]
+    runs REPS decompose + recompose pairs of the seeded field of SHAPE
+    (comma-separated sides) in DTYPE (f32 | f64 | f32_mixed); NCLASSES > 0
+    rebuilds from that many coefficient classes; TUNE = param:value[,...]
+    plan-wide tuning switches (mgard_plan_tune on level 0).  Prints one
+    line, for runs under a profiler."""
+    import torch
+
+    from paper_2007_04457_gb300 import mgard, synth
+
+    shape = tuple(int(x) for x in spec[0].split(","))
+    dtype = spec[1] if len(spec) > 1 else "f32"
+    reps = int(spec[2]) if len(spec) > 2 else 1
+    nclasses = int(spec[3]) if len(spec) > 3 else 0
+    plan = mgard.Plan(shape, dtype=dtype)
+    if len(spec) > 4 and spec[4]:
+        for kv in spec[4].split(","):
+            k, v = kv.split(":")
+            plan.tune(0, int(k), int(v))
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    u = synth.sinusoid_field_torch(shape, N_MODES if len(shape) == 3 else 8, SEED, "cuda", tdt)
+    ws = plan.workspace(u.device)
+    for _ in range(reps):
+        plan.decompose(u, ws)
+        if nclasses > 0:
+            plan.recompose_classes(u, nclasses, ws)
+        else:
+            plan.recompose(u, ws)
+    torch.cuda.synchronize()
+    print(f"case ok: shape={shape} dtype={dtype} levels={plan.levels} reps={reps}"
+          + (f" nclasses={nclasses}" if nclasses > 0 else ""))
+
+
 def main():
+    if "--case" in sys.argv:
+        return run_case(sys.argv[sys.argv.index("--case") + 1:])
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)

@@ -153,8 +153,25 @@ MGARD_API mgard_status mgard_recompose_classes(const mgard_plan *plan, int nclas
  *            2^22 polls of tens of nanoseconds each).  A wait runs out only
  *            when the limit is far too small for the work between barriers;
  *            the result is then wrong, and mgard_plan_check reports it.
+ *   param 7  plan-wide: the row-chunk kernels (one warp per row segment
+ *            of 256 or 512 columns, moved in coalesced 16-byte words through
+ *            a per-warp shared-memory ring of asynchronous copies; the
+ *            restriction also solving along the contiguous dimension when a
+ *            row is one segment) on the levels they take: 2D/3D, rows of
+ *            2^k 256 + 1 nodes, n1 = 1 mod 8, a 16-byte aligned array.  The
+ *            value is a mask of the ones kept out: bit 0 the coefficient and
+ *            interpolation sweeps, bit 1 the restriction (default 2: the
+ *            row-chunk sweeps with the strip restriction); 3 = the tile and
+ *            strip kernels on every level.  All forms differ only in
+ *            floating-point rounding order.  The
+ *            row-chunk kernels read whole 16-byte words: up to 12 bytes
+ *            beyond an array's last element, inside the word that holds it.
+ *   param 9  plan-wide: coarse intervals (sweeps) or planes (restriction)
+ *            per work item of the row-chunk kernels (0 = automatic).
  *   mgard_plan_get_tune also reports param 5: the first level the
- *   cooperative kernel runs (-1: none).
+ *   cooperative kernel runs (-1: none), and param 8: the row-chunk
+ *   restriction's segment width of the level (512 or 256 columns; 0: not a
+ *   row-chunk level).
  * Returns MGARD_ERR_INVALID_ARG for an unknown parameter or value. */
 MGARD_API mgard_status mgard_plan_tune(mgard_plan *plan, int level, int param, int value);
 

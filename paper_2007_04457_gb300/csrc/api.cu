@@ -63,6 +63,14 @@ struct mgard_level {
     int zchunk, nzc, tiles_y, tiles_x;
     int rgrid_dec, rgrid_rec;
     int kuni32[3], kuni64[3];  // 1: the interior rows of K (float / double table) are all equal
+    int wuni2;           // 1: every odd node of dim 2 has interpolation weights (1/2, 1/2)
+    // row-chunk kernels (rowchunk.cuh): used when rc_q[0] > 0; per kernel
+    // (sweep, restriction) the sub-segments per segment and segments per row
+    int rc_q[2] = {0, 0}, rc_s[2] = {0, 0};
+    bool rc_xs = false;          // the restriction also solves along dim 2
+    int rc_grid[2] = {0, 0};     // blocks: sweep, restriction
+    int rc_zc[2] = {0, 0};       // coarse intervals (sweep) / planes (restriction) per chunk
+    int rc_nzc[2] = {0, 0};      // chunk counts
 };
 
 struct mgard_plan {
@@ -96,6 +104,8 @@ struct mgard_plan {
     int coop_j = 0, coop_auto = 0, coop_s = 0;
     bool coop_off = false;
     int coop_spin = 0;                // barrier poll limit (0: default)
+    int rc_off = kRcDefaultOff;       // tune: row-chunk kernels kept out (bit 0 sweeps, bit 1 restriction)
+    int rc_zreq = 0;                  // tune: coarse intervals / planes per row-chunk item (0: automatic)
     int coop_grid = 0;
     size_t coop_smem = 0;
     int coop_hcap = 0;
@@ -273,11 +283,12 @@ cudaError_t run_restrict_level(const mgard_plan *P, int j, int mode, void *A, ch
 // (slowest) one applies V += z (sign +1), V -= z (sign -1) or leaves z in F
 // (sign 0).  With src, the first sweep reads its right-hand sides from src.
 template <typename TW>
-cudaError_t run_solves(const mgard_plan *P, int j, int sign, char *ws, cudaStream_t st, const void *src = nullptr)
+cudaError_t run_solves(const mgard_plan *P, int j, int sign, char *ws, cudaStream_t st, const void *src = nullptr,
+                       int first = 0)
 {
     const mgard_level &L = P->lv[j];
     const int nd = P->ndim;
-    for (int q = 0; q < nd; ++q) {
+    for (int q = first; q < nd; ++q) {
         const int k = 2 - q;  // internal dim index, fastest first
         SolveParams sp;
         sp.F = ws + L.f_off;
@@ -293,7 +304,7 @@ cudaError_t run_solves(const mgard_plan *P, int j, int sign, char *ws, cudaStrea
         sp.nw = 0;
         sp.lpb = 32;
         sp.vmode = (q == nd - 1) ? (sign > 0 ? 1 : (sign < 0 ? 2 : 0)) : 0;
-        sp.src = (q == 0) ? src : nullptr;  // the first sweep may read its right-hand sides elsewhere
+        sp.src = (q == first) ? src : nullptr;  // the first sweep may read its right-hand sides elsewhere
         cudaError_t err = timed(P, sp.vmode ? KIND_SOLVE_FUSED : KIND_SOLVE, j, st,
                                 [&] { return launch_solve<TW>(sp, L.svar, P->num_sms, st); });
         if (err != cudaSuccess) return err;
@@ -335,6 +346,64 @@ cudaError_t run_interp_level(const mgard_plan *P, int j, void *A, char *ws, cuda
 {
     const PlaceParams p = place_params<T>(P, j, A, ws);
     return timed(P, KIND_INTERP, j, st, [&] { return launch_interp<T, TW>(P->act, p, P->num_sms, st); });
+}
+
+// Row-chunk kernel `kind` (0 sweeps, 1 restriction) for level j on level
+// array A: an eligible level, not switched off, and a 16-byte aligned array
+// (the workspace arrays always are; the user array at level 0 may not be).
+bool rc_on(const mgard_plan *P, int j, const void *A, int kind)
+{
+    return P->lv[j].rc_q[0] > 0 && !(P->rc_off & (1 << kind)) && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+}
+
+// Leading dims whose solve the level's load-vector kernel already did.
+int solved_first(const mgard_plan *P, int j, const void *A)
+{
+    return (rc_on(P, j, A, 1) && P->lv[j].rc_xs) ? 1 : 0;
+}
+
+template <typename T, typename TW>
+RcParams rc_params(const mgard_plan *P, int j, void *A, char *ws, int kind)
+{
+    const mgard_level &L = P->lv[j];
+    RcParams p;
+    p.A = A;
+    p.F = ws + L.f_off;
+    p.V = ws + L.v_off;
+    p.n0 = (int)L.n[0]; p.n1 = (int)L.n[1]; p.n2 = (int)L.n[2];
+    p.m0 = (int)L.m[0]; p.m1 = (int)L.m[1]; p.m2 = (int)L.m[2];
+    p.S = L.rc_s[kind];
+    p.nb = kind == 0 ? (int)L.m[1] : (int)((L.m[1] + kRcRows - 1) / kRcRows);
+    p.zchunk = L.rc_zc[kind];
+    p.nzc = L.rc_nzc[kind];
+    p.nitems = p.S * p.nb * p.nzc;
+    p.w0 = tab_ptr<T>(P, L.w_off[0]); p.w1 = tab_ptr<T>(P, L.w_off[1]); p.w2 = tab_ptr<T>(P, L.w_off[2]);
+    p.k0 = tab_ptr<T>(P, L.k_off[0]); p.k1 = tab_ptr<T>(P, L.k_off[1]); p.k2 = tab_ptr<T>(P, L.k_off[2]);
+    p.fx = tab_ptr<TW>(P, L.t_off[2]);
+    return p;
+}
+
+// Coefficients (MODE_DEC) or interpolation (MODE_REC) of level j.
+template <typename T, typename TW>
+cudaError_t run_rc_sweep(const mgard_plan *P, int j, int mode, void *A, char *ws, cudaStream_t st)
+{
+    const mgard_level &L = P->lv[j];
+    const RcParams p = rc_params<T, TW>(P, j, A, ws, 0);
+    return timed(P, mode == MODE_DEC ? KIND_PLACE : KIND_INTERP, j, st, [&] {
+        return launch_rc<T, TW>(0, L.rc_q[0], mode, P->act == ACT_3D, L.wuni2 != 0, false, p, L.rc_grid[0], st);
+    });
+}
+
+// Load vector and coarse gather of level j (with the dim-2 solve when rc_xs).
+template <typename T, typename TW>
+cudaError_t run_rc_restrict(const mgard_plan *P, int j, int mode, void *A, char *ws, cudaStream_t st)
+{
+    const mgard_level &L = P->lv[j];
+    const RcParams p = rc_params<T, TW>(P, j, A, ws, 1);
+    const bool ku = (sizeof(T) == 4 ? L.kuni32[2] : L.kuni64[2]) != 0;
+    return timed(P, mode == MODE_DEC ? KIND_RESTRICT_DEC : KIND_RESTRICT_REC, j, st, [&] {
+        return launch_rc<T, TW>(1, L.rc_q[1], mode, P->act == ACT_3D, ku, L.rc_xs, p, L.rc_grid[1], st);
+    });
 }
 
 // Levels small_j .. L-1 in one block, on the array of level small_j (the
@@ -428,12 +497,20 @@ mgard_status exec_decompose(const mgard_plan *P, void *data, char *ws, cudaStrea
     const int J = coop ? P->coop_j : P->small_j;
     for (int j = 0; j < J; ++j) {
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
-        err = (j == 0) ? run_coef_level<TU, TW>(P, j, A, ws, st) : run_coef_level<TW, TW>(P, j, A, ws, st);
+        if (rc_on(P, j, A, 0))
+            err = (j == 0) ? run_rc_sweep<TU, TW>(P, j, MODE_DEC, A, ws, st)
+                           : run_rc_sweep<TW, TW>(P, j, MODE_DEC, A, ws, st);
+        else
+            err = (j == 0) ? run_coef_level<TU, TW>(P, j, A, ws, st) : run_coef_level<TW, TW>(P, j, A, ws, st);
         if (err != cudaSuccess) return cuda_fail(err, "decompose: coefficient kernel");
-        err = (j == 0) ? run_restrict_level<TU, TW>(P, j, MODE_DEC, A, ws, st)
-                       : run_restrict_level<TW, TW>(P, j, MODE_DEC, A, ws, st);
+        if (rc_on(P, j, A, 1))
+            err = (j == 0) ? run_rc_restrict<TU, TW>(P, j, MODE_DEC, A, ws, st)
+                           : run_rc_restrict<TW, TW>(P, j, MODE_DEC, A, ws, st);
+        else
+            err = (j == 0) ? run_restrict_level<TU, TW>(P, j, MODE_DEC, A, ws, st)
+                           : run_restrict_level<TW, TW>(P, j, MODE_DEC, A, ws, st);
         if (err != cudaSuccess) return cuda_fail(err, "decompose: load-vector kernel");
-        err = run_solves<TW>(P, j, +1, ws, st);
+        err = run_solves<TW>(P, j, +1, ws, st, nullptr, solved_first(P, j, A));
         if (err != cudaSuccess) return cuda_fail(err, "decompose: correction solve kernel");
     }
     if (coop) {
@@ -465,8 +542,12 @@ mgard_status exec_recompose(const mgard_plan *P, void *data, char *ws, cudaStrea
     const int J = coop ? P->coop_j : std::max(P->small_j, D);
     for (int j = D; j < J; ++j) {
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
-        err = (j == 0) ? run_restrict_level<TU, TW>(P, j, MODE_REC, A, ws, st)
-                       : run_restrict_level<TW, TW>(P, j, MODE_REC, A, ws, st);
+        if (rc_on(P, j, A, 1))
+            err = (j == 0) ? run_rc_restrict<TU, TW>(P, j, MODE_REC, A, ws, st)
+                           : run_rc_restrict<TW, TW>(P, j, MODE_REC, A, ws, st);
+        else
+            err = (j == 0) ? run_restrict_level<TU, TW>(P, j, MODE_REC, A, ws, st)
+                           : run_restrict_level<TW, TW>(P, j, MODE_REC, A, ws, st);
         if (err != cudaSuccess) return cuda_fail(err, "recompose: load-vector kernel");
     }
     if (coop) {
@@ -478,10 +559,14 @@ mgard_status exec_recompose(const mgard_plan *P, void *data, char *ws, cudaStrea
         if (err != cudaSuccess) return cuda_fail(err, "recompose: single-block coarse-level kernel");
     }
     for (int j = J - 1; j >= D; --j) {
-        err = run_solves<TW>(P, j, -1, ws, st);
-        if (err != cudaSuccess) return cuda_fail(err, "recompose: correction solve kernel");
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
-        err = (j == 0) ? run_interp_level<TU, TW>(P, j, A, ws, st) : run_interp_level<TW, TW>(P, j, A, ws, st);
+        err = run_solves<TW>(P, j, -1, ws, st, nullptr, solved_first(P, j, A));
+        if (err != cudaSuccess) return cuda_fail(err, "recompose: correction solve kernel");
+        if (rc_on(P, j, A, 0))
+            err = (j == 0) ? run_rc_sweep<TU, TW>(P, j, MODE_REC, A, ws, st)
+                           : run_rc_sweep<TW, TW>(P, j, MODE_REC, A, ws, st);
+        else
+            err = (j == 0) ? run_interp_level<TU, TW>(P, j, A, ws, st) : run_interp_level<TW, TW>(P, j, A, ws, st);
         if (err != cudaSuccess) return cuda_fail(err, "recompose: interpolation kernel");
     }
     return MGARD_OK;
@@ -725,6 +810,84 @@ cudaError_t configure_level(mgard_plan *P, mgard_level &L, bool finest)
     return configure_restrict<TU, TW>(P, L, finest, &items, &slots);
 }
 
+// Row-chunk configuration of a 2D/3D level (rowchunk.cuh): rows of
+// 2^k 256 + 1 nodes with n1 = 1 mod 8 (then n1, n2, m1, m2 = 1 mod 4, which
+// the kernels' word offsets rely on).  Segments of 256 columns for the
+// sweeps; for the restriction segments of 512 columns where the rows split
+// into them and hold 4-byte elements (a row of one segment also solves
+// along dim 2), else 256.  Plane chunks and grids per kernel.  Leaves
+// rc_q[0] = 0 (the other kernels) otherwise.
+template <typename TU, typename TW>
+cudaError_t configure_rc(mgard_plan *P, mgard_level &L, bool finest)
+{
+    L.rc_q[0] = L.rc_q[1] = 0;
+    if (P->act == ACT_1D) return cudaSuccess;
+    const int es = (int)(finest ? P->elem_user : P->elem_ws);
+    const int64_t n1 = L.n[1], n2 = L.n[2];
+    if ((n2 - 1) % 256 != 0 || n1 < 9 || (n1 - 1) % 8 != 0) return cudaSuccess;
+    const int E = 16 / es;
+    const int qs = 256 / (32 * E);                                   // 256-column segments
+    const int wr = (es == 4 && (n2 - 1) % 512 == 0) ? 512 : 256;
+    const int qr = wr / (32 * E);
+    const int Ss = (int)((n2 - 1) / 256), Sr = (int)((n2 - 1) / wr);
+    const bool hz = P->act == ACT_3D, xs = (Sr == 1), wu = L.wuni2 != 0;
+    const bool ku = (es == 4 ? L.kuni32[2] : L.kuni64[2]) != 0;
+    int bd = 0, br = 0, bx = 0;
+    cudaError_t err;
+    if (finest) {
+        err = rc_occupancy<TU, TW>(0, qs, MODE_DEC, hz, wu, false, Ss, &bd);
+        if (err == cudaSuccess) err = rc_occupancy<TU, TW>(0, qs, MODE_REC, hz, wu, false, Ss, &br);
+        if (err == cudaSuccess) err = rc_occupancy<TU, TW>(1, qr, MODE_DEC, hz, ku, xs, Sr, &bx);
+    } else {
+        err = rc_occupancy<TW, TW>(0, qs, MODE_DEC, hz, wu, false, Ss, &bd);
+        if (err == cudaSuccess) err = rc_occupancy<TW, TW>(0, qs, MODE_REC, hz, wu, false, Ss, &br);
+        if (err == cudaSuccess) err = rc_occupancy<TW, TW>(1, qr, MODE_DEC, hz, ku, xs, Sr, &bx);
+    }
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return cudaSuccess;  // not available here: the other kernels
+    }
+    const int bs = std::min(bd, br);
+    if (bs < 1 || bx < 1) return cudaSuccess;
+    const int64_t m0 = L.m[0], m1 = L.m[1];
+    // sweep: work items of one coarse row of a segment and a chunk of coarse
+    // intervals, about four per resident warp
+    const int64_t slots_s = (int64_t)bs * P->num_sms * kRcWarps;
+    int64_t nzc = 1, zc = 0;
+    if (hz) {
+        nzc = std::max<int64_t>(1, std::min<int64_t>((4 * slots_s + Ss * m1 - 1) / (Ss * m1), m0 - 1));
+        zc = (m0 - 1 + nzc - 1) / nzc;
+        if (P->rc_zreq > 0) zc = std::min<int64_t>(P->rc_zreq, m0 - 1);
+        nzc = (m0 - 1 + zc - 1) / zc;
+    }
+    L.rc_zc[0] = (int)zc;
+    L.rc_nzc[0] = (int)nzc;
+    const int64_t items_s = (int64_t)Ss * m1 * nzc;
+    L.rc_grid[0] = (int)std::min<int64_t>((items_s + kRcWarps - 1) / kRcWarps, (int64_t)bs * P->num_sms);
+    // restriction: blocks of kRcRows coarse rows of a segment and a chunk of
+    // coarse planes (each chunk re-reads 3 fine planes), about two per warp
+    const int64_t nb = (m1 + kRcRows - 1) / kRcRows;
+    const int64_t slots_r = (int64_t)bx * P->num_sms * kRcWarps;
+    int64_t nzr = 1, zr = 1;
+    if (hz) {
+        nzr = std::max<int64_t>(1, std::min<int64_t>((2 * slots_r + Sr * nb - 1) / (Sr * nb), std::max<int64_t>(1, (m0 - 1) / 2)));
+        zr = std::max<int64_t>(1, (m0 - 1 + nzr - 1) / nzr);
+        if (P->rc_zreq > 0) zr = std::min<int64_t>(P->rc_zreq, std::max<int64_t>(1, m0 - 1));
+        nzr = std::max<int64_t>(1, (m0 - 1 + zr - 1) / zr);
+    }
+    L.rc_zc[1] = (int)zr;
+    L.rc_nzc[1] = (int)nzr;
+    const int64_t items_r = (int64_t)Sr * nb * nzr;
+    L.rc_grid[1] = (int)std::min<int64_t>((items_r + kRcWarps - 1) / kRcWarps, (int64_t)bx * P->num_sms);
+    if (items_s >= (int64_t(1) << 31) || items_r >= (int64_t(1) << 31)) return cudaSuccess;
+    L.rc_q[0] = qs;
+    L.rc_q[1] = qr;
+    L.rc_s[0] = Ss;
+    L.rc_s[1] = Sr;
+    L.rc_xs = xs;
+    return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -837,6 +1000,7 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
             lv.w_off[q] = lv.k_off[q] = lv.t_off[q] = 0;
             lv.kuni32[q] = lv.kuni64[q] = 0;
         }
+        lv.wuni2 = 0;
         for (int k = 0; k < nd; ++k) {
             const int q = 3 - nd + k;
             const int64_t nf = (n[k] - 1) / stride + 1;
@@ -845,6 +1009,11 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
             lv.n[q] = nf;
             lv.m[q] = (nf - 1) / 2 + 1;
             build_dim_tables(xf, tab, &lv.w_off[q], &lv.k_off[q], &lv.t_off[q]);
+            if (q == 2) {
+                lv.wuni2 = 1;
+                for (int64_t i = 1; i + 1 < nf; i += 2)
+                    if (tab[lv.w_off[q] + 2 * i] != 0.5 || tab[lv.w_off[q] + 2 * i + 1] != 0.5) lv.wuni2 = 0;
+            }
             // interior K rows all equal (bitwise, in each table precision)
             lv.kuni32[q] = lv.kuni64[q] = 1;
             for (int64_t I = 2; I + 1 < lv.m[q]; ++I)
@@ -1008,8 +1177,28 @@ static cudaError_t configure_plan(mgard_plan *P)
         case MGARD_F64: err = configure_level<double, double>(P, lv, j == 0); break;
         default: err = configure_level<float, double>(P, lv, j == 0); break;
         }
+        if (err != cudaSuccess) break;
+        switch (P->dtype) {
+        case MGARD_F32: err = configure_rc<float, float>(P, lv, j == 0); break;
+        case MGARD_F64: err = configure_rc<double, double>(P, lv, j == 0); break;
+        default: err = configure_rc<float, double>(P, lv, j == 0); break;
+        }
     }
     if (err == cudaSuccess) err = configure_coop(P);
+    return err;
+}
+
+// Row-chunk configuration of every level again (after a tuning change).
+static cudaError_t configure_plan_rc(mgard_plan *P)
+{
+    cudaError_t err = cudaSuccess;
+    for (int j = 0; j < P->L && err == cudaSuccess; ++j) {
+        switch (P->dtype) {
+        case MGARD_F32: err = configure_rc<float, float>(P, P->lv[j], j == 0); break;
+        case MGARD_F64: err = configure_rc<double, double>(P, P->lv[j], j == 0); break;
+        default: err = configure_rc<float, double>(P, P->lv[j], j == 0); break;
+        }
+    }
     return err;
 }
 
@@ -1110,11 +1299,20 @@ size_t mgard_workspace_bytes(const mgard_plan *P) { return P ? P->ws_bytes : 0; 
 int mgard_plan_launches(const mgard_plan *P, int recompose)
 {
     if (!P) return -1;
-    // per level: one restriction + ndim solve sweeps + the element-wise
-    // kernel(s): interpolation (recompose) or coefficients + coarse placement
+    // per level: one restriction + ndim solve sweeps (one fewer where the
+    // row-chunk restriction solves along dim 2) + the element-wise
+    // kernel(s): interpolation (recompose) or coefficients + coarse
+    // placement; then one launch for the coarse levels.  Counted for a
+    // 16-byte aligned user array.
     const int tail = recompose ? 1 : 2;
-    if (P->coop_j < P->L) return P->coop_j * (1 + P->ndim + tail) + 1;
-    return P->small_j * (1 + P->ndim + tail) + (P->small_j < P->L ? 1 : 0);
+    const bool coop = P->coop_j < P->L;
+    const int J = coop ? P->coop_j : P->small_j;
+    int n = 0;
+    for (int j = 0; j < J; ++j) {
+        const bool xs = P->lv[j].rc_q[0] > 0 && !(P->rc_off & 2) && P->lv[j].rc_xs;
+        n += 1 + P->ndim - (xs ? 1 : 0) + tail;
+    }
+    return n + (J < P->L ? 1 : 0);
 }
 
 static mgard_status check_call(const mgard_plan *P, void *data, void *ws, size_t ws_bytes)
@@ -1261,6 +1459,17 @@ mgard_status mgard_plan_tune(mgard_plan *P, int level, int param, int value)
         if (value < 0) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: barrier poll limit");
         P->coop_spin = value;
         return MGARD_OK;
+    case 7:
+        if (value < 0 || value > 3) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: row-chunk switch");
+        P->rc_off = value;
+        return MGARD_OK;
+    case 9: {
+        if (value < 0) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: row-chunk planes per item");
+        P->rc_zreq = value;
+        cudaError_t e2 = configure_plan_rc(P);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "plan_tune: row-chunk configuration");
+        return MGARD_OK;
+    }
     case 4:
         if (value != 0 && value != 1) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: cooperative switch");
         P->coop_off = value != 0;
@@ -1289,6 +1498,9 @@ int mgard_plan_get_tune(const mgard_plan *P, int level, int param)
     case 4: return P->coop_off ? 1 : 0;
     case 5: return P->coop_j < P->L ? P->coop_j : -1;
     case 6: return P->coop_spin;
+    case 7: return P->rc_off;
+    case 9: return P->rc_zreq;
+    case 8: return L.rc_q[1] > 0 ? 32 * (16 / (int)(level == 0 ? P->elem_user : P->elem_ws)) * L.rc_q[1] : 0;
     default: return -1;
     }
 }

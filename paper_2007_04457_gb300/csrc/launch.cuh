@@ -87,4 +87,18 @@ cudaError_t launch_adj_even(int act, const AdjParams &p, cudaStream_t st);
 template <typename T, typename TW>
 cudaError_t launch_prolong(const ProlongParams &p, int num_sms, cudaStream_t st);
 
+
+// Row-chunk level kernels (rowchunk.cuh): kind 0 = sweep (mode MODE_DEC:
+// coefficients, MODE_REC: interpolation), kind 1 = load vector + coarse
+// gather (xs: with the dim-2 solve).  Q = sub-segments of 32 words per
+// segment (4-byte level arrays: 2 or 4, segments of 256 or 512 columns;
+// 8-byte: 4, segments of 256), hz = 3D, u = uniform interpolation weights (sweep) or
+// K_2 rows (restriction) along dim 2.
+template <typename T, typename TW>
+cudaError_t rc_occupancy(int kind, int Q, int mode, bool hz, bool u, bool xs, int S, int *blocks_per_sm);
+
+template <typename T, typename TW>
+cudaError_t launch_rc(int kind, int Q, int mode, bool hz, bool u, bool xs, const RcParams &p, int grid,
+                      cudaStream_t st);
+
 }  // namespace mg

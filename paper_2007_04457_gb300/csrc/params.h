@@ -81,4 +81,30 @@ struct ProlongParams {
                              // kernel walks its own strips of 32 columns x 64 rows)
 };
 
+
+// Row-chunk level kernels (rowchunk.cuh): a warp takes one segment of 32 C
+// fine columns of a row (lane L: columns C L .. C L + C - 1, plus the
+// segment's closing column for the last segment), so every row is moved in
+// aligned 16-byte words.  Level arrays are 16-byte aligned; n1 - 1 is a
+// multiple of 8 and n2 - 1 = 32 C S.
+constexpr int kRcWarps = 4;  // warps per block of the row-chunk kernels
+constexpr int kRcRows = 2;   // coarse rows per row-chunk restriction item
+// row-chunk kernels kept out by default (bit 0 sweeps, bit 1 restriction):
+// the restriction is measured slower than the strip kernel + dim-2 solve
+constexpr int kRcDefaultOff = 2;
+
+struct RcParams {
+    void *A;                   // level array (type T), n0 x n1 x n2
+    void *F;                   // load vector on N_{l-1} (type TW)
+    void *V;                   // coarse values (type TW)
+    int n0, n1, n2, m0, m1, m2;
+    int S;                     // segments per row
+    int nb;                    // row items: coarse rows (sweep) or row blocks (restriction)
+    int zchunk, nzc;           // coarse intervals / planes per chunk, chunk count
+    int nitems;                // S * nb * nzc
+    const void *w0, *w1, *w2;  // interpolation weight pairs per fine node (type T)
+    const void *k0, *k1, *k2;  // K = P^T M_l rows, 5 per coarse node (type T)
+    const void *fx;            // LU factors of M_{l-1} along dim 2, 3 per coarse node (type TW)
+};
+
 }  // namespace mg
