@@ -63,18 +63,59 @@ def algorithmic_bytes(shape, L, S):
 
 
 def kernel_bytes(kind, shape, S, SW):
-    """Compulsory bytes of one finest-level launch of a kernel kind."""
+    """Compulsory bytes of one finest-level launch of a kernel kind: what the
+    kernel must read and write at least (M = finest nodes, Mc = coarse)."""
     M = level_nodes(shape, 1)
     Mf, Mc = M[0], M[1]
     return {
-        0: Mf * S + 2 * Mc * SW,                   # read level, write F and V
-        1: Mf * S + 2 * Mc * SW,                   # read level, write F and V
+        0: Mf * S + 2 * Mc * SW,                   # read the level, write F and V
+        1: Mf * S + 2 * Mc * SW,                   # read the level, write F and V
         2: 2 * Mc * SW,                            # read + write F
         3: 3 * Mc * SW,                            # read F, read + write V
         4: 2 * Mf * S,                             # read + write the level
-        5: 2 * Mf * S + Mc * SW,                   # read coefficients + V, write level
+        5: 2 * Mf * S + Mc * (SW - S),             # read coefficients (not the coarse nodes) and V, write the level
         6: Mc * SW + Mc * S,                       # read V, write the coarse nodes
     }[kind]
+
+
+# kernel identities of the finest-level launch kinds: the restriction is one
+# kernel for both directions, the other kinds one kernel each
+KERNEL_OF_KIND = {0: "restriction", 1: "restriction", 2: "solve x/y", 3: "solve z + correction",
+                  4: "coefficient sweep", 5: "interpolation sweep", 6: "coarse placement"}
+
+
+def kernel_groups(prof, shape, S, SW):
+    """Per kernel identity: launches, total ms and compulsory bytes of the
+    finest-level launches in a profiled pass."""
+    out = {}
+    for _, kind, lvl, c, t in prof:
+        if kind not in KERNEL_OF_KIND:
+            continue
+        g = out.setdefault(KERNEL_OF_KIND[kind], {"launches": 0, "ms": 0.0, "bytes": 0})
+        g["launches"] += c
+        g["ms"] += t
+        g["bytes"] += c * kernel_bytes(kind, shape, S, SW)
+    return out
+
+
+def fp64_flops(shape, L):
+    """FP64 floating-point operations of one decompose + recompose, counted
+    per node as the kernels evaluate them (a two-point interpolation = 3,
+    a stencil tap = 2, a Thomas step = 2 forward + 3 backward):
+      coefficients / interpolation: 4 per level node (the separable
+        interpolant and the subtraction or addition), each direction;
+      load vector: 5 taps (2 flops each) per coarse column and fine row
+        (2 on the rows of coarse nodes), 2.5 taps per coarse column and
+        fine row along dim 1, 2.5 per coarse column and row and fine plane
+        along dim 0: about 9 per fine node, each direction;
+      solves: 5 per coarse node and dimension, each direction;
+      correction: 1 per coarse node, each direction."""
+    M = level_nodes(shape, L)
+    d = len(shape)
+    total = 0
+    for j in range(L):
+        total += 2 * (4 * M[j] + 9 * M[j] + 5 * d * M[j + 1] + M[j + 1])
+    return total
 
 
 def measured_peak():
@@ -88,9 +129,10 @@ def measured_peak():
 # Headers that hold nothing but the device code of other kernels: a change
 # there cannot alter the code, launch or memory traffic of a kernel defined
 # elsewhere.  Keys: the kernel names recorded in profiles/traffic.txt.
-_OWN_HEADER = {"coef": "sweep.cuh", "interp": "sweep.cuh", "prolong": "prolong.cuh"}
+_OWN_HEADER = {"coefficient sweep": "rowchunk.cuh", "interpolation sweep": "rowchunk.cuh",
+               "restriction": "restrict_strip.cuh", "prolong": "prolong.cuh"}
 _DEVICE_ONLY_HEADERS = ("adjoint.cuh", "multi.cuh", "prolong.cuh", "restrict.cuh", "restrict_strip.cuh",
-                        "small.cuh", "solve.cuh", "sweep.cuh")
+                        "rowchunk.cuh", "small.cuh", "solve.cuh", "sweep.cuh")
 
 
 def kernel_source_hash(kernel=None):
@@ -117,7 +159,9 @@ def recorded_traffic(kernel_name):
         return None
     cur = kernel_source_hash(kernel_name)
     for line in open(path):
-        parts = line.split()
+        if line.startswith("#"):
+            continue
+        parts = line.rstrip("\n").split("\t")
         if len(parts) >= 3 and parts[0] == kernel_name and parts[1] == cur:
             return float(parts[2])
     return None
@@ -138,7 +182,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -210,65 +254,107 @@ def job_gbs(bytes_per_rank_step, steps, world, ms_max):
     return world * bytes_per_rank_step * steps / (ms_max / 1e3) / 1e9
 
 
-def run_reference(args):
-    """The oracle (plain FP64 CPU code) on the host cores, same metric."""
-    world, rank, _ = dist_setup()
-    if rank != 0:
-        return
-    import numpy as np
-
+def _oracle_worker(job):
+    """One host process: the FP64 oracle on its own n^3 sub-field (seeded by
+    its index, the generator of the GPU runs), decompose and recompose timed
+    separately; returns (decompose s, recompose s, bytes)."""
+    n, seed, reps = job
     import oracle
     from paper_2007_04457_gb300 import synth
 
-    n = 129
     shape = (n, n, n)
-    L = 7
-    u = synth.sinusoid_field(shape, N_MODES, SEED, dtype=np.float32).astype(np.float64)
-    dec_b, rec_b = algorithmic_bytes(shape, L, 4)
-    for _ in range(args.warmup):
-        oracle.recompose(oracle.decompose(u))
-    times = []
-    for _ in range(args.steps):
+    u = synth.sinusoid_field(shape, N_MODES, seed, dtype=np.float32).astype(np.float64)
+    td = tr = 0.0
+    for _ in range(reps):
         t0 = time.perf_counter()
-        oracle.recompose(oracle.decompose(u))
-        times.append(time.perf_counter() - t0)
-    total = sum(times)
-    value = (dec_b + rec_b) * args.steps / total / 1e9
+        c = oracle.decompose(u)
+        t1 = time.perf_counter()
+        oracle.recompose(c)
+        t2 = time.perf_counter()
+        td += t1 - t0
+        tr += t2 - t1
+    d, r = algorithmic_bytes(shape, (n - 1).bit_length() - 1, 4)
+    return td, tr, reps * (d + r), reps * d, reps * r
+
+
+class OraclePool:
+    """The host cores as independent partitions (one sub-field per core, as
+    the paper's per-GPU partitions): a pool of `spawn`ed processes, one per
+    core, each timing the oracle on its own sub-field."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+
+    def run(self, n, reps, seed0=SEED):
+        """Aggregate GB/s (algorithmic bytes of every partition over the
+        slowest partition's time), and decompose / recompose GB/s."""
+        res = self.pool.map(_oracle_worker, [(n, seed0 + i, reps) for i in range(self.cores)])
+        t = max(a + b for a, b, _, _, _ in res)
+        td = max(a for a, _, _, _, _ in res)
+        tr = max(b for _, b, _, _, _ in res)
+        tot = sum(x[2] for x in res)
+        return {"gbs": tot / t / 1e9, "decompose_gbs": sum(x[3] for x in res) / td / 1e9,
+                "recompose_gbs": sum(x[4] for x in res) / tr / 1e9, "seconds": t}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def run_reference(args):
+    """The oracle (plain FP64 CPU code) on every host core, same metric: each
+    step refactors one 129^3 sub-field per core (independent partitions)."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    pool = OraclePool()
+    n = 129
+    for _ in range(args.warmup):
+        pool.run(n, 1)
+    total = 0.0
+    bytes_ = 0.0
+    dg, rg = [], []
+    for _ in range(args.steps):
+        r = pool.run(n, 1)
+        total += r["seconds"]
+        bytes_ += r["gbs"] * r["seconds"] * 1e9
+        dg.append(r["decompose_gbs"])
+        rg.append(r["recompose_gbs"])
+    pool.close()
+    value = bytes_ / total / 1e9
+    sample = f"{pool.cores} x 129^3 sub-fields of the same generator per step (one per core), FP64 oracle"
     line = {
         "impl": "reference", "metric": "decompose+recompose GB/s (algorithmic bytes) at 513^3 FP32",
         "value": value, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "513^3 FP32 decompose+recompose, 9 levels",
-                   "sample": "129^3 sub-grid of the same generator per step, 7 levels"},
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": "129^3, FP64 oracle, one decompose+recompose per step"},
+        "config": {"workload": "513^3 FP32 decompose+recompose, 9 levels", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": pool.cores, "kind": "oracle",
+                         "sample": sample, "decompose_gbs": statistics.median(dg),
+                         "recompose_gbs": statistics.median(rg)},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def cpu_baseline_sample():
-    """Oracle on a bounded sample (257^3 sub-grid, FP64, one thread)."""
-    import numpy as np
-
-    import oracle
-    from paper_2007_04457_gb300 import synth
-
-    n = 257
-    shape = (n, n, n)
-    u = synth.sinusoid_field(shape, N_MODES, SEED, dtype=np.float32).astype(np.float64)
-    dec_b, rec_b = algorithmic_bytes(shape, 8, 4)
-    t0 = time.perf_counter()
-    reps = 0
-    while True:
-        oracle.recompose(oracle.decompose(u))
-        reps += 1
-        if time.perf_counter() - t0 > 8.0 or reps >= 3:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": (dec_b + rec_b) * reps / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"257^3 sub-grid of the same generator, FP64 oracle, {reps} decompose+recompose"}
+    """The oracle on the host cores: one 257^3 sub-field per core at once
+    (every core), and one alone (one core); decompose and recompose timed
+    separately."""
+    pool = OraclePool()
+    allc = pool.run(257, 1)
+    pool.close()
+    one = OraclePool(1)
+    single = one.run(257, 1)
+    one.close()
+    return {"value": allc["gbs"], "unit": "GB/s", "cores": pool.cores, "kind": "oracle",
+            "sample": f"{pool.cores} x 257^3 sub-fields of the same generator (one per core), FP64 oracle, "
+                      "one decompose+recompose each",
+            "decompose_gbs": allc["decompose_gbs"], "recompose_gbs": allc["recompose_gbs"],
+            "single_core": {"value": single["gbs"], "decompose_gbs": single["decompose_gbs"],
+                            "recompose_gbs": single["recompose_gbs"], "sample": "one 257^3 sub-field"}}
 
 
 def _timed(torch, stream, fn, steps):
@@ -435,24 +521,66 @@ def run_nonuniform(torch, mgard, synth, dev, stream, rank, world, max_over_ranks
     return out
 
 
+def level_masks(torch, shape, L, dev):
+    """Boolean device masks of N_l \\ N_{l-1} for l = L..1, and of N_0."""
+    for l in range(L, -1, -1):
+        s = 1 << (L - l)
+        on = coarse = None
+        for k, n in enumerate(shape):
+            idx = torch.arange(n, device=dev)
+            sh = [1] * len(shape)
+            sh[k] = n
+            a = (idx % s == 0).view(sh)
+            b = (idx % (2 * s) == 0).view(sh)
+            on = a if on is None else on & a
+            coarse = b if coarse is None else coarse & b
+        yield l, (on & ~coarse) if l > 0 else on
+
+
 def run_mixed(torch, mgard, synth, dev, stream, rank, world, max_over_ranks):
     """1025 x 1025 x 513 FP32 field (12 modes + Gaussian blob) per rank, FP64
-    solves and coarse-level accumulation, 9 levels; whole-job GB/s."""
+    solves and coarse-level accumulation, 9 levels; whole-job GB/s.  The
+    error of the decomposition per level (the coefficients of N_l \\ N_{l-1}
+    and the coarsest values: max and RMS of |mixed - reference| / max|u|)
+    is taken on the same field against the FP64 path of this library, which
+    the parity tests hold within 1e-12 of the FP64 oracle."""
     shape = (1025, 1025, 513)
     plan = mgard.Plan(shape, dtype="f32_mixed")
     u = synth.sinusoid_field_torch(shape, 12, 3 + rank, dev, torch.float32, blob=True)
     ws = plan.workspace(dev)
+    # per-level error of one decomposition against the FP64 path
+    ref = u.double()
+    p64 = mgard.Plan(shape, dtype="f64")
+    p64.decompose(ref, p64.workspace(dev), stream)
+    got = u.clone()
+    plan.decompose(got, ws, stream)
+    torch.cuda.synchronize()
+    scale = float(u.abs().max())
+    rows = []
+    for l, mt in level_masks(torch, shape, plan.levels, dev):
+        d = (got[mt].double() - ref[mt]) / scale
+        rows.append({"level": l, "max": float(d.abs().max()), "rms": float(d.pow(2).mean().sqrt())})
+        del mt, d
+    del ref, got, p64
+    torch.cuda.empty_cache()
     step = lambda: (plan.decompose(u, ws, stream), plan.recompose(u, ws, stream))
     for _ in range(3):
         step()
     ms = max_over_ranks(_timed(torch, stream, step, 5))
     d, r = algorithmic_bytes(shape, plan.levels, 4)
     out = {"value": job_gbs(d + r, 1, world, ms), "unit": "GB/s", "ms_per_step": ms, "levels": plan.levels,
-           "workload": "1025x1025x513 FP32 field, FP64 solves and coarse arrays"}
+           "workload": "1025x1025x513 FP32 field, FP64 solves and coarse arrays",
+           "per_level_error": {"reference": "FP64 path of this library (within 1e-12 of the FP64 oracle)",
+                               "normalised_by": "max|u|", "rows": rows,
+                               "max": max(x["max"] for x in rows)}}
     del u, ws
     plan.close()
     torch.cuda.empty_cache()
     return out
+
+
+def plan_tune_get(mgard, plan, param):
+    return mgard.mgard_plan_get_tune(plan.handle, 0, param)
 
 
 def run_case(spec):
@@ -494,8 +622,8 @@ def main():
         return run_case(sys.argv[sys.argv.index("--case") + 1:])
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -538,45 +666,67 @@ def main():
         plan.decompose(u, ws, stream)
         plan.recompose(u, ws, stream)
 
+    # clocks are sampled from the warm-up on (the timed region alone is
+    # shorter than the sampling interval at the default step count)
+    clk = ClockSampler(local).__enter__()
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
 
-    # timed region: whole steps, with event pairs around the finest-level kernels
-    mgard.mgard_profile_enable(plan.handle, 1)
-    mgard.mgard_profile_read(plan.handle)
+    # timed region: whole steps, no per-kernel events
     barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    try:
         e0.record(stream)
         for _ in range(args.steps):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
+    finally:
+        clk.__exit__(None, None, None)
     barrier()
     ms = e0.elapsed_time(e1)
     ms = max_over_ranks(ms)
+
+    # per-kernel times in a separate pass: the plan's event pairs around the
+    # finest-level launches (on the stream the kernels run on)
+    kp = max(3, args.steps // 4)
+    mgard.mgard_profile_enable(plan.handle, 1)
+    mgard.mgard_profile_read(plan.handle)
+    ep0 = torch.cuda.Event(enable_timing=True)
+    ep1 = torch.cuda.Event(enable_timing=True)
+    ep0.record(stream)
+    for _ in range(kp):
+        step()
+    ep1.record(stream)
+    torch.cuda.synchronize()
+    ms_prof = ep0.elapsed_time(ep1)
     prof = [(KIND_NAMES[k], k, lv, c, t) for k, lv, c, t in mgard.mgard_profile_read(plan.handle)]
     mgard.mgard_profile_enable(plan.handle, 0)
 
     value = job_gbs(dec_b + rec_b, args.steps, world, ms)
     peak, peak_src = measured_peak()
-    top = max(prof, key=lambda r: r[4]) if prof else None
+    groups = kernel_groups(prof, SHAPE, S, S)
     roof = None
-    if top is not None:
-        name, kind, lvl, c, t = top
-        per_launch_ms = t / c
-        kb = kernel_bytes(kind, SHAPE, S, S)
+    if groups:
+        name, g = max(groups.items(), key=lambda kv: kv[1]["ms"])
+        per_launch_ms = g["ms"] / g["launches"]
+        kb = g["bytes"] / g["launches"]
         achieved = kb / (per_launch_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": f"{name} (finest level)", "achieved": achieved,
+        fn = {"restriction": "k_restrict_strip" if plan_tune_get(mgard, plan, 7) & 2 else "k_rc_restrict",
+              "coefficient sweep": "k_rc_sweep<MODE_DEC>", "interpolation sweep": "k_rc_sweep<MODE_REC>",
+              "solve x/y": "k_solve_chunks", "solve z + correction": "k_solve_lines",
+              "coarse placement": "k_scatter"}.get(name, name)
+        roof = {"bound": "hbm", "kernel": f"{name} ({fn}, finest level, both directions)", "achieved": achieved,
                 "peak": peak, "peak_source": f"{peak_src} hbm_gbs", "unit": "GB/s",
                 "frac": achieved / peak, "traffic": recorded_traffic(name),
                 "algorithmic_bytes_per_launch": kb, "ms_per_launch": per_launch_ms,
-                "share_of_step": t / ms}
+                "launches_per_step": g["launches"] / kp, "share_of_step": g["ms"] / ms_prof}
 
-    finest_share = {f"{r[0]}": round(r[4] / ms, 4) for r in prof}
+    finest_share = {k: round(v["ms"] / ms_prof, 4) for k, v in groups.items()}
+    kernel_frac = {k: round(v["bytes"] / (v["ms"] / 1e3) / 1e9 / peak, 3) for k, v in groups.items()}
 
     # FP64 alongside (same workload in double precision)
     fp64 = None
@@ -599,8 +749,20 @@ def main():
         torch.cuda.synchronize()
         ms64 = max_over_ranks(e0.elapsed_time(e1))
         d64, r64 = algorithmic_bytes(SHAPE, L, 8)
+        fl = fp64_flops(SHAPE, L)
+        tf = mgard.mgard_probe_fp64_peak(stream.cuda_stream)
+        t_bytes = (d64 + r64) / (peak * 1e9)
+        t_flops = fl / (tf * 1e12)
+        step_s = ms64 / k64 / 1e3
         fp64 = {"value": job_gbs(d64 + r64, k64, world, ms64), "unit": "GB/s",
-                "ms_per_step": ms64 / k64, "steps": k64}
+                "ms_per_step": ms64 / k64, "steps": k64,
+                "roofline": {"bound": "fp64" if t_flops > t_bytes else "hbm",
+                             "bytes_per_step": d64 + r64, "flops_per_step": fl,
+                             "hbm_peak_gbs": peak, "fp64_peak_tflops": tf,
+                             "fp64_peak_source": "measured by mgard_probe_fp64_peak (FMA chains, CUDA events)",
+                             "bound_ms": 1e3 * max(t_bytes, t_flops),
+                             "frac": max(t_bytes, t_flops) / step_s,
+                             "achieved_tflops": fl / step_s / 1e12}}
         del u64, ws64, plan64
         torch.cuda.empty_cache()
         u = synth.sinusoid_field_torch(SHAPE, N_MODES, SEED + rank, dev, torch.float32)
@@ -711,6 +873,7 @@ def main():
                        "parallelism": f"independent fields, {world} GPU(s)"},
             "roofline": roof,
             "finest_level_kernel_share": finest_share,
+            "finest_level_kernel_frac_of_hbm": kernel_frac,
             "fp64": fp64,
             "mixed": mixed,
             "batched": batched,

@@ -274,13 +274,26 @@ MGARD_API mgard_status mgard_batch_recompose(mgard_batch *batch, void *const *d_
  * the tables and workspace regions it then reads.  All calls on a device
  * share the array, so calls must not overlap: two calls on different streams,
  * or from different host threads, without an order between them, race on
- * it.  Calls in sequence on one stream are safe.  The first call on each
- * device looks up the array's address (cudaGetSymbolAddress) and caches it;
- * make that first call before any stream capture.  The tables are uploaded
- * from pageable host memory on every call. */
+ * it.  Calls in sequence on one stream are safe.  Every call looks up the
+ * current device's array (cudaGetSymbolAddress).  The tables are uploaded
+ * from pageable host memory on every call, so the call may block the host
+ * until the work queued before it on `stream` has run; for the same reason
+ * it cannot be captured into a CUDA graph: on a stream under capture it
+ * returns MGARD_ERR_INVALID_ARG and queues nothing.  It runs no kernel that
+ * waits on other blocks (the coarse levels take the single-block or
+ * per-level kernels, never the cooperative one), so no wait can run out. */
 #define MGARD_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 MGARD_API mgard_status mgard_decompose_noalloc(int ndim, const int64_t *dims, int nlevels, mgard_dtype dtype,
                                                void *d_data, void *stream);
+
+/* ---- Measurement support --------------------------------------------------
+ * FP64 fused multiply-add rate of the current device in TFLOP/s (2 flops per
+ * FMA), measured with CUDA events on `stream` over one launch of
+ * independent FMA chains on every SM (about a million FMAs per thread);
+ * synchronizes `stream`.  The paper has no counterpart: it is the
+ * denominator of the FP64 compute roofline of the benchmark.
+ *   tflops   out, host pointer (MGARD_ERR_INVALID_ARG when NULL) */
+MGARD_API mgard_status mgard_probe_fp64_peak(double *tflops, void *stream);
 
 /* Human-readable name of a status code (static string). */
 MGARD_API const char *mgard_status_string(mgard_status status);

@@ -1242,6 +1242,10 @@ mgard_status mg_plan_in_place(int ndim, const int64_t *dims, int nlevels, mgard_
         delete P;
         return cuda_fail(err, "static plan");
     }
+    // no cooperative kernel: its grid-barrier waits report a timeout through
+    // the plan's workspace, which does not outlive this call
+    P->coop_off = true;
+    P->coop_j = P->L;
     *out = P;
     return MGARD_OK;
 }

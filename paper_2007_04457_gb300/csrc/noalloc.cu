@@ -11,7 +11,6 @@
 // call allocates or frees device memory.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "mgard.h"
@@ -26,35 +25,11 @@ mgard_status mg_decompose_with(const mgard_plan *P, void *d_data, void *d_ws, si
 namespace {
 
 constexpr size_t kScratchBytes = MGARD_NOALLOC_SCRATCH_BYTES;
-constexpr int kMaxDevices = 64;
 
 // The scratch: one copy per device, made when this module is loaded on it.
 // Every call writes the tables and workspace regions it reads, so nothing
 // here has to start at zero.
 static __device__ __align__(256) unsigned char scratch[kScratchBytes];
-
-std::mutex g_mu;
-void *g_ptr[kMaxDevices] = {};
-
-// Address of the current device's scratch, looked up once per device (with
-// that device current) and cached.
-mgard_status scratch_of_current_device(void **out)
-{
-    int dev = -1;
-    cudaError_t err = cudaGetDevice(&dev);
-    if (err != cudaSuccess) return mg_cuda_fail(err, "mgard_decompose_noalloc: cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices)
-        return mg_fail(MGARD_ERR_INVALID_ARG, "mgard_decompose_noalloc: device ordinal beyond 63");
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_ptr[dev]) {
-        void *p = nullptr;
-        err = cudaGetSymbolAddress(&p, scratch);
-        if (err != cudaSuccess) return mg_cuda_fail(err, "mgard_decompose_noalloc: cudaGetSymbolAddress");
-        g_ptr[dev] = p;
-    }
-    *out = g_ptr[dev];
-    return MGARD_OK;
-}
 
 }  // namespace
 
@@ -62,13 +37,21 @@ extern "C" mgard_status mgard_decompose_noalloc(int ndim, const int64_t *dims, i
                                                 void *d_data, void *stream)
 {
     if (!d_data) return mg_fail(MGARD_ERR_INVALID_ARG, "mgard_decompose_noalloc: d_data is NULL");
-    void *base = nullptr;
-    mgard_status s = scratch_of_current_device(&base);
-    if (s != MGARD_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the tables are copied from host vectors that this call frees on return
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t err = cudaStreamIsCapturing(st, &cap);
+    if (err != cudaSuccess) return mg_cuda_fail(err, "mgard_decompose_noalloc: cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone)
+        return mg_fail(MGARD_ERR_INVALID_ARG, "mgard_decompose_noalloc: the stream is being captured; this call cannot be");
+    // the current device's copy of the scratch (host code only sees a
+    // stand-in for the symbol; the lookup is cheap, so it is not cached)
+    void *base = nullptr;
+    err = cudaGetSymbolAddress(&base, scratch);
+    if (err != cudaSuccess) return mg_cuda_fail(err, "mgard_decompose_noalloc: cudaGetSymbolAddress");
     mgard_plan *P = nullptr;
     size_t used = 0;
-    s = mg_plan_in_place(ndim, dims, nlevels, dtype, base, kScratchBytes, st, &P, &used);
+    mgard_status s = mg_plan_in_place(ndim, dims, nlevels, dtype, base, kScratchBytes, st, &P, &used);
     if (s != MGARD_OK) return s;
     s = mg_decompose_with(P, d_data, static_cast<unsigned char *>(base) + used, kScratchBytes - used, st);
     // the launches hold copies of what they need; the tables stay in the scratch

@@ -88,7 +88,10 @@ struct ProlongParams {
 // aligned 16-byte words.  Level arrays are 16-byte aligned; n1 - 1 is a
 // multiple of 8 and n2 - 1 = 32 C S.
 constexpr int kRcWarps = 4;  // warps per block of the row-chunk kernels
-constexpr int kRcRows = 2;   // coarse rows per row-chunk restriction item
+// coarse rows per row-chunk restriction item (a kernel template argument:
+// this toolkit's device compiler stops on the kernel when it derives the
+// count from its other arguments); four rows per item were measured slower
+constexpr int kRcRows = 2;
 // row-chunk kernels kept out by default (bit 0 sweeps, bit 1 restriction):
 // the restriction is measured slower than the strip kernel + dim-2 solve
 constexpr int kRcDefaultOff = 2;

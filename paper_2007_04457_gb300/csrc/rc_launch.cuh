@@ -28,8 +28,9 @@ Fn sweep_fn(int mode, bool hz, bool wu)
 template <typename T, typename TW, int Q, bool HZ>
 Fn restrict_fn_hz(bool ku, bool xs)
 {
-    if (ku) return xs ? k_rc_restrict<T, TW, Q, HZ, true, true> : k_rc_restrict<T, TW, Q, HZ, true, false>;
-    return xs ? k_rc_restrict<T, TW, Q, HZ, false, true> : k_rc_restrict<T, TW, Q, HZ, false, false>;
+    constexpr int TY = kRcRows;
+    if (ku) return xs ? k_rc_restrict<T, TW, Q, HZ, true, true, TY> : k_rc_restrict<T, TW, Q, HZ, true, false, TY>;
+    return xs ? k_rc_restrict<T, TW, Q, HZ, false, true, TY> : k_rc_restrict<T, TW, Q, HZ, false, false, TY>;
 }
 
 template <typename T, typename TW, int Q>

@@ -33,7 +33,7 @@
 // k_rc_restrict (both directions, Section III-A-2):
 //   F = (K_0 (x) K_1 (x) K_2) C,  C = A on N_l \ N_{l-1}, 0 on N_{l-1}
 //   V = A restricted to N_{l-1}
-// for a block of kRcRows coarse rows of one segment, streaming the planes of
+// for a block of TY coarse rows of one segment, streaming the planes of
 // a chunk: per fine row the dim-2 stencil of the lane's coarse columns (two
 // per word of 4-byte elements, one of 8-byte ones), the dim-1 stencil into
 // register accumulators, the dim-0 stencil into rolling accumulators over
@@ -678,12 +678,11 @@ inline size_t rc_restrict_smem(int S, bool ku, bool xs)
     return b;
 }
 
-template <typename T, typename TW, int Q, bool HZ, bool KU, bool XS>
+template <typename T, typename TW, int Q, bool HZ, bool KU, bool XS, int TY>
 __global__ void __launch_bounds__(32 * kRcWarps) k_rc_restrict(RcParams p)
 {
     constexpr int E = VecE<T>::value, W = 32 * E, NC = E / 2, WC = 32 * NC;
     constexpr int C2 = NC * Q;      // coarse nodes per lane and segment
-    constexpr int TY = kRcRows;
     constexpr int NR = 2 * TY + 3;  // fine rows feeding TY coarse rows
     constexpr int PPZ = HZ ? 2 * NR : NR;  // row positions per coarse plane (odd plane, even plane)
     constexpr int D = kRcRestrictD, NSLOT = D + 1;

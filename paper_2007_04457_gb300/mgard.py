@@ -72,6 +72,7 @@ def _load() -> ctypes.CDLL:
         "mgard_batch_decompose": ([vp, ctypes.POINTER(vp), vp, sz, vp], ctypes.c_int),
         "mgard_batch_recompose": ([vp, ctypes.POINTER(vp), vp, sz, vp], ctypes.c_int),
         "mgard_decompose_noalloc": ([ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
+        "mgard_probe_fp64_peak": ([ctypes.POINTER(ctypes.c_double), vp], ctypes.c_int),
         "mgard_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "mgard_last_error": ([], ctypes.c_char_p),
     }
@@ -197,6 +198,13 @@ def mgard_decompose_noalloc(ndim, dims, nlevels, dtype, d_data: int, stream: int
     static scratch (no device allocation; calls must not overlap)."""
     d = (ctypes.c_int64 * ndim)(*[int(v) for v in dims])
     _check(LIB.mgard_decompose_noalloc(ndim, d, nlevels, dtype, d_data, stream), "mgard_decompose_noalloc")
+
+
+def mgard_probe_fp64_peak(stream: int) -> float:
+    """FP64 FMA rate of the current device in TFLOP/s (measurement support)."""
+    out = ctypes.c_double(0.0)
+    _check(LIB.mgard_probe_fp64_peak(ctypes.byref(out), stream), "mgard_probe_fp64_peak")
+    return out.value
 
 
 def mgard_status_string(status: int) -> str:

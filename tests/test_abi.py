@@ -80,3 +80,5 @@ def test_null_arguments(lib):
     assert lib.mgard_plan_destroy(None) == 0
     lib.mgard_workspace_bytes.restype = ctypes.c_size_t
     assert lib.mgard_workspace_bytes(None) == 0
+    lib.mgard_probe_fp64_peak.restype = ctypes.c_int
+    assert lib.mgard_probe_fp64_peak(None, None) == 1

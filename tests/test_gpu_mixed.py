@@ -65,3 +65,29 @@ def test_mixed_precision_per_level_errors():
     # the FP64 coarse arrays pay off on the coarse levels
     coarse = lambda e: sum(e[l][1] ** 2 for l in range(0, 3))
     assert coarse(errs["f32_mixed"]) <= coarse(errs["f32"])
+
+
+def test_mixed_precision_sides_1025_against_oracle():
+    """1025 x 1025 x 65: two sides of 1025 nodes, where the mixed scheme's
+    FP64 coarse arrays and solves matter most (6 levels), against the FP64
+    oracle: every level within 1e-5 of max|u|, and the recomposition of the
+    oracle's coefficients back to the field."""
+    from paper_2007_04457_gb300 import mgard
+    shape = (1025, 1025, 65)
+    u = synth.sinusoid_field(shape, 12, seed=3, blob=True, dtype=np.float32)
+    want = oracle.decompose(u.astype(np.float64))
+    scale = float(np.abs(u).max())
+    plan = mgard.Plan(shape, dtype="f32_mixed")
+    t = torch.from_numpy(u).cuda()
+    plan.decompose(t)
+    torch.cuda.synchronize()
+    errs = per_level_errors(t.cpu().numpy().astype(np.float64), want, plan.levels, scale)
+    print("\nlevel  mixed max / rms (1025 x 1025 x 65)")
+    for l in range(plan.levels, -1, -1):
+        print(f"{l:5d}  {errs[l][0]:.2e} / {errs[l][1]:.2e}")
+    assert max(v[0] for v in errs.values()) <= 1e-5
+    t.copy_(torch.from_numpy(want.astype(np.float32)))
+    plan.recompose(t)
+    torch.cuda.synchronize()
+    back = t.cpu().numpy().astype(np.float64)
+    assert np.abs(back - u).max() / scale <= 1e-5

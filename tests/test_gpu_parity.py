@@ -157,3 +157,21 @@ def test_full_size_513_cubed_fp32_matches_oracle():
     torch.cuda.synchronize()
     back = t.cpu().numpy().astype(np.float64)
     assert _relerr(back, u.astype(np.float64)) <= 1e-5
+
+
+def test_full_size_513_cubed_fp64_matches_oracle():
+    """513^3 FP64, 9 levels (the benchmark's FP64 line), against the FP64
+    oracle on the whole array at 1e-12, and the round trip."""
+    mg = _mg()
+    shape = (513, 513, 513)
+    u = synth.sinusoid_field(shape, 12, seed=2, dtype=np.float64)
+    plan = mg.Plan(shape, dtype="f64")
+    t = torch.from_numpy(u).cuda()
+    plan.decompose(t)
+    torch.cuda.synchronize()
+    got = t.cpu().numpy()
+    want = oracle.decompose(u)
+    assert _relerr(got, want) <= 1e-12
+    plan.recompose(t)
+    torch.cuda.synchronize()
+    assert _relerr(t.cpu().numpy(), u) <= 1e-12

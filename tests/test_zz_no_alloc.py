@@ -4,8 +4,9 @@ scratch) against the plan-based mgard_decompose, through the C ABI.
 Two calls in a row on fresh copies of the field must each match the regular
 entry point within the parity tolerance (max relative error over the array:
 1e-5 FP32 / mixed, 1e-12 FP64); a shape beyond the scratch is rejected with
-MGARD_ERR_WORKSPACE and leaves the field untouched.  This file is collected
-last so that it also runs after every other GPU test in the same process.
+MGARD_ERR_WORKSPACE and leaves the field untouched; a call on a stream under
+capture is refused with MGARD_ERR_INVALID_ARG.  This file is collected last
+so that it also runs after every other GPU test in the same process.
 """
 import numpy as np
 import pytest
@@ -17,6 +18,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-12, "f32": 1e-5, "f32_mixed": 1e-5}
+INVALID_ARG = 1
 WORKSPACE = 3
 
 
@@ -87,3 +89,28 @@ def test_noalloc_rejects_shape_beyond_scratch():
     _noalloc(mg, small, -1, "f32")
     torch.cuda.synchronize()
     assert _relerr(small, want) <= TOL["f32"]
+
+
+def test_noalloc_refuses_stream_capture():
+    """The call uploads its tables from host memory it frees on return, so it
+    refuses a stream under capture before queueing anything; afterwards it
+    works as before."""
+    mg = _mg()
+    shape = (33, 33, 33)
+    u = torch.from_numpy(synth.sinusoid_field(shape, 12, seed=10, dtype=np.float32)).cuda()
+    t = u.clone()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    status = None
+    with torch.cuda.graph(g, stream=s):
+        try:
+            mg.mgard_decompose_noalloc(t.dim(), t.shape, -1, mg._DTYPE_CODES["f32"], t.data_ptr(), s.cuda_stream)
+        except mg.MgardError as e:
+            status = e.status
+    assert status == INVALID_ARG
+    torch.cuda.synchronize()
+    assert bool((t == u).all())
+    want = mg.Plan(shape, dtype="f32").decompose(u.clone())
+    _noalloc(mg, t, -1, "f32")
+    torch.cuda.synchronize()
+    assert _relerr(t, want) <= TOL["f32"]
