@@ -147,41 +147,66 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
-// elements of T in a slot: a field row segment (its Q W columns as words and
-// the word after) or a compact row of TW (WC Q + 2 values), 16-byte multiple
+// bytes of a slot: a field row segment (the word before it, its Q W
+// columns as words, the word after) or a compact row of TW (WC Q + 2
+// values), a 16-byte multiple
 template <typename T, typename TW, int Q>
 struct RingSlot {
     static constexpr int E = VecE<T>::value, W = 32 * E, NC = E / 2, WC = 32 * NC;
-    static constexpr int FIELD_B = (W * Q + E) * (int)sizeof(T);
+    static constexpr int FIELD_B = (W * Q + 2 * E) * (int)sizeof(T);
     static constexpr int COARSE_B = (WC * Q + 2) * (int)sizeof(TW);
     static constexpr int BYTES = ((FIELD_B > COARSE_B ? FIELD_B : COARSE_B) + 15) / 16 * 16;
 };
 
-// copy the aligned words of the row segment whose first column is seg, at
-// word offset a
+// Copy the aligned words of the row segment whose first column is seg (word
+// offset a): word w of the segment goes to slot word w + 1; lane L copies
+// words 32 q + L, lane 0 also the word after the segment and, when
+// `before`, the word before it.
 template <typename T, int Q>
-__device__ __forceinline__ void ring_copy_row(T *slot, const T *seg, int a, int L)
+__device__ __forceinline__ void ring_copy_row(T *slot, const T *seg, int a, int L, bool before)
 {
     constexpr int E = VecE<T>::value, W = 32 * E;
     const T *g = seg - a;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) cp_async16(slot + W * q + E * L, g + W * q + E * L);
-    if (L == 0) cp_async16(slot + W * Q, g + W * Q);
+    for (int q = 0; q < Q; ++q) cp_async16(slot + W * q + E * L + E, g + W * q + E * L);
+    if (L == 0) {
+        cp_async16(slot + W * Q + E, g + W * Q);
+        if (before) cp_async16(slot, g - E);
+    }
 }
 
-// the copied words back: w[q] = word 32 q + L, w[Q] = the word after (lane 0)
-template <typename T, int Q>
-__device__ __forceinline__ void ring_words(const T *slot, int L, T (&w)[Q + 1][VecE<T>::value])
+// Canonical windows of a row segment from its slot (every lane's copies
+// complete and visible: after the warp's barrier): v[q][H + i] = seg[W q +
+// E L + i], i = -H .. E, A = word offset of the segment.  The lane reads its
+// own word and its neighbours' from the slot.  Left-halo values of
+// sub-segment 0 of lane 0 are 0 at a row start (!left).
+template <typename T, int Q, int H, int A>
+__device__ __forceinline__ void rw_slot(const T *slot, int L, bool left, T (&v)[Q][H + VecE<T>::value + 1])
 {
     constexpr int E = VecE<T>::value, W = 32 * E;
+    static_assert(A >= 0 && A < E, "word offset");
+    // canonical i is element (i + A) mod E of slot word (own + 1) + floor((i + A) / E)
+    constexpr int DLO = (A - H >= 0) ? 0 : -((H - A + E - 1) / E);
+    constexpr int DHI = 1;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) ld16(slot + W * q + E * L, w[q]);
+    for (int q = 0; q < Q; ++q) {
+        T w[DHI - DLO + 1][E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) w[Q][e] = T(0);
-    if (L == 0) ld16(slot + W * Q, w[Q]);
+        for (int d = DLO; d <= DHI; ++d) ld16(slot + W * q + E * (L + 1 + d), w[d - DLO]);
+#pragma unroll
+        for (int i = -H; i <= E; ++i) {
+            const int r = i + A;
+            const int d = (r >= 0) ? r / E : -((-r + E - 1) / E);
+            const int e = r - d * E;
+            T x = w[d - DLO][e];
+            if (i < 0 && q == 0 && L == 0 && !left) x = T(0);
+            v[q][H + i] = x;
+        }
+    }
 }
 
-// copy a compact row window (c_load's values): pairs from crow - par
+// Copy a compact row window (pairs of coarse values from crow - par, pair
+// index 32 q + L; lane 0 also pair 32 Q), or single values for NC = 1.
 template <typename TW, int Q, int NC>
 __device__ __forceinline__ void ring_copy_crow(TW *slot, const TW *crow, int par, int L)
 {
@@ -204,35 +229,29 @@ __device__ __forceinline__ void ring_copy_crow(TW *slot, const TW *crow, int par
     }
 }
 
-// Canonical windows of one row segment from its words w (ring_words):
-// v[q][H + i] = seg[W q + E L + i], i = -H .. E, A = (element offset of seg)
-// mod E.  Left-halo values of sub-segment 0 of lane 0 come from the previous
-// segment (left, read from global memory) or are 0 at a row start.
-template <typename T, int Q, int H, int A>
-__device__ __forceinline__ void rw_canon(const T (&w)[Q + 1][VecE<T>::value], const T *seg, int L, bool left,
-                                         T (&v)[Q][H + VecE<T>::value + 1])
+// Compact row window from its slot (after the warp's barrier):
+// v[q][j] = crow[WC q + NC L + j], j = 0 .. NC; par = (offset of crow) mod 2.
+template <typename TW, int Q, int NC>
+__device__ __forceinline__ void c_slot(const TW *slot, int L, int par, TW (&v)[Q][NC + 1])
 {
-    constexpr int E = VecE<T>::value;
-    static_assert(A >= 0 && A < E, "word offset");
+    constexpr int WC = 32 * NC;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-#pragma unroll
-        for (int i = 0; i <= E; ++i) {
-            const int p = A + i;
-            if (p < E) v[q][H + i] = w[q][p];
-            else v[q][H + i] = from_right(w[q][p - E], w[q + 1][p - E], L);
-        }
-    }
-    if constexpr (H > 0) {
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-#pragma unroll
-            for (int i = -H; i < 0; ++i) {
-                T x;
-                if (A + i >= 0) x = w[q][A + i];
-                else x = from_left(v[q][H + E + i], v[q > 0 ? q - 1 : 0][H + E + i], L);
-                if (q == 0 && L == 0) x = left ? ((A + i >= 0) ? x : seg[i]) : T(0);
-                v[q][H + i] = x;
+        if constexpr (NC == 1) {
+            v[q][0] = slot[WC * q + L];
+            v[q][1] = slot[WC * q + L + 1];
+        } else {
+            TW a, b, a2, b2;
+            ld_pair(slot + WC * q + 2 * L, a, b);
+            ld_pair(slot + WC * q + 2 * L + 2, a2, b2);
+            if (par == 0) {
+                v[q][0] = a;
+                v[q][1] = b;
+                v[q][2] = a2;
+            } else {  // pairs (2L - 1, 2L)
+                v[q][0] = b;
+                v[q][1] = a2;
+                v[q][2] = b2;
             }
         }
     }
@@ -295,47 +314,6 @@ __device__ __forceinline__ void c_store(TW *crow, int L, const TW (&o)[Q][NC], T
         }
     }
     if (extra) crow[WC * Q] = ox;
-}
-
-// Compact coarse row window from its ring slot (ring_copy_crow):
-// v[q][j] = crow[WC q + NC L + j], j = 0 .. NC.
-template <typename TW, int Q, int NC>
-__device__ __forceinline__ void c_canon(const TW *slot, int L, int par, TW (&v)[Q][NC + 1])
-{
-    constexpr int WC = 32 * NC;
-    if constexpr (NC == 1) {
-        TW w[Q + 1];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) w[q] = slot[WC * q + L];
-        w[Q] = (L == 0) ? slot[WC * Q] : TW(0);
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            v[q][0] = w[q];
-            v[q][1] = from_right(w[q], w[q + 1], L);
-        }
-    } else {
-        TW a[Q + 1], b[Q + 1];
-        a[Q] = b[Q] = TW(0);
-#pragma unroll
-        for (int q = 0; q < Q; ++q) ld_pair(slot + WC * q + 2 * L, a[q], b[q]);
-        if (L == 0) ld_pair(slot + WC * Q, a[Q], b[Q]);
-        if (par == 0) {
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                v[q][0] = a[q];
-                v[q][1] = b[q];
-                v[q][2] = from_right(a[q], a[q + 1], L);
-            }
-        } else {
-            // pairs (2L - 1, 2L)
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                v[q][0] = b[q];
-                v[q][1] = from_right(a[q], a[q + 1], L);
-                v[q][2] = from_right(b[q], b[q + 1], L);
-            }
-        }
-    }
 }
 
 // Multilinear interpolation along dim 2 of a canonical window e (even
@@ -421,44 +399,56 @@ __global__ void __launch_bounds__(32 * kRcWarps) k_rc_sweep(RcParams p)
         const int Z0 = HZ ? c * p.zchunk : 0;
         const int Z1 = HZ ? min(Z0 + p.zchunk, m0 - 1) : 0;
 
-        // issue the copies of row position j (an empty group past the end)
-        auto issue = [&](int j) {
-            const int Zj = Z0 + j / RPS, k = j % RPS;
-            if (Zj <= Z1) {
-                void *slot = ring + (j % NSLOT) * SB;
-                int kf = k;  // field row kind: 0 = (2Z, 2Y) .. 4 = (2Z-1, 2Y+1)
+        // issue the copies of the next row position (positions in order of
+        // use; an empty group past the end): coarse plane iz, row kind ik
+        int iz = Z0, ik = 0, islot = 0;
+        auto issue = [&]() {
+            if (iz <= Z1) {
+                void *slot = ring + islot * SB;
+                int kf = ik;  // field row kind: 0 = (2Z, 2Y) .. 4 = (2Z-1, 2Y+1)
                 if constexpr (!DEC) {
-                    if (k < 2) {
-                        if (k == 0 || two)
-                            ring_copy_crow<TW, Q, NC>(static_cast<TW *>(slot), V + ((int64_t)Zj * m1 + Y + k) * m2 + ccol0,
-                                                      (Zj + Y + k) & 1, L);
+                    if (ik < 2) {
+                        if (ik == 0 || two)
+                            ring_copy_crow<TW, Q, NC>(static_cast<TW *>(slot), V + ((int64_t)iz * m1 + Y + ik) * m2 + ccol0,
+                                                      (iz + Y + ik) & 1, L);
                         kf = -1;
                     } else {
-                        kf = (k == 2) ? 0 : (k == 3 ? 1 : k - 1);
+                        kf = (ik == 2) ? 0 : (ik == 3 ? 1 : ik - 1);
                     }
                 }
                 if (kf >= 0) {
                     // kf = 0, 1, 2: rows 2Y, 2Y+1, 2Y+2 of plane 2Z; 3, 4: rows 2Y, 2Y+1 of plane 2Z-1
                     const bool oddp = kf >= 3;
-                    const int z = oddp ? 2 * Zj - 1 : 2 * Zj;
+                    const int z = oddp ? 2 * iz - 1 : 2 * iz;
                     const int y = 2 * Y + (oddp ? kf - 3 : kf);
-                    const bool ok = (!oddp || (HZ && Zj > Z0)) && (y == 2 * Y || two);
+                    const bool ok = (!oddp || (HZ && iz > Z0)) && (y == 2 * Y || two);
                     if (ok)
-                        ring_copy_row<T, Q>(static_cast<T *>(slot), A + ((int64_t)z * n1 + y) * n2 + col0, (z + y) % E, L);
+                        ring_copy_row<T, Q>(static_cast<T *>(slot), A + ((int64_t)z * n1 + y) * n2 + col0, (z + y) % E,
+                                            L, false);
                 }
             }
             cp_async_commit();
+            if (++ik == RPS) {
+                ik = 0;
+                ++iz;
+            }
+            if (++islot == NSLOT) islot = 0;
         };
-        // wait for row position i; its slot, valid until the next take (which
-        // refills the slot of position i - 1 + NSLOT, i.e. this one's successor
-        // in the ring: read a slot before taking the next position)
-        auto take = [&](int i) -> const unsigned char * {
-            issue(i + D);
+        // wait for row position i and make every lane's copies visible; its
+        // slot stays valid until the next take (whose copies refill the
+        // slot of position i - 1 + NSLOT, the one after it in the ring)
+        int tslot = 0;
+        auto take = [&]() -> const unsigned char * {
+            __syncwarp();  // every lane has read the slot that issue() refills
+            issue();
             cp_async_wait<D>();
-            return ring + (i % NSLOT) * SB;
+            __syncwarp();
+            const unsigned char *r = ring + tslot * SB;
+            if (++tslot == NSLOT) tslot = 0;
+            return r;
         };
 #pragma unroll 1
-        for (int j = 0; j < D; ++j) issue(j);
+        for (int j = 0; j < D; ++j) issue();
 
         T wl[Q][NC], wr[Q][NC];
 #pragma unroll
@@ -486,7 +476,6 @@ __global__ void __launch_bounds__(32 * kRcWarps) k_rc_sweep(RcParams p)
         for (int Z = Z0; Z <= Z1; ++Z) {
             const bool own_even = !HZ || Z < Z1 || Z == m0 - 1;
             const bool odd = HZ && Z > Z0;  // the odd plane 2Z - 1 is this item's
-            const int i0 = (Z - Z0) * RPS;
             T *segA = A + ((int64_t)(2 * Z) * n1 + 2 * Y) * n2 + col0;  // even plane 2Z, row 2Y
             T wzl = T(0), wzr = T(0);
             if (odd) {
@@ -496,26 +485,20 @@ __global__ void __launch_bounds__(32 * kRcWarps) k_rc_sweep(RcParams p)
             const int par = (Z + Y) & 1;  // offset of row (2Z, 2Y) is 2 par mod E
             auto step = [&](auto PC) {
                 constexpr int A0 = (2 * decltype(PC)::value) % E;
-                T w[Q + 1][E];
                 Row cA, cB, X0, XH;
                 if constexpr (DEC) {
                     Row eH;
-                    ring_words<T, Q>(reinterpret_cast<const T *>(take(i0)), L, w);
-                    rw_canon<T, Q, 0, A0>(w, segA, L, false, cA);
-                    ring_words<T, Q>(reinterpret_cast<const T *>(take(i0 + 1)), L, w);
-                    rw_canon<T, Q, 0, (A0 + 1) % E>(w, segA, L, false, cB);
-                    ring_words<T, Q>(reinterpret_cast<const T *>(take(i0 + 2)), L, w);
-                    rw_canon<T, Q, 0, (A0 + 2) % E>(w, segA, L, false, eH);
+                    rw_slot<T, Q, 0, A0>(reinterpret_cast<const T *>(take()), L, false, cA);
+                    rw_slot<T, Q, 0, (A0 + 1) % E>(reinterpret_cast<const T *>(take()), L, false, cB);
+                    rw_slot<T, Q, 0, (A0 + 2) % E>(reinterpret_cast<const T *>(take()), L, false, eH);
                     x_interp<T, Q, WU>(cA, wl, wr, X0);
                     x_interp<T, Q, WU>(eH, wl, wr, XH);
                 } else {
                     TW vA[Q][NC + 1], vH[Q][NC + 1];
-                    c_canon<TW, Q, NC>(reinterpret_cast<const TW *>(take(i0)), L, par, vA);
-                    c_canon<TW, Q, NC>(reinterpret_cast<const TW *>(take(i0 + 1)), L, par ^ 1, vH);
-                    ring_words<T, Q>(reinterpret_cast<const T *>(take(i0 + 2)), L, w);
-                    rw_canon<T, Q, 0, A0>(w, segA, L, false, cA);
-                    ring_words<T, Q>(reinterpret_cast<const T *>(take(i0 + 3)), L, w);
-                    rw_canon<T, Q, 0, (A0 + 1) % E>(w, segA, L, false, cB);
+                    c_slot<TW, Q, NC>(reinterpret_cast<const TW *>(take()), L, par, vA);
+                    c_slot<TW, Q, NC>(reinterpret_cast<const TW *>(take()), L, par ^ 1, vH);
+                    rw_slot<T, Q, 0, A0>(reinterpret_cast<const T *>(take()), L, false, cA);
+                    rw_slot<T, Q, 0, (A0 + 1) % E>(reinterpret_cast<const T *>(take()), L, false, cB);
                     x_interp_c<T, TW, Q, WU>(vA, wl, wr, X0);
                     x_interp_c<T, TW, Q, WU>(vH, wl, wr, XH);
                 }
@@ -546,16 +529,15 @@ __global__ void __launch_bounds__(32 * kRcWarps) k_rc_sweep(RcParams p)
                     }
                 }
                 // the odd plane 2Z - 1 (its positions are taken in any case;
-                // each slot is read before the next take reuses the one before)
-                constexpr int KO = DEC ? 3 : 4;
-                T wB[Q + 1][E];
-                ring_words<T, Q>(reinterpret_cast<const T *>(take(i0 + KO)), L, w);
-                ring_words<T, Q>(reinterpret_cast<const T *>(take(i0 + KO + 1)), L, wB);
+                // each slot is read before the next take)
+                Row oA, oB;
+                const T *sO = reinterpret_cast<const T *>(take());
+                if (odd) rw_slot<T, Q, 0, (A0 + E - 1) % E>(sO, L, false, oA);
+                const T *sO2 = reinterpret_cast<const T *>(take());
+                if (odd) rw_slot<T, Q, 0, A0>(sO2, L, false, oB);
                 if (odd) {
                     T *segO = segA - plane;  // plane 2Z - 1, row 2Y
-                    Row oA, oB, out;
-                    rw_canon<T, Q, 0, (A0 + E - 1) % E>(w, segO, L, false, oA);
-                    rw_canon<T, Q, 0, A0>(wB, segO, L, false, oB);
+                    Row out;
 #pragma unroll
                     for (int q = 0; q < Q; ++q)
 #pragma unroll
@@ -743,28 +725,39 @@ __global__ void __launch_bounds__(32 * kRcWarps) k_rc_restrict(RcParams p)
         const int Zfirst = (HZ && Zs > 0) ? Zs - 1 : Zs;
         const int Zlast = HZ ? min(Ze, m0 - 1) : 0;
 
-        // row position j: coarse plane Zfirst + j / PPZ, then the odd plane's
-        // NR rows 2 Y0 - 2 .. 2 Y0 + 2 TY (3D), then the even plane's
-        auto issue = [&](int j) {
-            const int Zj = Zfirst + j / PPZ, k = j % PPZ;
-            const bool oddp = HZ && k < NR;
-            const int r = oddp ? k : k - (HZ ? NR : 0);
+        // row positions in order of use: per coarse plane Zfirst.. the odd
+        // plane's NR rows 2 Y0 - 2 .. 2 Y0 + 2 TY (3D), then the even
+        // plane's; issue() copies the next one (coarse plane iz, kind ik)
+        int iz = Zfirst, ik = 0, islot = 0;
+        auto issue = [&]() {
+            const bool oddp = HZ && ik < NR;
+            const int r = oddp ? ik : ik - (HZ ? NR : 0);
             const int y = 2 * Y0 - 2 + r;
-            const bool ok = Zj <= Zlast && y >= 0 && y < n1 && (!oddp || (Zj >= 1 && Zj >= Zs));
+            const bool ok = iz <= Zlast && y >= 0 && y < n1 && (!oddp || (iz >= 1 && iz >= Zs));
             if (ok) {
-                const int z = oddp ? 2 * Zj - 1 : (HZ ? 2 * Zj : 0);
-                ring_copy_row<T, Q>(reinterpret_cast<T *>(ring + (j % NSLOT) * SB),
-                                    A + ((int64_t)z * n1 + y) * n2 + col0, (z + y) % E, L);
+                const int z = oddp ? 2 * iz - 1 : (HZ ? 2 * iz : 0);
+                ring_copy_row<T, Q>(reinterpret_cast<T *>(ring + islot * SB), A + ((int64_t)z * n1 + y) * n2 + col0,
+                                    (z + y) % E, L, s > 0);
             }
             cp_async_commit();
+            if (++ik == PPZ) {
+                ik = 0;
+                ++iz;
+            }
+            if (++islot == NSLOT) islot = 0;
         };
-        auto take = [&](int i) -> const T * {
-            issue(i + D);
+        int tslot = 0;
+        auto take = [&]() -> const T * {
+            __syncwarp();  // every lane has read the slot that issue() refills
+            issue();
             cp_async_wait<D>();
-            return reinterpret_cast<const T *>(ring + (i % NSLOT) * SB);
+            __syncwarp();
+            const T *r = reinterpret_cast<const T *>(ring + tslot * SB);
+            if (++tslot == NSLOT) tslot = 0;
+            return r;
         };
 #pragma unroll 1
-        for (int j = 0; j < D; ++j) issue(j);
+        for (int j = 0; j < D; ++j) issue();
 
         // K_2 rows: interior rows shared (KU); the lane's first node of
         // sub-segment 0 (the grid's first at L = 0 of segment 0) and the
@@ -840,11 +833,9 @@ __global__ void __launch_bounds__(32 * kRcWarps) k_rc_restrict(RcParams p)
             // dim-2 and dim-1 stencils of fine plane `pl` into g; AP = word
             // offset of its row 2 Y0 - 2; EVEN: an even plane (its even rows
             // hold coarse nodes, C = 0 there, and those are gathered into V)
-            const int ipos = (Z - Zfirst) * PPZ;
             auto plane_pass = [&](auto APC, auto EVC, const T *pl, int Zv, T (&g)[TY][Q][NC], T (&gx)[TY]) {
                 constexpr int AP = decltype(APC)::value;
                 constexpr bool EVEN = decltype(EVC)::value != 0;
-                const int ip = ipos + ((HZ && EVEN) ? NR : 0);
 #pragma unroll
                 for (int j = 0; j < TY; ++j) {
                     gx[j] = T(0);
@@ -856,12 +847,10 @@ __global__ void __launch_bounds__(32 * kRcWarps) k_rc_restrict(RcParams p)
                 static_for<0, NR>([&](auto RC) {
                     constexpr int r = decltype(RC)::value;
                     const int y = 2 * Y0 - 2 + r;
-                    const T *slot = take(ip + r);
+                    const T *slot = take();
                     if (y < 0 || y >= n1) return;
-                    T w[Q + 1][E];
-                    ring_words<T, Q>(slot, L, w);
                     T v[Q][E + 3];
-                    rw_canon<T, Q, 2, (AP + r) % E>(w, pl + (int64_t)y * n2, L, s > 0, v);
+                    rw_slot<T, Q, 2, (AP + r) % E>(slot, L, s > 0, v);
                     constexpr bool MASK = EVEN && (r % 2 == 0);
                     T h[Q][NC], hx;
 #pragma unroll
@@ -921,7 +910,7 @@ __global__ void __launch_bounds__(32 * kRcWarps) k_rc_restrict(RcParams p)
                 if constexpr (HZ) {
                     if (!has_odd) {
 #pragma unroll 1
-                        for (int r = 0; r < NR; ++r) take(ipos + r);  // the positions of the missing plane
+                        for (int r = 0; r < NR; ++r) take();  // the positions of the missing plane
                     } else {  // plane 2Z - 1: tap 3 of Z - 1, tap 1 of Z
                         plane_pass(IC<(A0 + E - 1) % E>{}, IC<0>{}, A + (int64_t)(2 * Z - 1) * plane + col0, Z, g, gx);
                         const T kzP3 = __ldg(k0 + 5 * (Z - 1) + 3), kzC1 = __ldg(k0 + 5 * Z + 1);
