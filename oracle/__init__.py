@@ -22,3 +22,4 @@ from .oracle import (  # noqa: F401
     decompose_adjoint_per_dim,
     recompose_adjoint_per_dim,
 )
+from .quantize import node_classes, quantize, dequantize  # noqa: F401,E402
