@@ -495,6 +495,45 @@ def run_progressive(torch, mgard, plan, u, ws, stream, peak):
             "full_recompose_ms": full, "runs": rows}
 
 
+def run_quantize(torch, mgard, plan, u, ws, stream, peak):
+    """Quantization of the decomposed 513^3 FP32 field (one bin width per
+    coefficient class, 1e-4 max|u| each) and de-quantization: each reads 4
+    and writes 4 bytes per node; median of 7 event-timed calls.  Also the
+    share of zero codes and the rebuilt field's max error against u."""
+    L = plan.levels
+    orig = u.clone()
+    scale = float(u.abs().max())
+    bins = [1e-4 * scale] * (L + 1)
+    plan.decompose(u, ws, stream)
+    codes = torch.empty(u.shape, dtype=torch.int32, device=u.device)
+
+    def median(fn, reps=7):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sorted(a.elapsed_time(b) for a, b in ev)[reps // 2]
+
+    plan.quantize(u, bins, codes, stream)
+    tq = median(lambda: plan.quantize(u, bins, codes, stream))
+    back = torch.empty_like(u)
+    td = median(lambda: plan.dequantize(codes, bins, back, stream))
+    zeros = float((codes == 0).float().mean())
+    plan.dequantize_recompose(codes, bins, back, ws, stream)
+    torch.cuda.synchronize()
+    err = float((back - orig).abs().max())
+    nb = 8 * u.numel()
+    u.copy_(orig)
+    del orig, back, codes
+    torch.cuda.empty_cache()
+    return {"workload": "513^3 FP32 decomposed field, bins 1e-4 max|u| per class",
+            "quantize_ms": tq, "quantize_gbs": nb / (tq / 1e3) / 1e9, "quantize_frac_of_measured_hbm":
+            nb / (tq / 1e3) / 1e9 / peak, "dequantize_ms": td, "dequantize_gbs": nb / (td / 1e3) / 1e9,
+            "zero_codes": zeros, "rebuilt_max_abs_error": err, "rebuilt_error_in_bins": err / bins[0]}
+
+
 def run_nonuniform(torch, mgard, synth, dev, stream, rank, world, max_over_ranks, uniform_ms):
     """513^3 FP32 on a tanh-clustered grid along every dimension
     (boundary-layer grading, beta = 2: spacings from 0.15x to 2.1x the mean):
@@ -633,6 +672,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-progressive", action="store_true")
     ap.add_argument("--no-nonuniform", action="store_true")
+    ap.add_argument("--no-quantize", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -849,6 +889,7 @@ def main():
                     "decompose_frac_of_pass_model": in_bytes / (t_dec / 1e3) / 1e9 / (peak / 8.43)}
 
     progressive = None if args.no_progressive else run_progressive(torch, mgard, plan, u, ws, stream, peak)
+    quantize = None if args.no_quantize else run_quantize(torch, mgard, plan, u, ws, stream, peak)
     nonuniform = None if args.no_nonuniform else run_nonuniform(
         torch, mgard, synth, dev, stream, rank, world, max_over_ranks, ms / args.steps)
     batched = None if args.no_batch else run_batched(torch, mgard, synth, dev, stream, rank)
@@ -879,6 +920,7 @@ def main():
             "batched": batched,
             "adjoint": adjoint,
             "progressive": progressive,
+            "quantize": quantize,
             "nonuniform": nonuniform,
             "paper_metric": paper_metric,
             "e2e": e2e,

@@ -286,6 +286,39 @@ MGARD_API mgard_status mgard_batch_recompose(mgard_batch *batch, void *const *d_
 MGARD_API mgard_status mgard_decompose_noalloc(int ndim, const int64_t *dims, int nlevels, mgard_dtype dtype,
                                                void *d_data, void *stream);
 
+/* ---- Quantization of the coefficient classes ------------------------------
+ * Section V-B (lossy compression): the quantization and de-quantization of
+ * the decomposed field run on the GPU between the decomposition and an
+ * entropy coder.  The paper does not state the quantizer; these calls use a
+ * uniform quantizer with one bin width per coefficient class:
+ *   class of a node: the class it holds in the in-place layout (Fig. 3):
+ *     class 0 = the coarsest values N_0, class l = the level-l coefficients
+ *     N_l \ N_{l-1}, l = 1 .. L;
+ *   code = sign(c) floor(|c| / bin_k + 1/2), computed in the field's
+ *     precision (FP32 for MGARD_F32 and MGARD_F32_MIXED, FP64 for MGARD_F64)
+ *     as one rounded product with 1 / bin_k (itself rounded to that
+ *     precision) and one rounded addition, saturating at +-(2^31 - 1);
+ *   de-quantized value = code x bin_k (rounded to the field's precision).
+ * |c - code x bin_k| <= bin_k / 2 up to rounding of the product (unless
+ * saturated).
+ *   bins      host array of L + 1 positive finite bin widths, index = class
+ *             (MGARD_ERR_INVALID_ARG otherwise, nothing launched)
+ *   d_data    the decomposed field (device, the plan's shape and type)
+ *   d_codes   int32 device array of the field's node count, same layout
+ * Asynchronous on `stream`; no workspace.  mgard_decompose_quantize is
+ * mgard_decompose then mgard_quantize on `stream` (d_data ends up holding
+ * the decomposed field); mgard_dequantize_recompose is mgard_dequantize into
+ * d_data then mgard_recompose. */
+MGARD_API mgard_status mgard_quantize(const mgard_plan *plan, const double *bins, const void *d_data,
+                                      int32_t *d_codes, void *stream);
+MGARD_API mgard_status mgard_dequantize(const mgard_plan *plan, const double *bins, const int32_t *d_codes,
+                                        void *d_data, void *stream);
+MGARD_API mgard_status mgard_decompose_quantize(const mgard_plan *plan, const double *bins, void *d_data,
+                                                int32_t *d_codes, void *d_ws, size_t ws_bytes, void *stream);
+MGARD_API mgard_status mgard_dequantize_recompose(const mgard_plan *plan, const double *bins,
+                                                  const int32_t *d_codes, void *d_data, void *d_ws,
+                                                  size_t ws_bytes, void *stream);
+
 /* ---- Measurement support --------------------------------------------------
  * FP64 fused multiply-add rate of the current device in TFLOP/s (2 flops per
  * FMA), measured with CUDA events on `stream` over one launch of

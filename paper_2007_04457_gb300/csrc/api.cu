@@ -15,6 +15,7 @@
 
 #include "mgard.h"
 #include "launch.cuh"
+#include "quant.cuh"
 
 using namespace mg;
 
@@ -1347,6 +1348,54 @@ mgard_status mg_decompose_with(const mgard_plan *P, void *d_data, void *d_ws, si
     return mgard_decompose(P, d_data, d_ws, ws_bytes, st);
 }
 
+// Quantization / de-quantization of a plan's field (quant.cuh); mode 0 quantizes
+// field -> codes, 1 de-quantizes codes -> field.
+template <typename T>
+static mgard_status run_quant(const mgard_plan *P, int mode, const double *bins, const void *field,
+                              const int32_t *codes_in, void *field_out, int32_t *codes_out, cudaStream_t st)
+{
+    QuantParams<T> p{};
+    p.c = static_cast<const T *>(field);
+    p.q = codes_out;
+    p.qi = codes_in;
+    p.d = static_cast<T *>(field_out);
+    p.n0 = P->n[0];
+    p.n1 = P->n[1];
+    p.n2 = P->n[2];
+    p.L = P->L;
+    for (int k = 0; k <= P->L; ++k) {
+        if (!(bins[k] > 0.0) || !std::isfinite(bins[k]))
+            return fail(MGARD_ERR_INVALID_ARG, "quantize: every bin must be positive and finite");
+        const T b = static_cast<T>(bins[k]);
+        if (!(b > T(0)) || !std::isfinite((double)b))
+            return fail(MGARD_ERR_INVALID_ARG, "quantize: a bin is out of the field precision's range");
+        p.bin[k] = b;
+        p.inv[k] = T(1) / b;
+    }
+    const int64_t rows = p.n0 * p.n1;
+    const int64_t blocks = std::min<int64_t>((rows + kQuantWarps - 1) / kQuantWarps, (int64_t)P->num_sms * 16);
+    if (mode == 0) k_quant<T, 0><<<(unsigned)blocks, 32 * kQuantWarps, 0, st>>>(p);
+    else k_quant<T, 1><<<(unsigned)blocks, 32 * kQuantWarps, 0, st>>>(p);
+    const cudaError_t err = cudaGetLastError();
+    return err == cudaSuccess ? MGARD_OK : cuda_fail(err, mode == 0 ? "quantize kernel" : "dequantize kernel");
+}
+
+static mgard_status quant_call(const mgard_plan *P, int mode, const double *bins, const void *field,
+                               const int32_t *codes_in, void *field_out, int32_t *codes_out, void *stream)
+{
+    if (!P) return fail(MGARD_ERR_INVALID_ARG, "quantize: plan is NULL");
+    if (!bins) return fail(MGARD_ERR_INVALID_ARG, "quantize: bins is NULL");
+    if (mode == 0 && (!field || !codes_out)) return fail(MGARD_ERR_INVALID_ARG, "quantize: NULL device pointer");
+    if (mode == 1 && (!codes_in || !field_out)) return fail(MGARD_ERR_INVALID_ARG, "dequantize: NULL device pointer");
+    if (P->L + 1 > kQuantMaxClasses) return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "quantize: too many levels");
+    const void *f = mode == 0 ? field : field_out;
+    if (reinterpret_cast<uintptr_t>(f) % P->elem_user != 0)
+        return fail(MGARD_ERR_INVALID_ARG, "quantize: the field is not aligned to its element size");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (P->elem_user == 8) return run_quant<double>(P, mode, bins, field, codes_in, field_out, codes_out, st);
+    return run_quant<float>(P, mode, bins, field, codes_in, field_out, codes_out, st);
+}
+
 // Decomposition (dir 0) or recomposition (dir 1); allow_coop = false keeps
 // the cooperative kernel out (batches run fields concurrently on several
 // streams, and a cooperative launch holds every SM).
@@ -1551,6 +1600,37 @@ mgard_status mgard_recompose_host(const mgard_plan *P, const void *h_in, void *h
                                   size_t ws_bytes, void *stream)
 {
     return host_call(false, P, h_in, h_out, d_data, d_ws, ws_bytes, stream);
+}
+
+mgard_status mgard_quantize(const mgard_plan *P, const double *bins, const void *d_data, int32_t *d_codes, void *stream)
+{
+    return quant_call(P, 0, bins, d_data, nullptr, nullptr, d_codes, stream);
+}
+
+mgard_status mgard_dequantize(const mgard_plan *P, const double *bins, const int32_t *d_codes, void *d_data,
+                              void *stream)
+{
+    return quant_call(P, 1, bins, nullptr, d_codes, d_data, nullptr, stream);
+}
+
+mgard_status mgard_decompose_quantize(const mgard_plan *P, const double *bins, void *d_data, int32_t *d_codes,
+                                      void *d_ws, size_t ws_bytes, void *stream)
+{
+    if (!P || !bins || !d_codes) return fail(MGARD_ERR_INVALID_ARG, "decompose_quantize: NULL argument");
+    mgard_status s = mgard_decompose(P, d_data, d_ws, ws_bytes, stream);
+    if (s != MGARD_OK) return s;
+    return mgard_quantize(P, bins, d_data, d_codes, stream);
+}
+
+mgard_status mgard_dequantize_recompose(const mgard_plan *P, const double *bins, const int32_t *d_codes,
+                                        void *d_data, void *d_ws, size_t ws_bytes, void *stream)
+{
+    if (!P || !bins || !d_codes) return fail(MGARD_ERR_INVALID_ARG, "dequantize_recompose: NULL argument");
+    mgard_status s = check_call(P, d_data, d_ws, ws_bytes);
+    if (s != MGARD_OK) return s;
+    s = mgard_dequantize(P, bins, d_codes, d_data, stream);
+    if (s != MGARD_OK) return s;
+    return mgard_recompose(P, d_data, d_ws, ws_bytes, stream);
 }
 
 mgard_status mgard_profile_enable(mgard_plan *P, int levels)

@@ -73,6 +73,10 @@ def _load() -> ctypes.CDLL:
         "mgard_batch_recompose": ([vp, ctypes.POINTER(vp), vp, sz, vp], ctypes.c_int),
         "mgard_decompose_noalloc": ([ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
         "mgard_probe_fp64_peak": ([ctypes.POINTER(ctypes.c_double), vp], ctypes.c_int),
+        "mgard_quantize": ([vp, ctypes.POINTER(ctypes.c_double), vp, vp, vp], ctypes.c_int),
+        "mgard_dequantize": ([vp, ctypes.POINTER(ctypes.c_double), vp, vp, vp], ctypes.c_int),
+        "mgard_decompose_quantize": ([vp, ctypes.POINTER(ctypes.c_double), vp, vp, vp, sz, vp], ctypes.c_int),
+        "mgard_dequantize_recompose": ([vp, ctypes.POINTER(ctypes.c_double), vp, vp, vp, sz, vp], ctypes.c_int),
         "mgard_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "mgard_last_error": ([], ctypes.c_char_p),
     }
@@ -200,6 +204,31 @@ def mgard_decompose_noalloc(ndim, dims, nlevels, dtype, d_data: int, stream: int
     _check(LIB.mgard_decompose_noalloc(ndim, d, nlevels, dtype, d_data, stream), "mgard_decompose_noalloc")
 
 
+def _bins_arg(bins):
+    arr = (ctypes.c_double * len(bins))(*[float(b) for b in bins])
+    return arr
+
+
+def mgard_quantize(plan: int, bins, d_data: int, d_codes: int, stream: int) -> None:
+    _check(LIB.mgard_quantize(plan, _bins_arg(bins), d_data, d_codes, stream), "mgard_quantize")
+
+
+def mgard_dequantize(plan: int, bins, d_codes: int, d_data: int, stream: int) -> None:
+    _check(LIB.mgard_dequantize(plan, _bins_arg(bins), d_codes, d_data, stream), "mgard_dequantize")
+
+
+def mgard_decompose_quantize(plan: int, bins, d_data: int, d_codes: int, d_ws: int, ws_bytes: int,
+                             stream: int) -> None:
+    _check(LIB.mgard_decompose_quantize(plan, _bins_arg(bins), d_data, d_codes, d_ws, ws_bytes, stream),
+           "mgard_decompose_quantize")
+
+
+def mgard_dequantize_recompose(plan: int, bins, d_codes: int, d_data: int, d_ws: int, ws_bytes: int,
+                               stream: int) -> None:
+    _check(LIB.mgard_dequantize_recompose(plan, _bins_arg(bins), d_codes, d_data, d_ws, ws_bytes, stream),
+           "mgard_dequantize_recompose")
+
+
 def mgard_probe_fp64_peak(stream: int) -> float:
     """FP64 FMA rate of the current device in TFLOP/s (measurement support)."""
     out = ctypes.c_double(0.0)
@@ -293,6 +322,44 @@ class Plan:
     def recompose_adjoint(self, data, workspace=None, stream=None):
         """In place transpose of recompose."""
         mgard_recompose_adjoint(self.handle, *self._args(data, workspace, stream))
+        return data
+
+    def _codes(self, data, codes):
+        torch = _torch()
+        if codes is None:
+            codes = torch.empty(data.shape, dtype=torch.int32, device=data.device)
+        if not codes.is_cuda or codes.dtype != torch.int32 or codes.numel() != data.numel() \
+                or not codes.is_contiguous():
+            raise ValueError("codes must be a contiguous CUDA int32 tensor of the field's size")
+        return codes
+
+    def quantize(self, data, bins, codes=None, stream=None):
+        """int32 codes of a decomposed field, one bin width per coefficient
+        class (levels + 1 of them, class 0 = coarsest values)."""
+        codes = self._codes(data, codes)
+        d, _, _, st = self._args(data, None, stream)
+        mgard_quantize(self.handle, bins, d, codes.data_ptr(), st)
+        return codes
+
+    def dequantize(self, codes, bins, data, stream=None):
+        """codes x bin width of each node's class, into the field `data`."""
+        self._codes(data, codes)
+        d, _, _, st = self._args(data, None, stream)
+        mgard_dequantize(self.handle, bins, codes.data_ptr(), d, st)
+        return data
+
+    def decompose_quantize(self, data, bins, codes=None, workspace=None, stream=None):
+        """Decompose `data` in place, then its int32 codes."""
+        codes = self._codes(data, codes)
+        d, w, wb, st = self._args(data, workspace, stream)
+        mgard_decompose_quantize(self.handle, bins, d, codes.data_ptr(), w, wb, st)
+        return codes
+
+    def dequantize_recompose(self, codes, bins, data, workspace=None, stream=None):
+        """The field rebuilt from codes (de-quantized into `data`, recomposed)."""
+        self._codes(data, codes)
+        d, w, wb, st = self._args(data, workspace, stream)
+        mgard_dequantize_recompose(self.handle, bins, codes.data_ptr(), d, w, wb, st)
         return data
 
     def tune(self, level: int, param: int, value: int) -> None:

@@ -82,3 +82,9 @@ def test_null_arguments(lib):
     assert lib.mgard_workspace_bytes(None) == 0
     lib.mgard_probe_fp64_peak.restype = ctypes.c_int
     assert lib.mgard_probe_fp64_peak(None, None) == 1
+    for name in ("mgard_quantize", "mgard_dequantize"):
+        getattr(lib, name).restype = ctypes.c_int
+        assert getattr(lib, name)(None, None, None, None, None) == 1
+    for name in ("mgard_decompose_quantize", "mgard_dequantize_recompose"):
+        getattr(lib, name).restype = ctypes.c_int
+        assert getattr(lib, name)(None, None, None, None, None, ctypes.c_size_t(0), None) == 1
