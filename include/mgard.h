@@ -228,19 +228,59 @@ MGARD_API mgard_status mgard_recompose_adjoint(const mgard_plan *plan, void *d_d
                                      size_t ws_bytes, void *stream);
 
 /* Batches of independent fields (each with its own plan: shapes, levels and
- * tile settings may differ).  A batch call replays one CUDA graph that holds
- * every field's level kernels, spread over `streams` internal streams so
- * fields run concurrently; the graph is captured on the first call for a
- * given set of data pointers / workspace and re-captured when they change.
- * Not part of the paper (its fields are processed one at a time).
+ * tile settings may differ).  Not part of the paper (its fields are
+ * processed one at a time); the level steps are those of Section II-A.
+ * A batch call is one CUDA-graph launch in one of two forms:
+ *  - persistent (the default when every field fits it): one launch of a
+ *    persistent kernel whose blocks pull work items -- planes, line panels,
+ *    the small tail and the final placement of every level of every field --
+ *    from a device queue.  The host orders the items by a list-scheduling
+ *    model of the launch (largest fields first, a few in flight at a time);
+ *    an item waits (bounded) until the tasks it depends on are done.  A
+ *    field fits when its fine rows (its last dimension; for 2D fields the
+ *    columns) have at most 1025 nodes, every level fits one block's shared
+ *    memory (3D: coarse planes of up to 129 x 129 nodes in FP32), and all
+ *    fields share one element type.
+ *  - a graph of every field's per-level kernels spread over `streams`
+ *    internal streams, captured on the first call for a set of data
+ *    pointers / workspace and re-captured when they change.
  *   mgard_batch_create     plans: nfields plan pointers, kept (not copied)
  *                          and not freed by the batch; streams: 1..32
- *   mgard_batch_workspace_bytes   one workspace holding every field's slice
+ *   mgard_batch_workspace_bytes   one workspace that serves both forms
  *   mgard_batch_decompose / mgard_batch_recompose
  *                          d_data: nfields device pointers (host array);
- *                          the graph runs on `stream`
- * The first call on a stream captures: it must not itself be inside a
- * stream capture. */
+ *                          the launch goes to `stream`.  Calls of one
+ *                          direction must be ordered (one stream): they
+ *                          share the batch's counters.
+ *   mgard_batch_tune       param 0: 1 = persistent, 0 = graph of per-field
+ *                          launches (MGARD_ERR_INVALID_ARG for 1 when a
+ *                          field does not fit); 1: polls of a dependency
+ *                          wait before it gives up (>= 1); 2: test hook,
+ *                          1 = the first item also waits for a count that
+ *                          nothing reaches (its wait runs out); 3: blocks
+ *                          per SM of the persistent grid (0 = as many as
+ *                          fit; rebuilds the work lists); 4: measurement,
+ *                          1 = every block records its busy and waiting
+ *                          time per item kind
+ *   mgard_batch_profile_read   dir 0 / 1: per item kind (A, B, C, D, small
+ *                          tail, placement) the block-milliseconds busy and
+ *                          waiting for dependencies, and the items, summed
+ *                          over the calls since the last read (6 entries
+ *                          each, host arrays); synchronizes the device and
+ *                          clears the record
+ *   mgard_batch_get        0 persistent on, 1 poll limit, 2 test hook,
+ *                          3 blocks per SM requested, 4 every field fits,
+ *                          5 grid blocks, 6 blocks per SM that fit,
+ *                          7 / 8 work items of a decomposition /
+ *                          recomposition, 9 / 10 their modelled time (us),
+ *                          11 dynamic shared memory bytes; -1 otherwise
+ *   mgard_batch_check      synchronizes `stream`, then MGARD_ERR_TIMEOUT if
+ *                          a dependency wait of the persistent kernel ran
+ *                          out since the last check (the results of that
+ *                          call are then not valid), else MGARD_OK; clears
+ *                          the record.
+ * The first call of a direction captures its graph: it must not itself be
+ * inside a stream capture. */
 typedef struct mgard_batch mgard_batch;
 MGARD_API mgard_status mgard_batch_create(int nfields, mgard_plan *const *plans, int streams,
                                           mgard_batch **out);
@@ -250,6 +290,11 @@ MGARD_API mgard_status mgard_batch_decompose(mgard_batch *batch, void *const *d_
                                              size_t ws_bytes, void *stream);
 MGARD_API mgard_status mgard_batch_recompose(mgard_batch *batch, void *const *d_data, void *d_ws,
                                              size_t ws_bytes, void *stream);
+MGARD_API mgard_status mgard_batch_tune(mgard_batch *batch, int param, int value);
+MGARD_API long long mgard_batch_get(const mgard_batch *batch, int param);
+MGARD_API mgard_status mgard_batch_check(mgard_batch *batch, void *stream);
+MGARD_API mgard_status mgard_batch_profile_read(mgard_batch *batch, int dir, double *busy_ms, double *wait_ms,
+                                                long long *items);
 
 /* ---- Decomposition without any device allocation --------------------------
  * The paper has no counterpart: it is a deployment variant of

@@ -15,6 +15,7 @@
 
 #include "mgard.h"
 #include "launch.cuh"
+#include "plan_view.h"
 #include "quant.cuh"
 
 using namespace mg;
@@ -1254,6 +1255,37 @@ mgard_status mg_plan_in_place(int ndim, const int64_t *dims, int nlevels, mgard_
 // Decomposition with a host-built plan (used by the entry point that must not
 // allocate; validation as in mgard_decompose).
 mgard_status mg_decompose_with(const mgard_plan *P, void *d_data, void *d_ws, size_t ws_bytes, cudaStream_t st);
+
+namespace mg {
+
+bool plan_view(const mgard_plan *P, PlanView *v, PlanLevelView *lv)
+{
+    if (!P || !v) return false;
+    v->ndim = P->ndim;
+    v->L = P->L;
+    v->dtype = P->dtype;
+    v->device = P->device;
+    v->num_sms = P->num_sms;
+    v->elem_user = P->elem_user;
+    v->elem_ws = P->elem_ws;
+    for (int d = 0; d < 3; ++d) v->n[d] = P->n[d];
+    if (lv) {
+        const bool f32 = P->elem_ws == sizeof(float);
+        for (int j = 0; j < P->L; ++j) {
+            const mgard_level &L = P->lv[j];
+            for (int d = 0; d < 3; ++d) {
+                lv[j].n[d] = L.n[d];
+                lv[j].m[d] = L.m[d];
+                lv[j].w[d] = f32 ? (const void *)tab_ptr<float>(P, L.w_off[d]) : (const void *)tab_ptr<double>(P, L.w_off[d]);
+                lv[j].k[d] = f32 ? (const void *)tab_ptr<float>(P, L.k_off[d]) : (const void *)tab_ptr<double>(P, L.k_off[d]);
+                lv[j].fac[d] = f32 ? (const void *)tab_ptr<float>(P, L.t_off[d]) : (const void *)tab_ptr<double>(P, L.t_off[d]);
+            }
+        }
+    }
+    return true;
+}
+
+}  // namespace mg
 
 extern "C" {
 

@@ -6,6 +6,7 @@
 
 #include "params.h"
 #include "multi_params.h"
+#include "persist_params.h"
 #include "small_params.h"
 
 namespace mg {
@@ -100,5 +101,14 @@ cudaError_t rc_occupancy(int kind, int Q, int mode, bool hz, bool u, bool xs, in
 template <typename T, typename TW>
 cudaError_t launch_rc(int kind, int Q, int mode, bool hz, bool u, bool xs, const RcParams &p, int grid,
                       cudaStream_t st);
+
+// The persistent batch kernel (persist.cuh): blocks resident per SM with
+// `smem` bytes of dynamic shared memory, and the launch (any grid: its items
+// never wait on an item no block holds).
+template <typename TX, typename TW>
+cudaError_t persist_occupancy(int mode, size_t smem, int *blocks_per_sm);
+
+template <typename TX, typename TW>
+cudaError_t launch_persist(int mode, const PersistParams &p, int grid, size_t smem, cudaStream_t st);
 
 }  // namespace mg

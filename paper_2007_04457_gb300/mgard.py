@@ -71,6 +71,12 @@ def _load() -> ctypes.CDLL:
         "mgard_batch_workspace_bytes": ([vp], sz),
         "mgard_batch_decompose": ([vp, ctypes.POINTER(vp), vp, sz, vp], ctypes.c_int),
         "mgard_batch_recompose": ([vp, ctypes.POINTER(vp), vp, sz, vp], ctypes.c_int),
+        "mgard_batch_tune": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "mgard_batch_get": ([vp, ctypes.c_int], ctypes.c_longlong),
+        "mgard_batch_check": ([vp, vp], ctypes.c_int),
+        "mgard_batch_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)],
+                                     ctypes.c_int),
         "mgard_decompose_noalloc": ([ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
         "mgard_probe_fp64_peak": ([ctypes.POINTER(ctypes.c_double), vp], ctypes.c_int),
         "mgard_quantize": ([vp, ctypes.POINTER(ctypes.c_double), vp, vp, vp], ctypes.c_int),
@@ -413,9 +419,39 @@ def mgard_batch_recompose(batch: int, d_data, d_ws: int, ws_bytes: int, stream: 
     _check(LIB.mgard_batch_recompose(batch, arr, d_ws, ws_bytes, stream), "mgard_batch_recompose")
 
 
+def mgard_batch_tune(batch: int, param: int, value: int) -> None:
+    _check(LIB.mgard_batch_tune(batch, param, value), "mgard_batch_tune")
+
+
+def mgard_batch_get(batch: int, param: int) -> int:
+    return int(LIB.mgard_batch_get(batch, param))
+
+
+def mgard_batch_profile_read(batch: int, direction: int):
+    """Per item kind (A, B, C, D, small, place): block-ms busy, block-ms
+    waiting, items -- summed since the last read."""
+    busy = (ctypes.c_double * 6)()
+    wait = (ctypes.c_double * 6)()
+    items = (ctypes.c_longlong * 6)()
+    _check(LIB.mgard_batch_profile_read(batch, direction, busy, wait, items), "mgard_batch_profile_read")
+    return list(busy), list(wait), list(items)
+
+
+def mgard_batch_check(batch: int, stream: int) -> int:
+    """The status code (0, or 5 = MGARD_ERR_TIMEOUT when a dependency wait of
+    the persistent kernel ran out); does not raise."""
+    return int(LIB.mgard_batch_check(batch, stream))
+
+
 class Batch:
     """Independent fields (one Plan each) refactored by one CUDA-graph launch
-    per call.  The plans must outlive the batch."""
+    per call: the persistent kernel when every field fits it, else the graph
+    of per-field launches.  The plans must outlive the batch."""
+
+    # mgard_batch_get parameters
+    GET = {"persistent": 0, "spin": 1, "stall": 2, "blocks_per_sm_req": 3, "eligible": 4, "grid": 5,
+           "occupancy": 6, "items_dec": 7, "items_rec": 8, "model_us_dec": 9, "model_us_rec": 10,
+           "smem": 11}
 
     def __init__(self, plans, streams: int = 8):
         self.plans = list(plans)
@@ -447,6 +483,29 @@ class Batch:
     def recompose(self, fields, workspace=None, stream=None):
         mgard_batch_recompose(self.handle, *self._args(fields, workspace, stream))
         return fields
+
+    def tune(self, param: int, value: int) -> None:
+        """0: 1 = persistent kernel, 0 = graph of per-field launches;
+        1: dependency polls before a wait gives up; 2: test hook (1 = the
+        first item waits for a count nothing reaches); 3: blocks per SM (0 =
+        as many as fit).  The workspace size does not change."""
+        mgard_batch_tune(self.handle, param, value)
+
+    def get(self, name: str) -> int:
+        return mgard_batch_get(self.handle, self.GET[name])
+
+    KINDS = ("A", "B", "C", "D", "small", "place")
+
+    def profile(self, direction: int) -> dict:
+        """Block-ms busy / waiting and items per item kind since the last
+        read (tuning param 4 = 1 records them)."""
+        busy, wait, items = mgard_batch_profile_read(self.handle, direction)
+        return {k: {"busy_ms": b, "wait_ms": w, "items": n} for k, b, w, n in zip(self.KINDS, busy, wait, items)}
+
+    def check(self, stream=None) -> int:
+        torch = _torch()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return mgard_batch_check(self.handle, s.cuda_stream)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -1,4 +1,6 @@
-"""Batched fields in one CUDA-graph launch and the autotuner, on the GPU."""
+"""Batched fields as a CUDA graph of per-field launches (tuning param 0 =
+0) and the autotuner, on the GPU.  The persistent form is covered by
+test_gpu_persist.py."""
 import numpy as np
 import pytest
 
@@ -25,6 +27,8 @@ def test_batch_equals_single_fields_and_oracle(tmp_path):
     fields = [torch.from_numpy(h).cuda() for h in host]
     single = [f.clone() for f in fields]
     batch = mg.Batch(plans, streams=4)
+    batch.tune(0, 0)
+    assert batch.get("persistent") == 0
     for _ in range(2):  # the second call replays the captured graph
         work = [f.clone() for f in fields]
         batch.decompose(work)
@@ -51,6 +55,7 @@ def test_batch_recaptures_for_new_pointers():
     mg = _mg()
     plans = [mg.Plan(s, dtype="f32") for s in SHAPES[:3]]
     batch = mg.Batch(plans, streams=2)
+    batch.tune(0, 0)
     a = [torch.randn(p.shape, device="cuda") for p in plans]
     b = [x.clone() for x in a]
     batch.decompose(a)
