@@ -85,6 +85,26 @@ MGARD_API mgard_status mgard_plan_create(int ndim, const int64_t *dims, int nlev
                                const double *const *coords, mgard_dtype dtype,
                                mgard_plan **out);
 
+/* A plan with a level count per dimension: dimension k coarsens in the
+ * first levels[k] steps from the finest level and keeps all its nodes after
+ * that (P = I along it: no interpolation, and its stencil factor M and the
+ * solve with M cancel), so short sides stop early while the others go on;
+ * L = max_k levels[k].  levels: ndim entries (entries of size-1 dims are
+ * ignored), -1 = that dimension's maximum; NULL = every dimension its
+ * maximum.  Not part of the paper's runs (equal sides only, Section IV);
+ * Eq. 1-2 hold unchanged on the nested tensor-product spaces.  With equal
+ * counts the plan is the plain one (mgard_plan_create with nlevels = L).
+ * Otherwise mgard_decompose / mgard_recompose (and their _host forms) run
+ * the levels on the persistent kernel of the batch calls, as a batch of one
+ * field: the shape must fit it (fine rows of at most 1025 nodes, coarse
+ * planes within a block's shared memory), else
+ * MGARD_ERR_UNSUPPORTED_SHAPE; calls of one direction must be ordered (one
+ * stream).  The adjoints, mgard_recompose_classes, the quantization calls
+ * and mgard_plan_tune return MGARD_ERR_UNSUPPORTED_SHAPE for such a plan. */
+MGARD_API mgard_status mgard_plan_create_per_dim(int ndim, const int64_t *dims, const int *levels,
+                                                 const double *const *coords, mgard_dtype dtype,
+                                                 mgard_plan **out);
+
 /* Release a plan and its device tables (NULL is accepted). */
 MGARD_API mgard_status mgard_plan_destroy(mgard_plan *plan);
 

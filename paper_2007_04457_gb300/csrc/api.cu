@@ -57,6 +57,7 @@ struct mgard_level {
     int64_t w_off[3];    // interpolation weight pairs (2 per fine node)
     int64_t k_off[3];    // R*M stencil rows (5 per coarse node)
     int64_t t_off[3];    // tridiagonal factors of M_{l-1} (3 per coarse node)
+    int co[3];           // 1: the dim coarsens at this level (0: size 1, or kept with all its nodes)
     size_t v_off, f_off; // workspace offsets of V_j and F_j (bytes)
     int rcfg;            // load-vector tile configuration
     bool rcfg_user;      // set by mgard_plan_tune (else chosen per level)
@@ -77,6 +78,11 @@ struct mgard_level {
 
 struct mgard_plan {
     int ndim;            // squeezed dimension count
+    // per-dimension level counts: some dim stops coarsening before the last
+    // level; such a plan runs on the persistent kernel (an internal batch of
+    // this one field)
+    bool per_dim = false;
+    mgard_batch *pd_batch = nullptr;
     int act;             // active-dimension mask (ACT_1D / ACT_2D / ACT_3D)
     int64_t n[3];        // finest node counts, leading dims padded with 1
     int L;
@@ -916,7 +922,8 @@ const char *mgard_last_error(void) { return g_last_error.c_str(); }
 // double, returned in *tab) and the workspace layout.  Allocates no device
 // memory; the table pointers of the plan are left null.
 static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, const double *const *coords,
-                                    mgard_dtype dtype, mgard_plan **out, std::vector<double> *tab_out)
+                                    mgard_dtype dtype, mgard_plan **out, std::vector<double> *tab_out,
+                                    const int *dim_levels = nullptr)
 {
     if (!out) return fail(MGARD_ERR_INVALID_ARG, "plan_create: out is NULL");
     *out = nullptr;
@@ -929,10 +936,12 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
     // squeeze size-1 dimensions
     std::vector<int64_t> n;
     std::vector<std::vector<double>> x;
+    std::vector<int> lk_req;  // requested level count of each kept dim (-1: its maximum)
     for (int k = 0; k < ndim; ++k) {
         if (dims[k] < 1) return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "plan_create: dims must be >= 1");
         if (dims[k] > (int64_t(1) << 31)) return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "plan_create: dimension too large");
         if (dims[k] == 1) continue;
+        lk_req.push_back(dim_levels ? dim_levels[k] : -2);
         std::vector<double> xk(dims[k]);
         if (coords && coords[k]) {
             for (int64_t i = 0; i < dims[k]; ++i) xk[i] = coords[k][i];
@@ -960,8 +969,28 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
         if (!ok || Lmax >= 30) break;
         ++Lmax;
     }
-    const int L = (nlevels < 0) ? Lmax : nlevels;
-    if (L > Lmax)
+    int L = (nlevels < 0) ? Lmax : nlevels;
+    // per-dimension level counts: dim k coarsens in the first Lk[k] steps
+    std::vector<int> Lk(nd, 0);
+    bool per_dim = false;
+    if (dim_levels) {
+        L = 0;
+        for (int k = 0; k < nd; ++k) {
+            int own = 0;
+            while (own < 30 && (n[k] - 1) % (int64_t(1) << (own + 1)) == 0 && (n[k] - 1) >= (int64_t(1) << (own + 1)))
+                ++own;
+            const int want = lk_req[k] < 0 ? own : lk_req[k];
+            if (lk_req[k] < -1 || want > own)
+                return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "plan_create_per_dim: dim " + std::to_string(k) + " allows " +
+                                                             std::to_string(own) + " levels");
+            Lk[k] = want;
+            L = std::max(L, want);
+        }
+        for (int k = 0; k < nd; ++k) per_dim = per_dim || Lk[k] != L;
+    } else {
+        for (int k = 0; k < nd; ++k) Lk[k] = L;
+    }
+    if (L > Lmax && !per_dim)
         return fail(MGARD_ERR_UNSUPPORTED_SHAPE,
                     "plan_create: every (dims[k]-1) must be divisible by 2^nlevels (max levels here: " +
                         std::to_string(Lmax) + ")");
@@ -975,6 +1004,7 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
     if (nd < 3) P->n[0] = 1;
     if (nd < 2) P->n[1] = 1;
     P->L = L;
+    P->per_dim = per_dim;
     P->dtype = dtype;
     P->elem_user = (dtype == MGARD_F64) ? 8 : 4;
     P->elem_ws = (dtype == MGARD_F32) ? 4 : 8;
@@ -995,21 +1025,27 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
     P->lv.resize(L);
     for (int j = 0; j < L; ++j) {
         mgard_level &lv = P->lv[j];
-        const int64_t stride = int64_t(1) << j;
         for (int q = 0; q < 3; ++q) {
             lv.n[q] = 1;
             lv.m[q] = 1;
+            lv.co[q] = 0;
             lv.w_off[q] = lv.k_off[q] = lv.t_off[q] = 0;
             lv.kuni32[q] = lv.kuni64[q] = 0;
         }
         lv.wuni2 = 0;
         for (int k = 0; k < nd; ++k) {
             const int q = 3 - nd + k;
+            const int64_t stride = int64_t(1) << std::min(j, Lk[k]);
             const int64_t nf = (n[k] - 1) / stride + 1;
+            lv.n[q] = nf;
+            if (j >= Lk[k]) {  // kept with all its nodes: P = I, no tables
+                lv.m[q] = nf;
+                continue;
+            }
             std::vector<double> xf(nf);
             for (int64_t i = 0; i < nf; ++i) xf[i] = x[k][i * stride];
-            lv.n[q] = nf;
             lv.m[q] = (nf - 1) / 2 + 1;
+            lv.co[q] = 1;
             build_dim_tables(xf, tab, &lv.w_off[q], &lv.k_off[q], &lv.t_off[q]);
             if (q == 2) {
                 lv.wuni2 = 1;
@@ -1047,7 +1083,7 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
     // weight of the right N_{L-D} neighbour of every finest node (0 on
     // N_{L-D} itself), D = 1..L, from the coordinates
     P->pro_off.assign(L, std::array<int64_t, 3>{0, 0, 0});
-    for (int D = 1; D <= L; ++D) {
+    for (int D = 1; D <= (per_dim ? 0 : L); ++D) {
         const int64_t s = int64_t(1) << D;
         for (int k = 0; k < nd; ++k) {
             P->pro_off[D - 1][3 - nd + k] = (int64_t)tab.size();
@@ -1060,7 +1096,7 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
 
     // the finest level whose array the single-block kernel takes
     P->small_auto = L;
-    for (int j = 0; j < L; ++j) {
+    for (int j = 0; j < (per_dim ? 0 : L); ++j) {
         const int64_t *nj = (j == 0) ? P->n : P->lv[j - 1].m;
         const int64_t es = (int64_t)P->elem_ws;
         const int64_t base = small_elems(nj) + small_tab_elems(nj, L - j), hp = small_hplane(nj);
@@ -1081,7 +1117,7 @@ static mgard_status build_plan_host(int ndim, const int64_t *dims, int nlevels, 
     // thread's registers, the grid runs every level until the array is small
     // enough for block 0 to finish in shared memory (H: all fine planes)
     P->coop_auto = L;
-    for (int j = 0; j < L; ++j) {
+    for (int j = 0; j < (per_dim ? 0 : L); ++j) {
         const int64_t *nj = (j == 0) ? P->n : P->lv[j - 1].m;
         if (nj[0] <= kMultiMaxSide && nj[1] <= kMultiMaxSide && nj[2] <= kMultiMaxSide) {
             P->coop_auto = j;
@@ -1276,6 +1312,7 @@ bool plan_view(const mgard_plan *P, PlanView *v, PlanLevelView *lv)
             for (int d = 0; d < 3; ++d) {
                 lv[j].n[d] = L.n[d];
                 lv[j].m[d] = L.m[d];
+                lv[j].co[d] = L.co[d];
                 lv[j].w[d] = f32 ? (const void *)tab_ptr<float>(P, L.w_off[d]) : (const void *)tab_ptr<double>(P, L.w_off[d]);
                 lv[j].k[d] = f32 ? (const void *)tab_ptr<float>(P, L.k_off[d]) : (const void *)tab_ptr<double>(P, L.k_off[d]);
                 lv[j].fac[d] = f32 ? (const void *)tab_ptr<float>(P, L.t_off[d]) : (const void *)tab_ptr<double>(P, L.t_off[d]);
@@ -1289,14 +1326,14 @@ bool plan_view(const mgard_plan *P, PlanView *v, PlanLevelView *lv)
 
 extern "C" {
 
-mgard_status mgard_plan_create(int ndim, const int64_t *dims, int nlevels, const double *const *coords,
-                               mgard_dtype dtype, mgard_plan **out)
+static mgard_status plan_create(int ndim, const int64_t *dims, int nlevels, const double *const *coords,
+                                mgard_dtype dtype, mgard_plan **out, const int *dim_levels)
 {
     if (!out) return fail(MGARD_ERR_INVALID_ARG, "plan_create: out is NULL");
     *out = nullptr;  // NULL on every failure path
     std::vector<double> tab;
     mgard_plan *P = nullptr;
-    mgard_status s = build_plan_host(ndim, dims, nlevels, coords, dtype, &P, &tab);
+    mgard_status s = build_plan_host(ndim, dims, nlevels, coords, dtype, &P, &tab, dim_levels);
     if (s != MGARD_OK) return s;
     // device tables in double and float
     std::vector<float> tab32(tab.begin(), tab.end());
@@ -1304,18 +1341,46 @@ mgard_status mgard_plan_create(int ndim, const int64_t *dims, int nlevels, const
     if (err == cudaSuccess) err = cudaMalloc(&P->tab32, tab32.size() * sizeof(float));
     if (err == cudaSuccess) err = cudaMemcpy(P->tab64, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(P->tab32, tab32.data(), tab32.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (err == cudaSuccess) err = configure_plan(P);
+    if (err == cudaSuccess && !P->per_dim) err = configure_plan(P);
     if (err != cudaSuccess) {
         mgard_plan_destroy(P);
         return cuda_fail(err, "plan_create: device tables");
+    }
+    if (P->per_dim) {
+        // the persistent kernel runs the plan: a batch of this one field
+        s = mgard_batch_create(1, &P, 1, &P->pd_batch);
+        if (s == MGARD_OK && mgard_batch_get(P->pd_batch, 0) != 1)
+            s = fail(MGARD_ERR_UNSUPPORTED_SHAPE, "plan_create_per_dim: the shape does not fit the persistent kernel "
+                                                  "(rows of at most 1025 nodes, coarse planes within a block's "
+                                                  "shared memory)");
+        if (s != MGARD_OK) {
+            mgard_plan_destroy(P);
+            return s;
+        }
+        P->ws_bytes = std::max(P->ws_bytes, mgard_batch_workspace_bytes(P->pd_batch));
     }
     *out = P;
     return MGARD_OK;
 }
 
+mgard_status mgard_plan_create(int ndim, const int64_t *dims, int nlevels, const double *const *coords,
+                               mgard_dtype dtype, mgard_plan **out)
+{
+    return plan_create(ndim, dims, nlevels, coords, dtype, out, nullptr);
+}
+
+mgard_status mgard_plan_create_per_dim(int ndim, const int64_t *dims, const int *levels, const double *const *coords,
+                                       mgard_dtype dtype, mgard_plan **out)
+{
+    if (!dims && out) *out = nullptr;
+    std::vector<int> all(ndim > 0 && ndim <= 3 ? ndim : 1, -1);
+    return plan_create(ndim, dims, -1, coords, dtype, out, levels ? levels : all.data());
+}
+
 mgard_status mgard_plan_destroy(mgard_plan *P)
 {
     if (!P) return MGARD_OK;
+    if (P->pd_batch) mgard_batch_destroy(P->pd_batch);
     if (P->owns_tables) {
         if (P->tab64) cudaFree(P->tab64);
         if (P->tab32) cudaFree(P->tab32);
@@ -1336,6 +1401,7 @@ size_t mgard_workspace_bytes(const mgard_plan *P) { return P ? P->ws_bytes : 0; 
 int mgard_plan_launches(const mgard_plan *P, int recompose)
 {
     if (!P) return -1;
+    if (P->per_dim) return 1;  // one persistent launch
     // per level: one restriction + ndim solve sweeps (one fewer where the
     // row-chunk restriction solves along dim 2) + the element-wise
     // kernel(s): interpolation (recompose) or coefficients + coarse
@@ -1416,6 +1482,7 @@ static mgard_status quant_call(const mgard_plan *P, int mode, const double *bins
                                const int32_t *codes_in, void *field_out, int32_t *codes_out, void *stream)
 {
     if (!P) return fail(MGARD_ERR_INVALID_ARG, "quantize: plan is NULL");
+    if (P->per_dim) return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "quantize: not for per-dimension level counts");
     if (!bins) return fail(MGARD_ERR_INVALID_ARG, "quantize: bins is NULL");
     if (mode == 0 && (!field || !codes_out)) return fail(MGARD_ERR_INVALID_ARG, "quantize: NULL device pointer");
     if (mode == 1 && (!codes_in || !field_out)) return fail(MGARD_ERR_INVALID_ARG, "dequantize: NULL device pointer");
@@ -1436,6 +1503,11 @@ mgard_status mg_transform(const mgard_plan *P, int dir, void *d_data, void *d_ws
 {
     mgard_status s = check_call(P, d_data, d_ws, ws_bytes);
     if (s != MGARD_OK) return s;
+    if (P->per_dim) {
+        void *data[1] = {d_data};
+        return dir == 0 ? mgard_batch_decompose(P->pd_batch, data, d_ws, ws_bytes, st)
+                        : mgard_batch_recompose(P->pd_batch, data, d_ws, ws_bytes, st);
+    }
     char *ws = static_cast<char *>(d_ws);
     if (dir == 0) {
         switch (P->dtype) {
@@ -1468,6 +1540,7 @@ mgard_status mgard_recompose_classes(const mgard_plan *P, int nclasses, void *d_
 {
     mgard_status s = check_call(P, d_data, d_ws, ws_bytes);
     if (s != MGARD_OK) return s;
+    if (P->per_dim) return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "recompose_classes: not for per-dimension level counts");
     if (nclasses < 1 || nclasses > P->L + 1)
         return fail(MGARD_ERR_INVALID_ARG, "recompose_classes: nclasses must be in 1.." + std::to_string(P->L + 1));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1484,6 +1557,7 @@ mgard_status mgard_decompose_adjoint(const mgard_plan *P, void *d_data, void *d_
 {
     mgard_status s = check_call(P, d_data, d_ws, ws_bytes);
     if (s != MGARD_OK) return s;
+    if (P->per_dim) return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "decompose_adjoint: not for per-dimension level counts");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(d_ws);
     switch (P->dtype) {
@@ -1497,6 +1571,7 @@ mgard_status mgard_recompose_adjoint(const mgard_plan *P, void *d_data, void *d_
 {
     mgard_status s = check_call(P, d_data, d_ws, ws_bytes);
     if (s != MGARD_OK) return s;
+    if (P->per_dim) return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "recompose_adjoint: not for per-dimension level counts");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(d_ws);
     switch (P->dtype) {
@@ -1518,6 +1593,7 @@ static cudaError_t reconfigure(mgard_plan *P, int j)
 mgard_status mgard_plan_tune(mgard_plan *P, int level, int param, int value)
 {
     if (!P || level < 0 || level >= P->L) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: bad plan or level");
+    if (P->per_dim) return fail(MGARD_ERR_UNSUPPORTED_SHAPE, "plan_tune: not for per-dimension level counts");
     mgard_level &L = P->lv[level];
     const mgard_level saved = L;
     switch (param) {

@@ -118,8 +118,8 @@ int64_t cnt3(const int64_t *n) { return n[0] * n[1] * n[2]; }
 PlanLevelView relabel(const PlanLevelView &v)
 {
     PlanLevelView o = v;
-    o.n[0] = v.n[1]; o.m[0] = v.m[1]; o.w[0] = v.w[1]; o.k[0] = v.k[1]; o.fac[0] = v.fac[1];
-    o.n[1] = 1; o.m[1] = 1; o.w[1] = v.w[0]; o.k[1] = v.k[0]; o.fac[1] = v.fac[0];
+    o.n[0] = v.n[1]; o.m[0] = v.m[1]; o.w[0] = v.w[1]; o.k[0] = v.k[1]; o.fac[0] = v.fac[1]; o.co[0] = v.co[1];
+    o.n[1] = 1; o.m[1] = 1; o.w[1] = v.w[0]; o.k[1] = v.k[0]; o.fac[1] = v.fac[0]; o.co[1] = 0;
     return o;
 }
 
@@ -127,11 +127,21 @@ PlanLevelView relabel(const PlanLevelView &v)
 int64_t level_smem_elems(const PlanLevelView &v)
 {
     const int n1 = (int)v.n[1], n2 = (int)v.n[2], m0 = (int)v.m[0], m1 = (int)v.m[1], m2 = (int)v.m[2];
-    int64_t e = PersistSmem::a(n1, n2, m1, m2);
-    e = std::max<int64_t>(e, PersistSmem::b(n1, m1, m2));
+    const int pm = v.co[1];
+    int64_t e = PersistSmem::a(pm, n1, n2, m1, m2);
+    e = std::max<int64_t>(e, PersistSmem::b(pm, m1, m2));
     e = std::max<int64_t>(e, PersistSmem::c(m0));
-    e = std::max<int64_t>(e, PersistSmem::d(n1, n2, m2));
+    e = std::max<int64_t>(e, PersistSmem::d(pm, n1, n2, m2));
     return e;
+}
+
+// A dim kept with all its nodes at some level (per-dimension level counts).
+bool has_kept_dims(const std::vector<PlanLevelView> &lv)
+{
+    for (const auto &l : lv)
+        for (int d = 0; d < 3; ++d)
+            if (l.n[d] > 1 && !l.co[d]) return true;
+    return false;
 }
 
 constexpr int64_t kPersistMaxSmem = 227 * 1024 - 64;
@@ -176,9 +186,9 @@ bool persist_analyse(const std::vector<mgard_plan *> &plans, Persist &S)
             return false;
         }
         // the small tail: from the first level j >= 1 whose array (V_{j-1})
-        // is small enough for one block
+        // is small enough for one block (its levels coarsen every dim)
         F.nd = F.L;
-        for (int j = 1; j < F.L; ++j) {
+        for (int j = has_kept_dims(F.lv) ? F.L : 1; j < F.L; ++j) {
             const int64_t *ns = F.lv[j - 1].m;
             const int64_t hp = small_hplane(ns), nlev = F.L - j;
             const int64_t el = small_elems(ns) + ns[0] * hp + small_tab_elems(ns, (int)nlev);
@@ -261,11 +271,13 @@ struct CostModel {
     double bpn;          // bytes per ns per block
     double over = 1500;  // per item
     size_t eu, ew;
-    double a(const PlanLevelView &l, int planes, bool first, bool dec) const
+    // rows of an item: a plane's rows (by planes) or `per` rows
+    static double rows(const PlanLevelView &l, int per, bool fine) { return l.co[1] ? (double)(fine ? l.n[1] : l.m[1]) : per; }
+    double a(const PlanLevelView &l, int per, bool first, bool dec) const
     {
         const double ex = (double)(first ? eu : ew);
-        const double fine = (double)planes * l.n[1] * l.n[2] * ex * (dec ? 2.3 : 1.1);
-        const double coarse = (double)planes * l.m[1] * l.m[2] * ew * 1.5;
+        const double fine = rows(l, per, true) * l.n[2] * ex * (dec ? 2.3 : 1.1);
+        const double coarse = rows(l, per, false) * l.m[2] * ew * 1.5;
         return over + (fine + coarse) / bpn;
     }
     double c(const PlanLevelView &l) const
@@ -273,15 +285,15 @@ struct CostModel {
         const double bytes = ((double)l.n[0] + l.m[0]) * kPersistPanel * ew;
         return over + bytes / bpn + 60.0 * ((l.m[0] + kPersistWarps - 1) / kPersistWarps);
     }
-    double b(const PlanLevelView &l, int planes, bool dec) const
+    double b(const PlanLevelView &l, int per, bool dec) const
     {
-        const double bytes = (double)planes * l.m[1] * l.m[2] * ew * (dec ? 3.0 : 2.0);
-        return over + bytes / bpn + (l.n[1] > 1 ? 30.0 * (l.m[1] + l.m[2]) : 10.0 * l.m[2] / 32 + 300.0);
+        const double bytes = rows(l, per, false) * l.m[2] * ew * (dec ? 3.0 : 2.0);
+        return over + bytes / bpn + (l.co[1] ? 30.0 * (l.m[1] + l.m[2]) : 10.0 * l.m[2] / 32 + 300.0);
     }
-    double d(const PlanLevelView &l, int planes, bool first) const
+    double d(const PlanLevelView &l, int per, bool first) const
     {
         const double ex = (double)(first ? eu : ew);
-        return over + ((double)planes * l.n[1] * l.n[2] * ex * 2.2 + (double)planes * l.m[1] * l.m[2] * ew * 2.0) / bpn;
+        return over + (rows(l, per, true) * l.n[2] * ex * 2.2 + rows(l, per, false) * l.m[2] * ew * 2.0) / bpn;
     }
     double small() const { return 40000.0; }
     double place(const PlanLevelView &l, bool first) const
@@ -306,17 +318,20 @@ void build_tasks(const Persist &S, int dir, const CostModel &cm, TaskList &T)
         const PField &F = S.f[fi];
         const int fld = (int)fi;
         if (F.L == 0) continue;
-        auto per_of = [](const PlanLevelView &l) { return l.n[1] > 1 ? 1 : kPersistWarps; };
+        // by planes (dim 1 coarsens): one plane per item; by rows: 8 rows
+        auto per_of = [](const PlanLevelView &l) { return l.co[1] ? 1 : kPersistWarps; };
+        auto fine_units = [](const PlanLevelView &l) { return l.co[1] ? l.n[0] : l.n[0] * l.n[1]; };
+        auto coarse_units = [](const PlanLevelView &l) { return l.co[1] ? l.m[0] : l.m[0] * l.m[1]; };
         auto panels = [](const PlanLevelView &l) { return l.m[1] * ceil_div(l.m[2], kPersistPanel); };
         std::vector<int> Bt(F.nd);
         int prev = -1, prevA = -1;
         for (int j = 0; j < F.nd; ++j) {
             const PlanLevelView &l = F.lv[j];
             const int gl = F.lv_base + j, per = per_of(l);
-            const int A = T.add(PK_A, gl, per, ceil_div(l.n[0], per), dec ? prev : prevA, -1,
+            const int A = T.add(PK_A, gl, per, ceil_div(fine_units(l), per), dec ? prev : prevA, -1,
                                 cm.a(l, per, j == 0, dec), fld);
             const int C = T.add(PK_C, gl, 1, panels(l), A, -1, cm.c(l), fld);
-            Bt[j] = T.add(PK_B, gl, per, ceil_div(l.m[0], per), C, -1, cm.b(l, per, dec), fld);
+            Bt[j] = T.add(PK_B, gl, per, ceil_div(coarse_units(l), per), C, -1, cm.b(l, per, dec), fld);
             prev = Bt[j];
             prevA = A;
         }
@@ -333,7 +348,8 @@ void build_tasks(const Persist &S, int dir, const CostModel &cm, TaskList &T)
             for (int j = F.nd - 1; j >= 0; --j) {
                 const PlanLevelView &l = F.lv[j];
                 const int per = per_of(l);
-                last = T.add(PK_D, F.lv_base + j, per, ceil_div(l.n[0], per), Bt[j], last, cm.d(l, per, j == 0), fld);
+                last = T.add(PK_D, F.lv_base + j, per, ceil_div(fine_units(l), per), Bt[j], last, cm.d(l, per, j == 0),
+                             fld);
             }
         }
     }
@@ -532,6 +548,7 @@ void persist_tables(Persist &S, int dir, void *const *d_data, char *ws)
                 L.w[d] = v.w[d];
                 L.k[d] = v.k[d];
                 L.fac[d] = v.fac[d];
+                L.co[d] = v.co[d];
             }
             L.first = (j == 0) ? 1 : 0;
         }

@@ -46,7 +46,7 @@ __device__ __forceinline__ unsigned persist_ld_acquire(const unsigned *p)
 template <typename TW>
 struct PGeo {
     int n0, n1, n2, m0, m1, m2;
-    int a0, a1, a2;
+    int c0, c1, c2;  // the dim coarsens at this level
     const TW *w0, *w1, *w2, *k0, *k1, *k2, *f0, *f1, *f2;
 };
 
@@ -56,7 +56,7 @@ __device__ __forceinline__ PGeo<TW> pgeo(const PersistLevel &L)
     PGeo<TW> g;
     g.n0 = L.n[0]; g.n1 = L.n[1]; g.n2 = L.n[2];
     g.m0 = L.m[0]; g.m1 = L.m[1]; g.m2 = L.m[2];
-    g.a0 = g.n0 > 1; g.a1 = g.n1 > 1; g.a2 = g.n2 > 1;
+    g.c0 = L.co[0]; g.c1 = L.co[1]; g.c2 = L.co[2];
     g.w0 = static_cast<const TW *>(L.w[0]); g.w1 = static_cast<const TW *>(L.w[1]);
     g.w2 = static_cast<const TW *>(L.w[2]);
     g.k0 = static_cast<const TW *>(L.k[0]); g.k1 = static_cast<const TW *>(L.k[1]);
@@ -87,7 +87,7 @@ __device__ __forceinline__ void persist_stage(T *dst, const T *src, int n, int s
 // ---------------------------------------------------------------------------
 // Shared-memory layouts (elements of TW), shared with the host, which sizes
 // the launch by the largest item of the batch.  rn / rm: a fine / coarse row
-// rounded up to four elements.
+// rounded up to four elements; pm: the level runs by planes (dim 1 coarsens).
 // ---------------------------------------------------------------------------
 struct PersistSmem {
     // phase A: tables w1, w2, k1, k2; the ring of K_2 C rows (active dim 1);
@@ -98,22 +98,22 @@ struct PersistSmem {
     {
         return persist_round4(2 * n1 + 2 * n2 + 5 * m1 + 5 * m2);
     }
-    static __host__ __device__ int a_ring(int n1, int m2) { return n1 > 1 ? kPersistRing * persist_round4(m2) : 0; }
-    static __host__ __device__ int a_warp(int n1, int n2, int m2)
+    static __host__ __device__ int a_ring(int pm, int m2) { return pm ? kPersistRing * persist_round4(m2) : 0; }
+    static __host__ __device__ int a_warp(int pm, int n2, int m2)
     {
         const int rn = persist_round4(n2), rm = persist_round4(m2);
-        return n1 > 1 ? 2 * rm + 4 * rn + 8 * rm : rm + rn + 2 * rm;
+        return pm ? 2 * rm + 4 * rn + 8 * rm : rm + rn + 2 * rm;
     }
-    static __host__ __device__ int64_t a(int n1, int n2, int m1, int m2)
+    static __host__ __device__ int64_t a(int pm, int n1, int n2, int m1, int m2)
     {
-        return a_tab(n1, n2, m1, m2) + a_ring(n1, m2) + (int64_t)kPersistWarps * a_warp(n1, n2, m2);
+        return a_tab(n1, n2, m1, m2) + a_ring(pm, m2) + (int64_t)kPersistWarps * a_warp(pm, n2, m2);
     }
     // phase B: factors of dims 2 and 1, then the coarse plane (active dim 1)
     // or one coarse row per warp
     static __host__ __device__ int b_tab(int m1, int m2) { return persist_round4(3 * m1 + 3 * m2); }
-    static __host__ __device__ int64_t b(int n1, int m1, int m2)
+    static __host__ __device__ int64_t b(int pm, int m1, int m2)
     {
-        return b_tab(m1, m2) + (n1 > 1 ? (int64_t)m1 * m2 : (int64_t)kPersistWarps * persist_round4(m2));
+        return b_tab(m1, m2) + (pm ? (int64_t)m1 * m2 : (int64_t)kPersistWarps * persist_round4(m2));
     }
     // phase C: factors of dim 0, the panel of F, the ring of G rows, four
     // carry arrays
@@ -126,14 +126,14 @@ struct PersistSmem {
     // sets of {two fine rows, four coarse source rows of V and z}, or one
     // fine row and four source rows
     static __host__ __device__ int d_tab(int n1, int n2) { return persist_round4(2 * n1 + 2 * n2); }
-    static __host__ __device__ int d_warp(int n1, int n2, int m2)
+    static __host__ __device__ int d_warp(int pm, int n2, int m2)
     {
         const int rn = persist_round4(n2), rm = persist_round4(m2);
-        return n1 > 1 ? 2 * rm + 4 * rn + 8 * rm : rn + 4 * rm;
+        return pm ? 2 * rm + 4 * rn + 8 * rm : rn + 4 * rm;
     }
-    static __host__ __device__ int64_t d(int n1, int n2, int m2)
+    static __host__ __device__ int64_t d(int pm, int n1, int n2, int m2)
     {
-        return d_tab(n1, n2) + (int64_t)kPersistWarps * d_warp(n1, n2, m2);
+        return d_tab(n1, n2) + (int64_t)kPersistWarps * d_warp(pm, n2, m2);
     }
 };
 
@@ -151,12 +151,12 @@ __device__ __forceinline__ void persist_a_row(const PGeo<TW> &g, XT *xrow, int i
                                               const TW *tw2, const TW *tk2, const TW *c0, const TW *c1, XT *rb,
                                               TW *hrow, int lane)
 {
-    const int q1 = g.a1 & i1 & 1;
+    const int q1 = g.c1 & i1 & 1;
     const bool rodd = podd || q1;  // every node of the row is outside the coarse grid
     if constexpr (MODE == MODE_DEC) {
         const TW wl1 = q1 ? tw1[2 * i1] : TW(1), wr1 = q1 ? tw1[2 * i1 + 1] : TW(0);
         for (int i2 = lane; i2 < g.n2; i2 += 32) {
-            const int q2 = g.a2 & i2 & 1, x = i2 >> 1;
+            const int q2 = g.c2 & i2 & 1, x = i2 >> g.c2;
             if (rodd || q2) {
                 const TW wl2 = q2 ? tw2[2 * i2] : TW(1), wr2 = q2 ? tw2[2 * i2 + 1] : TW(0);
                 const TW x0 = wl2 * c0[x] + wr2 * c0[x + q2];
@@ -170,10 +170,10 @@ __device__ __forceinline__ void persist_a_row(const PGeo<TW> &g, XT *xrow, int i
         }
     } else {
         for (int i2 = lane; i2 < g.n2; i2 += 32)
-            if (!(rodd || (g.a2 & i2 & 1))) rb[i2] = XT(0);
+            if (!(rodd || (g.c2 & i2 & 1))) rb[i2] = XT(0);
     }
     __syncwarp();
-    if (g.a2) {
+    if (g.c2) {
         for (int X = lane; X < g.m2; X += 32) {
             TW h = TW(0);
 #pragma unroll
@@ -183,8 +183,8 @@ __device__ __forceinline__ void persist_a_row(const PGeo<TW> &g, XT *xrow, int i
             }
             hrow[X] = h;
         }
-    } else if (lane == 0) {
-        hrow[0] = static_cast<TW>(rb[0]);
+    } else {  // P = I along dim 2: its stencil and solve cancel
+        for (int X = lane; X < g.m2; X += 32) hrow[X] = static_cast<TW>(rb[X]);
     }
     __syncwarp();
 }
@@ -196,31 +196,34 @@ __device__ void persist_a(const PersistLevel &L, int item, int per, TW *sm)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t np = (int64_t)g.n1 * g.n2, mc = (int64_t)g.m1 * g.m2;
     const int rn = persist_round4(g.n2), rm = persist_round4(g.m2);
-    const int sx = g.a2 ? 2 : 0;  // stride of the coarse nodes along a fine row
+    const int sx = g.c2 ? 2 : 1;  // stride of the coarse nodes along a fine row
     XT *X = static_cast<XT *>(L.X);
     TW *V = static_cast<TW *>(L.V), *G = static_cast<TW *>(L.G);
     TW *tw1 = sm, *tw2 = tw1 + 2 * g.n1, *tk1 = tw2 + 2 * g.n2, *tk2 = tk1 + 5 * g.m1;
     TW *ring = sm + PersistSmem::a_tab(g.n1, g.n2, g.m1, g.m2);
-    TW *wb = ring + PersistSmem::a_ring(g.n1, g.m2) + warp * PersistSmem::a_warp(g.n1, g.n2, g.m2);
+    TW *wb = ring + PersistSmem::a_ring(g.c1, g.m2) + warp * PersistSmem::a_warp(g.c1, g.n2, g.m2);
     TW *wrow0 = wb, *wrow1 = wb + rm;
 
-    if (!g.a1) {
-        // one row per plane: plane i0 = item * per + warp; the row and (odd
-        // plane of a decomposition) its neighbours' coarse nodes staged
-        const int i0 = item * per + warp;
-        const bool mine = warp < per && i0 < g.n0;
-        const bool podd = g.a0 && (i0 & 1);
+    if (!g.c1) {
+        // by rows: row r = item * per + warp of the n0 x n1 rows (its own
+        // coarse row: dim 1 does not coarsen); the row and (odd plane of a
+        // decomposition) its neighbours' coarse nodes staged
+        const int r = item * per + warp;
+        const bool mine = warp < per && r < g.n0 * g.n1;
+        const int i0 = mine ? r / g.n1 : 0, i1 = mine ? r % g.n1 : 0;
+        const bool podd = g.c0 && (i0 & 1);
+        const int64_t ro = (int64_t)i0 * np + (int64_t)i1 * g.n2;
         XT *rb = reinterpret_cast<XT *>(wb + rm);
         XT *sa = reinterpret_cast<XT *>(wb + rm + rn), *sb = reinterpret_cast<XT *>(wb + 2 * rm + rn);
         if (mine) {
-            persist_stage<XT>(rb, X + (int64_t)i0 * np, g.n2, 1, lane);
+            persist_stage<XT>(rb, X + ro, g.n2, 1, lane);
             if (MODE == MODE_DEC && podd) {
-                persist_stage<XT>(sa, X + (int64_t)(i0 - 1) * np, g.m2, sx, lane);
-                persist_stage<XT>(sb, X + (int64_t)(i0 + 1) * np, g.m2, sx, lane);
+                persist_stage<XT>(sa, X + ro - np, g.m2, sx, lane);
+                persist_stage<XT>(sb, X + ro + np, g.m2, sx, lane);
             }
         }
         cp_async_commit();
-        if (g.a2) {
+        if (g.c2) {
             persist_table<TW>(tw2, g.w2, 2 * g.n2);
             persist_table<TW>(tk2, g.k2, 5 * g.m2);
         }
@@ -228,7 +231,7 @@ __device__ void persist_a(const PersistLevel &L, int item, int per, TW *sm)
         __syncthreads();  // the tables
         if (mine) {
             const TW wl = podd ? __ldg(g.w0 + 2 * i0) : TW(0), wr = podd ? __ldg(g.w0 + 2 * i0 + 1) : TW(0);
-            TW *Vr = V + (int64_t)(i0 >> 1) * mc;
+            TW *Vr = V + (int64_t)(i0 >> g.c0) * mc + (int64_t)i1 * g.m2;
             for (int x = lane; x < g.m2; x += 32) {
                 if (podd) {
                     if (MODE == MODE_DEC) wrow0[x] = wl * static_cast<TW>(sa[x]) + wr * static_cast<TW>(sb[x]);
@@ -239,8 +242,8 @@ __device__ void persist_a(const PersistLevel &L, int item, int per, TW *sm)
                 }
             }
             __syncwarp();
-            persist_a_row<XT, TW, MODE>(g, X + (int64_t)i0 * np, 0, podd, tw1, tw2, tk2, wrow0, wrow0, rb,
-                                        G + (int64_t)i0 * mc, lane);
+            persist_a_row<XT, TW, MODE>(g, X + ro, i1, podd, tw1, tw2, tk2, wrow0, wrow0, rb,
+                                        G + (int64_t)i0 * mc + (int64_t)i1 * g.m2, lane);
         }
         return;
     }
@@ -252,12 +255,12 @@ __device__ void persist_a(const PersistLevel &L, int item, int per, TW *sm)
     // Y' = (pair batch start) - 1 + warp is reduced along dim 1 once the
     // rows 2Y' - 2 .. 2Y' + 2 are in the ring
     const int i0 = item;
-    const bool podd = g.a0 && (i0 & 1);
+    const bool podd = g.c0 && (i0 & 1);
     const TW wl = podd ? __ldg(g.w0 + 2 * i0) : TW(0), wr = podd ? __ldg(g.w0 + 2 * i0 + 1) : TW(0);
     TW *sets = wb + 2 * rm;
     XT *Xp = X + (int64_t)i0 * np;
     TW *Gp = G + (int64_t)i0 * mc;
-    TW *Vp = V + (int64_t)(i0 >> 1) * mc;
+    TW *Vp = V + (int64_t)(i0 >> g.c0) * mc;
     auto row = [&](int set, int k) { return reinterpret_cast<XT *>(sets + set * (2 * rn + 4 * rm) + k * rn); };
     auto src = [&](int set, int k) {
         return reinterpret_cast<XT *>(sets + set * (2 * rn + 4 * rm) + 2 * rn + k * rm);
@@ -288,7 +291,7 @@ __device__ void persist_a(const PersistLevel &L, int item, int per, TW *sm)
     stage_pair(warp, 0);
     persist_table<TW>(tw1, g.w1, 2 * g.n1);
     persist_table<TW>(tk1, g.k1, 5 * g.m1);
-    if (g.a2) {
+    if (g.c2) {
         persist_table<TW>(tw2, g.w2, 2 * g.n2);
         persist_table<TW>(tk2, g.k2, 5 * g.m2);
     }
@@ -372,8 +375,9 @@ __device__ void persist_c(const PersistLevel &L, int item, TW *sm)
     TW *S = sm + PersistSmem::c_tab(g.m0);
     TW *ring = S + (int64_t)g.m0 * PW;
     TW *cy = ring + RG * PW, *cp = cy + NW * PW, *cz = cp + NW * PW, *cq = cz + NW * PW;
-    if (!g.a0) {  // no dim 0: F is G
-        if (warp == 0 && xok) F[base] = G[base];
+    if (!g.c0) {  // P = I along dim 0 (m0 = n0): F is G
+        if (xok)
+            for (int Z = warp; Z < g.m0; Z += NW) F[Z * rs + base] = G[Z * rs + base];
         return;
     }
     // G row r of the panel into ring slot r % RG (zero-filled past the last
@@ -549,19 +553,20 @@ __device__ void persist_b(const PersistLevel &L, int item, int per, TW *sm)
     TW *tf2 = sm, *tf1 = tf2 + 3 * g.m2;
     TW *S = sm + PersistSmem::b_tab(g.m1, g.m2);
 
-    if (!g.a1) {
-        const int Z = item * per + warp;
-        const bool mine = warp < per && Z < g.m0;
+    if (!g.c1) {
+        // by rows: coarse row r = item * per + warp of the m0 x m1 rows
+        const int r = item * per + warp;
+        const bool mine = warp < per && r < g.m0 * g.m1;
         TW *row = S + warp * persist_round4(g.m2);
-        if (mine) persist_stage<TW>(row, F + (int64_t)Z * mc, g.m2, 1, lane);
+        if (mine) persist_stage<TW>(row, F + (int64_t)r * g.m2, g.m2, 1, lane);
         cp_async_commit();
-        if (g.a2) persist_table<TW>(tf2, g.f2, 3 * g.m2);
+        if (g.c2) persist_table<TW>(tf2, g.f2, 3 * g.m2);
         cp_async_wait<0>();
         __syncthreads();
         if (mine) {
-            if (g.a2) persist_warp_solve<TW>(row, g.m2, tf2, lane);
+            if (g.c2) persist_warp_solve<TW>(row, g.m2, tf2, lane);
             for (int x = lane; x < g.m2; x += 32) {
-                const int64_t o = (int64_t)Z * mc + x;
+                const int64_t o = (int64_t)r * g.m2 + x;
                 if constexpr (MODE == MODE_DEC) V[o] += row[x];
                 else F[o] = row[x];
             }
@@ -573,11 +578,11 @@ __device__ void persist_b(const PersistLevel &L, int item, int per, TW *sm)
     TW *Fz = F + (int64_t)Z * mc;
     for (int64_t e = tid; e < mc; e += nt) cp_async_elem<TW>(S + e, Fz + e, true);
     cp_async_commit();
-    if (g.a2) persist_table<TW>(tf2, g.f2, 3 * g.m2);
+    if (g.c2) persist_table<TW>(tf2, g.f2, 3 * g.m2);
     persist_table<TW>(tf1, g.f1, 3 * g.m1);
     cp_async_wait<0>();
     __syncthreads();
-    if (g.a2)
+    if (g.c2)
         for (int Yr = tid; Yr < g.m1; Yr += nt) persist_line_solve<TW>(S + (int64_t)Yr * g.m2, 1, g.m2, tf2);
     __syncthreads();
     for (int x = tid; x < g.m2; x += nt) persist_line_solve<TW>(S + x, g.m2, g.m1, tf1);
@@ -599,11 +604,11 @@ template <typename XT, typename TW>
 __device__ __forceinline__ void persist_d_row(const PGeo<TW> &g, XT *xrow, const XT *rb, int i1, bool podd,
                                               const TW *tw1, const TW *tw2, const TW *c0, const TW *c1, int lane)
 {
-    const int q1 = g.a1 & i1 & 1;
+    const int q1 = g.c1 & i1 & 1;
     const bool even_row = !podd && !q1;
     const TW wl1 = q1 ? tw1[2 * i1] : TW(1), wr1 = q1 ? tw1[2 * i1 + 1] : TW(0);
     for (int i2 = lane; i2 < g.n2; i2 += 32) {
-        const int q2 = g.a2 & i2 & 1, x = i2 >> 1;
+        const int q2 = g.c2 & i2 & 1, x = i2 >> g.c2;
         TW r;
         if (even_row && !q2) {
             r = c0[x];  // coarse node: V - z
@@ -627,19 +632,21 @@ __device__ void persist_d(const PersistLevel &L, int item, int per, TW *sm)
     XT *X = static_cast<XT *>(L.X);
     const TW *V = static_cast<const TW *>(L.V), *Zc = static_cast<const TW *>(L.F);
     TW *tw1 = sm, *tw2 = tw1 + 2 * g.n1;
-    TW *wb = sm + PersistSmem::d_tab(g.n1, g.n2) + warp * PersistSmem::d_warp(g.n1, g.n2, g.m2);
+    TW *wb = sm + PersistSmem::d_tab(g.n1, g.n2) + warp * PersistSmem::d_warp(g.c1, g.n2, g.m2);
 
-    if (!g.a1) {
-        // one row per plane; W = V - z of the coarse row(s) computed from
-        // the staged rows of V and z
-        const int i0 = item * per + warp;
-        const bool mine = warp < per && i0 < g.n0;
-        const bool podd = g.a0 && (i0 & 1);
+    if (!g.c1) {
+        // by rows; W = V - z of the coarse row(s) computed from the staged
+        // rows of V and z
+        const int r = item * per + warp;
+        const bool mine = warp < per && r < g.n0 * g.n1;
+        const int i0 = mine ? r / g.n1 : 0, i1 = mine ? r % g.n1 : 0;
+        const bool podd = g.c0 && (i0 & 1);
+        const int64_t ro = (int64_t)i0 * np + (int64_t)i1 * g.n2;
         XT *rb = reinterpret_cast<XT *>(wb);
-        TW *sv = wb + rn;  // V, z of coarse plane i0/2 (and i0/2 + 1 when odd)
+        TW *sv = wb + rn;  // V, z of the coarse row (and the next coarse plane's when odd)
         if (mine) {
-            persist_stage<XT>(rb, X + (int64_t)i0 * np, g.n2, 1, lane);
-            const int64_t o = (int64_t)(i0 >> 1) * mc;
+            persist_stage<XT>(rb, X + ro, g.n2, 1, lane);
+            const int64_t o = (int64_t)(i0 >> g.c0) * mc + (int64_t)i1 * g.m2;
             persist_stage<TW>(sv, V + o, g.m2, 1, lane);
             persist_stage<TW>(sv + rm, Zc + o, g.m2, 1, lane);
             if (podd) {
@@ -648,7 +655,7 @@ __device__ void persist_d(const PersistLevel &L, int item, int per, TW *sm)
             }
         }
         cp_async_commit();
-        if (g.a2) persist_table<TW>(tw2, g.w2, 2 * g.n2);
+        if (g.c2) persist_table<TW>(tw2, g.w2, 2 * g.n2);
         cp_async_wait<0>();
         __syncthreads();
         if (mine) {
@@ -657,7 +664,7 @@ __device__ void persist_d(const PersistLevel &L, int item, int per, TW *sm)
             for (int x = lane; x < g.m2; x += 32)
                 sv[x] = podd ? wl * (sv[x] - sv[rm + x]) + wr * (sv[2 * rm + x] - sv[3 * rm + x]) : sv[x] - sv[rm + x];
             __syncwarp();
-            persist_d_row<XT, TW>(g, X + (int64_t)i0 * np, rb, 0, podd, tw1, tw2, sv, sv, lane);
+            persist_d_row<XT, TW>(g, X + ro, rb, i1, podd, tw1, tw2, sv, sv, lane);
         }
         return;
     }
@@ -667,10 +674,10 @@ __device__ void persist_d(const PersistLevel &L, int item, int per, TW *sm)
     // next; per pair the two fine rows and the sources of W row Y+1 are
     // staged one pair ahead
     const int i0 = item;
-    const bool podd = g.a0 && (i0 & 1);
+    const bool podd = g.c0 && (i0 & 1);
     const TW wl = podd ? __ldg(g.w0 + 2 * i0) : TW(0), wr = podd ? __ldg(g.w0 + 2 * i0 + 1) : TW(0);
     XT *Xp = X + (int64_t)i0 * np;
-    const int64_t co = (int64_t)(i0 >> 1) * mc;
+    const int64_t co = (int64_t)(i0 >> g.c0) * mc;
     TW *wA = wb, *wB = wb + rm;
     TW *sets = wb + 2 * rm;
     auto row = [&](int set, int k) { return reinterpret_cast<XT *>(sets + set * (2 * rn + 4 * rm) + k * rn); };
@@ -704,7 +711,7 @@ __device__ void persist_d(const PersistLevel &L, int item, int per, TW *sm)
         cp_async_commit();
     }
     persist_table<TW>(tw1, g.w1, 2 * g.n1);
-    if (g.a2) persist_table<TW>(tw2, g.w2, 2 * g.n2);
+    if (g.c2) persist_table<TW>(tw2, g.w2, 2 * g.n2);
     __syncthreads();  // the tables
     if (Yb >= Ye) return;
     cp_async_wait<0>();
@@ -753,7 +760,7 @@ __device__ void persist_place(const PersistParams &p, const PersistTask &t, int 
         const int r = item * kPersistPlaceRows + rr * kPersistWarps + warp;
         if (r >= rows) break;
         const int Z = r / m1, Y = r % m1;
-        const int64_t orow = ((int64_t)(L.n[0] > 1 ? 2 * Z : 0) * n1 + (n1 > 1 ? 2 * Y : 0)) * n2;
+        const int64_t orow = ((int64_t)(Z << L.co[0]) * n1 + (Y << L.co[1])) * n2;
         for (int x0 = lane; x0 < m2; x0 += 32 * U) {
             const TW *src[U];
 #pragma unroll
@@ -764,11 +771,11 @@ __device__ void persist_place(const PersistParams &p, const PersistTask &t, int 
                 int k = 0, z = Z, y = Y, x = xc;
                 while (k + 1 < t.nlevels) {
                     const PersistLevel &N = lv[k + 1];
-                    const int odd = ((N.n[0] > 1) & z) | ((N.n[1] > 1) & y) | ((N.n[2] > 1) & x);
+                    const int odd = (N.co[0] & z) | (N.co[1] & y) | (N.co[2] & x);
                     if (odd & 1) break;
-                    z >>= 1;
-                    y >>= 1;
-                    x >>= 1;
+                    z >>= N.co[0];
+                    y >>= N.co[1];
+                    x >>= N.co[2];
                     ++k;
                 }
                 const PersistLevel &K = lv[k];
@@ -781,7 +788,7 @@ __device__ void persist_place(const PersistParams &p, const PersistTask &t, int 
 #pragma unroll
             for (int u = 0; u < U; ++u)
                 if (src[u]) {
-                    const int64_t o = orow + (n2 > 1 ? 2 * (x0 + 32 * u) : 0);
+                    const int64_t o = orow + ((x0 + 32 * u) << L.co[2]);
                     if (L.first) static_cast<TX *>(L.X)[o] = static_cast<TX>(v[u]);
                     else static_cast<TW *>(L.X)[o] = v[u];
                 }

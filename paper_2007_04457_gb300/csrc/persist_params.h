@@ -39,7 +39,11 @@ enum PersistKind {
 // One grid level of one field.  Fields with two active dims are relabelled
 // (rows, 1, columns), so that their rows are the planes of the items; a
 // field's first level works on the user array (type TX), the others on the
-// compact coarse array of the level before (type TW).
+// compact coarse array of the level before (type TW).  A dim that does not
+// coarsen at the level (co = 0, m = n) has P = I: no interpolation, and its
+// stencil factor M and solve with M cancel, so both are skipped.  A level
+// whose dim 1 does not coarsen runs "by rows": every fine row is its own
+// coarse row, and items take rows instead of planes.
 struct PersistLevel {
     void *X;                  // level array
     void *V;                  // compact coarse array V (TW)
@@ -49,6 +53,7 @@ struct PersistLevel {
     const void *w[3];         // interpolation weight pairs (TW)
     const void *k[3];         // 5-point stencil rows (TW)
     const void *fac[3];       // LU factors (a, inv, q) (TW)
+    int co[3];                // 1: the dim coarsens at this level (0: inactive, or kept with all its nodes)
     int first;                // 1: X has type TX
 };
 

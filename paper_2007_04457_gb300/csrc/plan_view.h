@@ -10,6 +10,7 @@ namespace mg {
 
 struct PlanLevelView {
     int64_t n[3], m[3];              // fine / coarse node counts (leading dims padded with 1)
+    int co[3];                       // 1: the dim coarsens at this level
     const void *w[3], *k[3], *fac[3];  // device tables in the plan's arithmetic type
 };
 

@@ -65,6 +65,8 @@ def _load() -> ctypes.CDLL:
         "mgard_plan_tune": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "mgard_plan_get_tune": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "mgard_plan_check": ([vp, vp, vp], ctypes.c_int),
+        "mgard_plan_create_per_dim": ([ctypes.c_int, i64p, ctypes.POINTER(ctypes.c_int), dpp, ctypes.c_int,
+                                       ctypes.POINTER(vp)], ctypes.c_int),
         "mgard_batch_create": ([ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)],
                                ctypes.c_int),
         "mgard_batch_destroy": ([vp], ctypes.c_int),
@@ -104,21 +106,38 @@ def _check(status: int, what: str) -> None:
 
 # --------------------------------------------------------------- C-named calls
 
+def _coords_arg(ndim, coords, keep):
+    if coords is None:
+        return None
+    import numpy as np
+    arrs = [np.ascontiguousarray(c, dtype=np.float64) for c in coords]
+    keep.extend(arrs)
+    return (ctypes.POINTER(ctypes.c_double) * ndim)(
+        *[a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in arrs])
+
+
 def mgard_plan_create(ndim, dims, nlevels, coords, dtype) -> int:
     """Returns the plan handle (an integer).  coords: None or ndim float64
     numpy arrays."""
     d = (ctypes.c_int64 * ndim)(*[int(v) for v in dims])
     out = ctypes.c_void_p()
     keep = []
-    cptr = None
-    if coords is not None:
-        import numpy as np
-        arrs = [np.ascontiguousarray(c, dtype=np.float64) for c in coords]
-        keep.extend(arrs)
-        cptr = (ctypes.POINTER(ctypes.c_double) * ndim)(
-            *[a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in arrs])
+    cptr = _coords_arg(ndim, coords, keep)
     _check(LIB.mgard_plan_create(ndim, d, nlevels, cptr, dtype, ctypes.byref(out)),
            "mgard_plan_create")
+    return out.value
+
+
+def mgard_plan_create_per_dim(ndim, dims, levels, coords, dtype) -> int:
+    """A plan with a level count per dimension (levels: None, or ndim ints,
+    -1 = that dimension's maximum)."""
+    d = (ctypes.c_int64 * ndim)(*[int(v) for v in dims])
+    lv = None if levels is None else (ctypes.c_int * ndim)(*[int(v) for v in levels])
+    out = ctypes.c_void_p()
+    keep = []
+    cptr = _coords_arg(ndim, coords, keep)
+    _check(LIB.mgard_plan_create_per_dim(ndim, d, lv, cptr, dtype, ctypes.byref(out)),
+           "mgard_plan_create_per_dim")
     return out.value
 
 
@@ -264,15 +283,24 @@ class Plan:
     nlevels: number of levels, -1 for the maximum the shape allows
     coords:  None (uniform) or one increasing float64 array per dimension
     dtype:   "f32", "f64" or "f32_mixed"
+    dim_levels: None, or a level count per dimension (-1 = that dimension's
+             maximum; "max" = all maxima): each dimension coarsens in its
+             first dim_levels[k] steps and then keeps its nodes
     """
 
-    def __init__(self, shape, nlevels: int = -1, coords=None, dtype: str = "f32"):
+    def __init__(self, shape, nlevels: int = -1, coords=None, dtype: str = "f32", dim_levels=None):
         if dtype not in _DTYPE_CODES:
             raise ValueError(f"dtype must be one of {sorted(_DTYPE_CODES)}")
         self.shape = tuple(int(n) for n in shape)
         self.dtype = dtype
-        self.handle = mgard_plan_create(len(self.shape), self.shape, nlevels, coords,
-                                        _DTYPE_CODES[dtype])
+        if dim_levels is None:
+            self.handle = mgard_plan_create(len(self.shape), self.shape, nlevels, coords,
+                                            _DTYPE_CODES[dtype])
+        else:
+            # a level count per dimension ("max" = every dimension its maximum)
+            lv = None if dim_levels == "max" else list(dim_levels)
+            self.handle = mgard_plan_create_per_dim(len(self.shape), self.shape, lv, coords,
+                                                    _DTYPE_CODES[dtype])
         self.levels = mgard_plan_levels(self.handle)
         self.workspace_bytes = mgard_workspace_bytes(self.handle)
         self._ws = None
