@@ -29,6 +29,8 @@
 // sets a status bit and the block goes on.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "params.h"
 #include "persist_params.h"
@@ -83,6 +85,25 @@ __device__ __forceinline__ void persist_stage(T *dst, const T *src, int n, int s
 {
     for (int i = lane; i < n; i += 32) cp_async_elem<T>(dst + i, src + (int64_t)i * s, true);
 }
+
+// Elements 2j and 2j+1 of a shared-memory row (8- or 16-byte aligned pair).
+template <typename T>
+struct Pair2 {
+    using V = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    static __device__ __forceinline__ void load(const T *row, int j, T &a, T &b)
+    {
+        const V v = reinterpret_cast<const V *>(row)[j];
+        a = static_cast<T>(v.x);
+        b = static_cast<T>(v.y);
+    }
+    static __device__ __forceinline__ void store(T *row, int j, T a, T b)
+    {
+        V v;
+        v.x = a;
+        v.y = b;
+        reinterpret_cast<V *>(row)[j] = v;
+    }
+};
 
 // ---------------------------------------------------------------------------
 // Shared-memory layouts (elements of TW), shared with the host, which sizes
@@ -153,15 +174,64 @@ __device__ __forceinline__ void persist_a_row(const PGeo<TW> &g, XT *xrow, int i
 {
     const int q1 = g.c1 & i1 & 1;
     const bool rodd = podd || q1;  // every node of the row is outside the coarse grid
+    if (g.c2) {
+        // lane takes the column pairs (2j, 2j+1): both read coarse nodes j
+        // (and j+1), the even column only when the row is odd
+        const int np2 = (g.n2 + 1) >> 1;
+        for (int j = lane; j < np2; j += 32) {
+            const bool ho = 2 * j + 1 < g.n2;
+            XT ue, uo;
+            if (ho) {
+                Pair2<XT>::load(rb, j, ue, uo);
+            } else {
+                ue = rb[2 * j];
+                uo = XT(0);
+            }
+            XT ce = XT(0), co = uo;
+            if constexpr (MODE == MODE_DEC) {
+                const TW a0 = c0[j];
+                const TW wl1 = q1 ? tw1[2 * i1] : TW(1), wr1 = q1 ? tw1[2 * i1 + 1] : TW(0);
+                const TW a1 = q1 ? c1[j] : a0;
+                if (rodd) {
+                    ce = static_cast<XT>(static_cast<TW>(ue) - (wl1 * a0 + wr1 * a1));
+                    xrow[2 * j] = ce;
+                }
+                if (ho) {
+                    TW wl2, wr2;
+                    Pair2<TW>::load(tw2, 2 * j + 1, wl2, wr2);
+                    const TW b0 = c0[j + 1], b1 = q1 ? c1[j + 1] : b0;
+                    const TW x0 = wl2 * a0 + wr2 * b0, x1 = wl2 * a1 + wr2 * b1;
+                    co = static_cast<XT>(static_cast<TW>(uo) - (wl1 * x0 + wr1 * x1));
+                    xrow[2 * j + 1] = co;
+                }
+            } else {
+                if (rodd) ce = ue;
+            }
+            if (ho) Pair2<XT>::store(rb, j, ce, co);
+            else rb[2 * j] = ce;
+        }
+        __syncwarp();
+        for (int X = lane; X < g.m2; X += 32) {
+            TW h = tk2[5 * X + 2] * static_cast<TW>(rb[2 * X]);
+            if (X > 0) {
+                XT r0, r1;
+                Pair2<XT>::load(rb, X - 1, r0, r1);
+                h += tk2[5 * X] * static_cast<TW>(r0) + tk2[5 * X + 1] * static_cast<TW>(r1);
+            }
+            if (2 * X + 1 < g.n2) {
+                h += tk2[5 * X + 3] * static_cast<TW>(rb[2 * X + 1]) + tk2[5 * X + 4] * static_cast<TW>(rb[2 * X + 2]);
+            }
+            hrow[X] = h;
+        }
+        __syncwarp();
+        return;
+    }
+    // P = I along dim 2: the row's own nodes, its stencil and solve cancel
     if constexpr (MODE == MODE_DEC) {
         const TW wl1 = q1 ? tw1[2 * i1] : TW(1), wr1 = q1 ? tw1[2 * i1 + 1] : TW(0);
         for (int i2 = lane; i2 < g.n2; i2 += 32) {
-            const int q2 = g.c2 & i2 & 1, x = i2 >> g.c2;
-            if (rodd || q2) {
-                const TW wl2 = q2 ? tw2[2 * i2] : TW(1), wr2 = q2 ? tw2[2 * i2 + 1] : TW(0);
-                const TW x0 = wl2 * c0[x] + wr2 * c0[x + q2];
-                const TW x1 = wl2 * c1[x] + wr2 * c1[x + q2];
-                const XT c = static_cast<XT>(static_cast<TW>(rb[i2]) - (wl1 * x0 + wr1 * x1));
+            if (rodd) {
+                const XT c = static_cast<XT>(static_cast<TW>(rb[i2]) - (wl1 * c0[i2] + wr1 * c1[i2]));
                 xrow[i2] = c;
                 rb[i2] = c;
             } else {
@@ -170,22 +240,10 @@ __device__ __forceinline__ void persist_a_row(const PGeo<TW> &g, XT *xrow, int i
         }
     } else {
         for (int i2 = lane; i2 < g.n2; i2 += 32)
-            if (!(rodd || (g.c2 & i2 & 1))) rb[i2] = XT(0);
+            if (!rodd) rb[i2] = XT(0);
     }
     __syncwarp();
-    if (g.c2) {
-        for (int X = lane; X < g.m2; X += 32) {
-            TW h = TW(0);
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                const int i2 = 2 * X - 2 + c;
-                if (i2 >= 0 && i2 < g.n2) h += tk2[5 * X + c] * static_cast<TW>(rb[i2]);
-            }
-            hrow[X] = h;
-        }
-    } else {  // P = I along dim 2: its stencil and solve cancel
-        for (int X = lane; X < g.m2; X += 32) hrow[X] = static_cast<TW>(rb[X]);
-    }
+    for (int X = lane; X < g.m2; X += 32) hrow[X] = static_cast<TW>(rb[X]);
     __syncwarp();
 }
 
@@ -386,20 +444,24 @@ __device__ void persist_c(const PersistLevel &L, int item, TW *sm)
         if (r < g.n0) cp_async_elem<TW>(ring + (r & (RG - 1)) * PW + lane, xok ? G + r * rs + base : G, xok);
     };
     // rows 0 .. 2 NW: those of the first NW coarse planes (2 per warp, warp 0
-    // also row 2 NW); then per group of NW planes the 2 NW rows after
+    // also row 2 NW), then the next group's 2 NW rows; per group of NW
+    // planes the rows two groups ahead (the ring spans the rows read by the
+    // slowest warp and those copied by the fastest)
     stage_row(2 * warp);
     stage_row(2 * warp + 1);
     if (warp == 0) stage_row(2 * NW);
     cp_async_commit();
+    stage_row(2 * NW + 1 + 2 * warp);
+    stage_row(2 * NW + 2 + 2 * warp);
+    cp_async_commit();
     persist_table<TW>(tf0, g.f0, 3 * g.m0);
     for (int z0 = 0; z0 < g.m0; z0 += NW) {
-        // rows 2 z0 + 2 NW + 1 .. 2 z0 + 4 NW: the next group's (its planes
-        // need rows up to 2 (z0 + 2 NW - 1) + 2)
-        const int nx = 2 * z0 + 2 * NW + 1;
+        // rows 2 z0 + 4 NW + 1 .. 2 z0 + 6 NW: the group after next
+        const int nx = 2 * z0 + 4 * NW + 1;
         stage_row(nx + 2 * warp);
         stage_row(nx + 2 * warp + 1);
         cp_async_commit();
-        cp_async_wait<1>();
+        cp_async_wait<2>();
         __syncthreads();
         const int Z = z0 + warp;
         if (Z < g.m0) {
@@ -607,19 +669,30 @@ __device__ __forceinline__ void persist_d_row(const PGeo<TW> &g, XT *xrow, const
     const int q1 = g.c1 & i1 & 1;
     const bool even_row = !podd && !q1;
     const TW wl1 = q1 ? tw1[2 * i1] : TW(1), wr1 = q1 ? tw1[2 * i1 + 1] : TW(0);
-    for (int i2 = lane; i2 < g.n2; i2 += 32) {
-        const int q2 = g.c2 & i2 & 1, x = i2 >> g.c2;
-        TW r;
-        if (even_row && !q2) {
-            r = c0[x];  // coarse node: V - z
-        } else {
-            const TW wl2 = q2 ? tw2[2 * i2] : TW(1), wr2 = q2 ? tw2[2 * i2 + 1] : TW(0);
-            const TW x0 = wl2 * c0[x] + wr2 * c0[x + q2];
-            const TW x1 = wl2 * c1[x] + wr2 * c1[x + q2];
-            r = static_cast<TW>(rb[i2]) + (wl1 * x0 + wr1 * x1);
+    if (g.c2) {
+        // lane takes the column pairs (2j, 2j+1), as in phase A
+        const int np2 = (g.n2 + 1) >> 1;
+        for (int j = lane; j < np2; j += 32) {
+            const bool ho = 2 * j + 1 < g.n2;
+            XT ue, uo = XT(0);
+            if (ho) Pair2<XT>::load(rb, j, ue, uo);
+            else ue = rb[2 * j];
+            const TW a0 = c0[j], a1 = q1 ? c1[j] : a0;
+            // even column: V - z on a coarse node, else C + the interpolant
+            xrow[2 * j] = static_cast<XT>(even_row ? a0 : static_cast<TW>(ue) + (wl1 * a0 + wr1 * a1));
+            if (ho) {
+                TW wl2, wr2;
+                Pair2<TW>::load(tw2, 2 * j + 1, wl2, wr2);
+                const TW b0 = c0[j + 1], b1 = q1 ? c1[j + 1] : b0;
+                const TW x0 = wl2 * a0 + wr2 * b0, x1 = wl2 * a1 + wr2 * b1;
+                xrow[2 * j + 1] = static_cast<XT>(static_cast<TW>(uo) + (wl1 * x0 + wr1 * x1));
+            }
         }
-        xrow[i2] = static_cast<XT>(r);
+        return;
     }
+    // P = I along dim 2
+    for (int i2 = lane; i2 < g.n2; i2 += 32)
+        xrow[i2] = static_cast<XT>(even_row ? c0[i2] : static_cast<TW>(rb[i2]) + (wl1 * c0[i2] + wr1 * c1[i2]));
 }
 
 template <typename XT, typename TW>
@@ -824,6 +897,8 @@ __global__ void __launch_bounds__(kPersistThreads, sizeof(TW) == 4 ? 2 : 1) k_pe
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
+    __shared__ int2 s_e;
+    __shared__ PersistTask s_t;
     __shared__ unsigned long long s_t1;
     TW *sm = reinterpret_cast<TW *>(smem_raw);
     for (;;) {
@@ -832,12 +907,14 @@ __global__ void __launch_bounds__(kPersistThreads, sizeof(TW) == 4 ? 2 : 1) k_pe
             s_item = it;
             if (it < p.nitems) {
                 const int2 e = p.items[it];
-                const PersistTask &t = p.tasks[e.x];
+                const PersistTask t = p.tasks[e.x];
                 const unsigned long long t0 = p.prof ? persist_clock() : 0ull;
                 for (int d = 0; d < 2; ++d)
                     if (t.dep[d] >= 0) persist_wait(p, p.done + t.dep[d], (unsigned)p.tasks[t.dep[d]].nitems);
                 if (p.stall && it == 0) persist_wait(p, p.zero, 1u);  // a count nothing reaches
                 __threadfence();
+                s_e = e;
+                s_t = t;
                 if (p.prof) {
                     s_t1 = persist_clock();
                     atomicAdd(p.prof + kPersistKinds + t.kind, s_t1 - t0);
@@ -845,10 +922,9 @@ __global__ void __launch_bounds__(kPersistThreads, sizeof(TW) == 4 ? 2 : 1) k_pe
             }
         }
         __syncthreads();
-        const int it = s_item;
-        if (it >= p.nitems) break;
-        const int2 e = p.items[it];
-        const PersistTask t = p.tasks[e.x];
+        if (s_item >= p.nitems) break;
+        const int2 e = s_e;
+        const PersistTask t = s_t;
         switch (t.kind) {
         case PK_A: {
             const PersistLevel &L = p.lv[t.level];

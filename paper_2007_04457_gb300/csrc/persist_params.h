@@ -17,11 +17,12 @@ constexpr int64_t kPersistMaxRow = 1025;
 constexpr int kPersistRing = 32;
 // columns of a phase-C panel: one line per lane
 constexpr int kPersistPanel = 32;
-// coarse rows per item of the final placement (two per warp)
-constexpr int kPersistPlaceRows = 16;
-// rows of G kept per block in phase C (a ring: the rows of the next eight
-// coarse planes are copied while the current ones are reduced)
-constexpr int kPersistGRing = 64;
+// coarse rows per item of the final placement (eight per warp)
+constexpr int kPersistPlaceRows = 64;
+// rows of G kept per block in phase C (a ring: the rows of the coarse
+// planes two groups of eight ahead are copied while the current ones are
+// reduced)
+constexpr int kPersistGRing = 128;
 constexpr int kPersistSpinLimit = 1 << 22;  // dependency polls (tens of ns each)
 // the small tail: arrays of at most this many nodes, finished by one block
 constexpr int64_t kPersistSmallNodes = 1000;
