@@ -281,7 +281,10 @@ MGARD_API mgard_status mgard_recompose_adjoint(const mgard_plan *plan, void *d_d
  *                          per SM of the persistent grid (0 = as many as
  *                          fit; rebuilds the work lists); 4: measurement,
  *                          1 = every block records its busy and waiting
- *                          time per item kind
+ *                          time per item kind; 5: queue order, 0 = fields
+ *                          by decreasing modelled time (a few in flight),
+ *                          1 = the longest modelled path to the end of a
+ *                          field first (rebuilds the work lists)
  *   mgard_batch_profile_read   dir 0 / 1: per item kind (A, B, C, D, small
  *                          tail, placement) the block-milliseconds busy and
  *                          waiting for dependencies, and the items, summed
@@ -293,7 +296,8 @@ MGARD_API mgard_status mgard_recompose_adjoint(const mgard_plan *plan, void *d_d
  *                          5 grid blocks, 6 blocks per SM that fit,
  *                          7 / 8 work items of a decomposition /
  *                          recomposition, 9 / 10 their modelled time (us),
- *                          11 dynamic shared memory bytes; -1 otherwise
+ *                          11 dynamic shared memory bytes, 12 queue
+ *                          order; -1 otherwise
  *   mgard_batch_check      synchronizes `stream`, then MGARD_ERR_TIMEOUT if
  *                          a dependency wait of the persistent kernel ran
  *                          out since the last check (the results of that

@@ -11,7 +11,11 @@ configurations.  This module does the same for the GB300 kernels:
 * ``tune`` ranks the tile configurations by that estimate, keeps the best
   ``top`` (three, as the paper does), times each of them with every solve
   warp count on the real plan, applies the fastest and caches it per
-  (GPU, shape, dtype).
+  (GPU, shape, dtype);
+* ``tune_batch`` does the same for the persistent batch kernel: its
+  launch parameters (blocks per SM, queue order) are ranked by the
+  makespan of the library's list-scheduling model of the launch, and only
+  the ``top`` best are timed.
 """
 from __future__ import annotations
 
@@ -162,3 +166,48 @@ def tune(plan, field=None, top: int = 3, reps: int = 3, cache: bool = True, cach
         store[key] = best
         save_cache(store, cache_path)
     return dict(best, cached=False)
+
+
+BATCH_BLOCKS_PER_SM = (0, 1)        # 0 = as many as fit
+BATCH_ORDERS = (0, 1)               # fields by size / longest remaining path first
+
+
+def tune_batch(batch, fields, workspace, top: int = 2, reps: int = 2) -> dict:
+    """Persistent batch kernel: rank (blocks per SM, queue order) by the
+    modelled makespan of a decompose + recompose, time the ``top`` best on
+    the real fields (decompose + recompose, which leaves them as they were up
+    to rounding) and keep the fastest."""
+    import torch
+
+    if batch.get("eligible") != 1:
+        return {"persistent": False}
+    batch.tune(0, 1)
+    cands = []
+    for bps in BATCH_BLOCKS_PER_SM:
+        for order in BATCH_ORDERS:
+            batch.tune(3, bps)
+            batch.tune(5, order)
+            cands.append((batch.get("model_us_dec") + batch.get("model_us_rec"), bps, order))
+    cands.sort()
+    timed = []
+    stream = torch.cuda.current_stream()
+    for model_us, bps, order in cands[:max(1, top)]:
+        batch.tune(3, bps)
+        batch.tune(5, order)
+        step = lambda: (batch.decompose(fields, workspace), batch.recompose(fields, workspace))
+        step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        timed.append((e0.elapsed_time(e1) / reps, bps, order, model_us))
+    ms, bps, order, model_us = min(timed)
+    batch.tune(3, bps)
+    batch.tune(5, order)
+    return {"persistent": True, "blocks_per_sm": bps, "order": order, "ms": ms, "model_us": model_us,
+            "ranked": [{"model_us": c[0], "blocks_per_sm": c[1], "order": c[2]} for c in cands],
+            "timed": [{"ms": t[0], "blocks_per_sm": t[1], "order": t[2]} for t in timed]}

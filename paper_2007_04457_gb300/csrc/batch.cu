@@ -20,6 +20,7 @@
 // first to the least loaded stream), each field's level kernels on its
 // stream, and the join back; later calls replay the graph.
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -77,6 +78,7 @@ struct Persist {
     size_t smem = 0, ws_bytes = 0;
     int num_sms = 0, occupancy = 0, bps_req = 0, grid = 0;
     int spin = kPersistSpinLimit, stall = 0;
+    int order = 0;                             // queue order: 0 fields by size, 1 longest remaining path
     std::vector<PersistTask> tasks[2];
     std::vector<int2> items[2];
     double model_ns[2] = {0, 0};
@@ -357,10 +359,10 @@ void build_tasks(const Persist &S, int dir, const CostModel &cm, TaskList &T)
 
 // List schedule of the items on `workers` identical workers: whenever a
 // worker is free it takes the next item of the ready task that comes first
-// (fields by decreasing modelled time, then task order).  The items in the
-// order they were taken form the queue; every item comes after all items of
-// the tasks it depends on.  Returns the modelled makespan (ns).
-double list_schedule(const TaskList &T, const std::vector<int> &field_rank, int workers, std::vector<int2> &out)
+// by `prio` (smaller first; ties by task order).  The items in the order
+// they were taken form the queue; every item comes after all items of the
+// tasks it depends on.  Returns the modelled makespan (ns).
+double list_schedule(const TaskList &T, const std::vector<int64_t> &prio, int workers, std::vector<int2> &out)
 {
     const int nt = (int)T.t.size();
     std::vector<int> ndeps(nt, 0), next(nt, 0), done(nt, 0);
@@ -376,7 +378,7 @@ double list_schedule(const TaskList &T, const std::vector<int> &field_rank, int 
     }
     using Key = std::pair<int64_t, int>;
     std::priority_queue<Key, std::vector<Key>, std::greater<Key>> ready;
-    auto key = [&](int i) { return Key((int64_t)field_rank[T.field[i]] * (int64_t)nt + i, i); };
+    auto key = [&](int i) { return Key(prio[i] * (int64_t)nt + i, i); };
     for (int i = 0; i < nt; ++i)
         if (ndeps[i] == 0) ready.push(key(i));
     using Ev = std::pair<double, int>;
@@ -493,8 +495,26 @@ mgard_status persist_build(Persist &S)
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return fc[a] > fc[b]; });
         for (int r = 0; r < nf; ++r) rank[order[r]] = r;
         for (int i = 0; i < nf; ++i) S.f[i].cost = fc[i];
+        // priority: 0 = fields by decreasing modelled time, then task order
+        // (a few fields in flight, their levels kept in L2); 1 = the longest
+        // modelled path from the task to the end of its field first
+        // (a task's span: its items' cost over the grid's width)
+        const int ntk = (int)T.t.size();
+        std::vector<int64_t> prio(ntk);
+        if (S.order == 1) {
+            std::vector<double> bl(ntk, 0.0);
+            for (int i = ntk - 1; i >= 0; --i) {  // dependents come later in the task list
+                const double span = T.cost[i] * std::ceil((double)T.t[i].nitems / S.grid);
+                bl[i] += span;
+                for (int d = 0; d < 2; ++d)
+                    if (T.t[i].dep[d] >= 0) bl[T.t[i].dep[d]] = std::max(bl[T.t[i].dep[d]], bl[i]);
+            }
+            for (int i = 0; i < ntk; ++i) prio[i] = -(int64_t)bl[i];
+        } else {
+            for (int i = 0; i < ntk; ++i) prio[i] = rank[T.field[i]];
+        }
         std::vector<int2> items;
-        S.model_ns[dir] = list_schedule(T, rank, S.grid, items);
+        S.model_ns[dir] = list_schedule(T, prio, S.grid, items);
         if (S.model_ns[dir] < 0 || !order_ok(T, items))
             return mg_fail(MGARD_ERR_INTERNAL, "batch: the work list does not respect the task dependencies");
         S.tasks[dir] = T.t;
@@ -826,6 +846,11 @@ mgard_status mgard_batch_tune(mgard_batch *B, int param, int value)
         S.prof_on = value == 1;
         persist_drop_graphs(S);
         return MGARD_OK;
+    case 5:  // queue order (0: fields by size, 1: longest remaining path first)
+        if (value != 0 && value != 1) return MGARD_ERR_INVALID_ARG;
+        if (!S.eligible) return mg_fail(MGARD_ERR_INVALID_ARG, "batch: " + S.why);
+        S.order = value;
+        return persist_build(S);
     case 3:  // blocks per SM (0: as many as fit)
         if (value < 0 || value > 32) return MGARD_ERR_INVALID_ARG;
         if (!S.eligible) return mg_fail(MGARD_ERR_INVALID_ARG, "batch: " + S.why);
@@ -852,6 +877,7 @@ long long mgard_batch_get(const mgard_batch *B, int param)
     case 9: return (long long)(S.model_ns[0] / 1000.0);
     case 10: return (long long)(S.model_ns[1] / 1000.0);
     case 11: return (long long)S.smem;
+    case 12: return S.order;
     default: return -1;
     }
 }

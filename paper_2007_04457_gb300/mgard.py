@@ -479,7 +479,7 @@ class Batch:
     # mgard_batch_get parameters
     GET = {"persistent": 0, "spin": 1, "stall": 2, "blocks_per_sm_req": 3, "eligible": 4, "grid": 5,
            "occupancy": 6, "items_dec": 7, "items_rec": 8, "model_us_dec": 9, "model_us_rec": 10,
-           "smem": 11}
+           "smem": 11, "order": 12}
 
     def __init__(self, plans, streams: int = 8):
         self.plans = list(plans)
@@ -516,7 +516,9 @@ class Batch:
         """0: 1 = persistent kernel, 0 = graph of per-field launches;
         1: dependency polls before a wait gives up; 2: test hook (1 = the
         first item waits for a count nothing reaches); 3: blocks per SM (0 =
-        as many as fit).  The workspace size does not change."""
+        as many as fit); 4: 1 = record busy / waiting time per item kind;
+        5: queue order (0 = fields by size, 1 = longest remaining path).
+        The workspace size does not change."""
         mgard_batch_tune(self.handle, param, value)
 
     def get(self, name: str) -> int:
