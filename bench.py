@@ -16,6 +16,7 @@ so no flush is needed between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
        python bench.py --case SHAPE DTYPE REPS [NCLASSES] [TUNE]   (profiling case)
+       python bench.py --batch-case REPS                           (profiling case)
 Under torchrun each rank refactors its own field (independent partitions,
 weak scaling, no collective on the data path).
 """
@@ -679,9 +680,35 @@ def run_case(spec):
           + (f" nclasses={nclasses}" if nclasses > 0 else ""))
 
 
+def run_batch_case(spec):
+    """One profiling case of the persistent batch kernel (no timing):
+    --batch-case REPS runs REPS decompose + recompose pairs of a smaller
+    uneven batch (4 x 257^3, 8 x 129^3, 8 x 65^3, 2 x 1025^2 FP32, the
+    batch generator's fields) in one persistent launch per direction."""
+    import torch
+
+    from paper_2007_04457_gb300 import mgard, synth
+
+    reps = int(spec[0]) if spec else 1
+    shapes = [(257, 257, 257)] * 4 + [(129, 129, 129)] * 8 + [(65, 65, 65)] * 8 + [(1025, 1025)] * 2
+    plans = [mgard.Plan(s, dtype="f32") for s in shapes]
+    fields = [synth.sinusoid_field_torch(s, N_MODES if len(s) == 3 else 8, 4 + i, "cuda", torch.float32)
+              for i, s in enumerate(shapes)]
+    batch = mgard.Batch(plans)
+    ws = batch.workspace("cuda")
+    for _ in range(reps):
+        batch.decompose(fields, ws)
+        batch.recompose(fields, ws)
+    torch.cuda.synchronize()
+    print(f"batch case ok: fields={len(shapes)} persistent={batch.get('persistent')} grid={batch.get('grid')} "
+          f"items={batch.get('items_dec') + batch.get('items_rec')} check={batch.check()}")
+
+
 def main():
     if "--case" in sys.argv:
         return run_case(sys.argv[sys.argv.index("--case") + 1:])
+    if "--batch-case" in sys.argv:
+        return run_batch_case(sys.argv[sys.argv.index("--batch-case") + 1:])
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
