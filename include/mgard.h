@@ -188,21 +188,49 @@ MGARD_API mgard_status mgard_recompose_classes(const mgard_plan *plan, int nclas
  *            beyond an array's last element, inside the word that holds it.
  *   param 9  plan-wide: coarse intervals (sweeps) or planes (restriction)
  *            per work item of the row-chunk kernels (0 = automatic).
+ *   param 10 plan-wide: 0 = the slab load-vector kernel on the levels it
+ *            takes (default): 3D levels whose array holds 4-byte elements
+ *            (FP32, and level 0 of the mixed scheme) in rows of 128 k + 1
+ *            nodes, k <= 8.  A block takes a band of coarse rows over whole
+ *            rows and a chunk of coarse planes; each fine plane's rows that
+ *            feed the band, one contiguous range, are staged in shared memory
+ *            by a single bulk asynchronous copy.  It reads whole 16-byte
+ *            words: up to 12 bytes before and after a range, inside the
+ *            words that hold its ends.  1 = the strip / tile / row-chunk
+ *            kernels instead.  The forms differ only in floating-point
+ *            rounding order.
+ *   param 11 plan-wide: coarse planes per slab work item (0 = automatic:
+ *            the count that deals the blocks the most even share of planes).
+ *   param 12 plan-wide: coarse rows per slab band, 4 or 8 (0 = automatic:
+ *            8, or 4 on levels with fewer than 8 coarse rows).
+ *   param 13 plan-wide: ring slots (planes staged at once) of the slab
+ *            kernel, 2 .. 16 (0 = automatic: 4); a count whose shared memory
+ *            does not fit leaves the affected levels to the other kernels.
+ *   param 14 plan-wide test hook: v > 0 announces each slab block's first
+ *            copy with 16 bytes more than it moves, so its wait runs out
+ *            after v microseconds (the block records it and returns; the
+ *            results are not valid and mgard_plan_check reports
+ *            MGARD_ERR_TIMEOUT); 0 = off, with the normal limit of 2 s per
+ *            wait.
  *   mgard_plan_get_tune also reports param 5: the first level the
- *   cooperative kernel runs (-1: none), and param 8: the row-chunk
+ *   cooperative kernel runs (-1: none), param 8: the row-chunk
  *   restriction's segment width of the level (512 or 256 columns; 0: not a
- *   row-chunk level).
+ *   row-chunk level), and for params 11 .. 13 the level's values (0: not a
+ *   slab level).
  * Returns MGARD_ERR_INVALID_ARG for an unknown parameter or value. */
 MGARD_API mgard_status mgard_plan_tune(mgard_plan *plan, int level, int param, int value);
 
 /* Current value of a tuning parameter of level j (-1 on error). */
 MGARD_API int mgard_plan_get_tune(const mgard_plan *plan, int level, int param);
 
-/* Status of the last cooperative launch that used workspace d_ws (the
- * plan's layout): synchronizes `stream`, then returns MGARD_ERR_TIMEOUT if a
- * grid-barrier wait of that launch ran out (its results are not valid),
- * else MGARD_OK (also when the plan has no cooperative kernel).  No paper
- * counterpart: a safeguard of this implementation's bounded waits. */
+/* Status of the bounded waits of the plan's last calls: synchronizes
+ * `stream`, then returns MGARD_ERR_TIMEOUT if a wait for a bulk copy of the
+ * slab load-vector kernel ran out since the last check (the plan's sticky
+ * status word, cleared by this call), or if a grid-barrier wait of the last
+ * cooperative launch that used workspace d_ws (the plan's layout) ran out;
+ * the results of such a call are not valid.  Else MGARD_OK (also when the
+ * plan runs neither kernel).  No paper counterpart: a safeguard of this
+ * implementation's bounded waits. */
 MGARD_API mgard_status mgard_plan_check(const mgard_plan *plan, const void *d_ws, void *stream);
 
 /* End-to-end forms with host buffers: copy h_in (host, prod(dims) elements,

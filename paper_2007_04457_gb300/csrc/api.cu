@@ -74,6 +74,9 @@ struct mgard_level {
     int rc_grid[2] = {0, 0};     // blocks: sweep, restriction
     int rc_zc[2] = {0, 0};       // coarse intervals (sweep) / planes (restriction) per chunk
     int rc_nzc[2] = {0, 0};      // chunk counts
+    // slab load-vector kernel (slab.cuh): used when slab_ty > 0
+    int slab_ty = 0, slab_ns = 0, slab_sb = 0;  // coarse rows per band, ring slots, slot bytes
+    int slab_nb = 0, slab_zc = 0, slab_nzc = 0, slab_grid = 0;
 };
 
 struct mgard_plan {
@@ -114,6 +117,11 @@ struct mgard_plan {
     int coop_spin = 0;                // barrier poll limit (0: default)
     int rc_off = kRcDefaultOff;       // tune: row-chunk kernels kept out (bit 0 sweeps, bit 1 restriction)
     int rc_zreq = 0;                  // tune: coarse intervals / planes per row-chunk item (0: automatic)
+    bool slab_off = false;            // tune: the slab load-vector kernel kept out
+    int slab_zreq = 0, slab_tyreq = 0, slab_nsreq = 0;  // tune: its planes per chunk, rows per band, slots (0: automatic)
+    int slab_hook = 0;                // tune: test hook (each block's first copy wait runs out)
+    unsigned long long slab_wait_ns = 2000000000ull;  // limit of one copy wait
+    unsigned *d_status = nullptr;     // device status word of the slab kernel (owned)
     int coop_grid = 0;
     size_t coop_smem = 0;
     int coop_hcap = 0;
@@ -364,10 +372,41 @@ bool rc_on(const mgard_plan *P, int j, const void *A, int kind)
     return P->lv[j].rc_q[0] > 0 && !(P->rc_off & (1 << kind)) && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
 }
 
+// The slab load-vector kernel for level j (configured: a 3D FP32 level array
+// with rows of 128 k + 1 nodes, not switched off).
+bool slab_on(const mgard_plan *P, int j) { return P->lv[j].slab_ty > 0; }
+
 // Leading dims whose solve the level's load-vector kernel already did.
 int solved_first(const mgard_plan *P, int j, const void *A)
 {
+    if (slab_on(P, j)) return 0;
     return (rc_on(P, j, A, 1) && P->lv[j].rc_xs) ? 1 : 0;
+}
+
+// Load vector and coarse gather of level j by the slab kernel.
+template <typename TW>
+cudaError_t run_slab(const mgard_plan *P, int j, int mode, const void *A, char *ws, cudaStream_t st)
+{
+    const mgard_level &L = P->lv[j];
+    SlabParams p;
+    p.A = A;
+    p.F = ws + L.f_off;
+    p.V = ws + L.v_off;
+    p.n0 = (int)L.n[0]; p.n1 = (int)L.n[1]; p.n2 = (int)L.n[2];
+    p.m0 = (int)L.m[0]; p.m1 = (int)L.m[1]; p.m2 = (int)L.m[2];
+    p.k0 = tab_ptr<float>(P, L.k_off[0]); p.k1 = tab_ptr<float>(P, L.k_off[1]); p.k2 = tab_ptr<float>(P, L.k_off[2]);
+    p.nb = L.slab_nb;
+    p.zchunk = L.slab_zc;
+    p.nzc = L.slab_nzc;
+    p.nitems = L.slab_nb * L.slab_nzc;
+    p.ns = L.slab_ns;
+    p.slot_bytes = L.slab_sb;
+    p.kuni1 = L.kuni32[1];
+    p.hook = P->slab_hook;
+    p.status = P->d_status;
+    p.wait_ns = P->slab_wait_ns;
+    return timed(P, mode == MODE_DEC ? KIND_RESTRICT_DEC : KIND_RESTRICT_REC, j, st,
+                 [&] { return launch_slab<TW>(L.slab_ty, p, L.slab_grid, st); });
 }
 
 template <typename T, typename TW>
@@ -511,7 +550,9 @@ mgard_status exec_decompose(const mgard_plan *P, void *data, char *ws, cudaStrea
         else
             err = (j == 0) ? run_coef_level<TU, TW>(P, j, A, ws, st) : run_coef_level<TW, TW>(P, j, A, ws, st);
         if (err != cudaSuccess) return cuda_fail(err, "decompose: coefficient kernel");
-        if (rc_on(P, j, A, 1))
+        if (slab_on(P, j))
+            err = run_slab<TW>(P, j, MODE_DEC, A, ws, st);
+        else if (rc_on(P, j, A, 1))
             err = (j == 0) ? run_rc_restrict<TU, TW>(P, j, MODE_DEC, A, ws, st)
                            : run_rc_restrict<TW, TW>(P, j, MODE_DEC, A, ws, st);
         else
@@ -550,7 +591,9 @@ mgard_status exec_recompose(const mgard_plan *P, void *data, char *ws, cudaStrea
     const int J = coop ? P->coop_j : std::max(P->small_j, D);
     for (int j = D; j < J; ++j) {
         void *A = (j == 0) ? data : (void *)(ws + P->lv[j - 1].v_off);
-        if (rc_on(P, j, A, 1))
+        if (slab_on(P, j))
+            err = run_slab<TW>(P, j, MODE_REC, A, ws, st);
+        else if (rc_on(P, j, A, 1))
             err = (j == 0) ? run_rc_restrict<TU, TW>(P, j, MODE_REC, A, ws, st)
                            : run_rc_restrict<TW, TW>(P, j, MODE_REC, A, ws, st);
         else
@@ -896,6 +939,76 @@ cudaError_t configure_rc(mgard_plan *P, mgard_level &L, bool finest)
     return cudaSuccess;
 }
 
+// Slab load-vector configuration of a 3D level whose array holds 4-byte
+// elements and whose rows have n2 = 128 k + 1 nodes (k <= 8): coarse rows per
+// band and ring slots (bands of 8 rows and 4 slots where they fit, or as
+// tuned), and the chunk of coarse planes that gives the blocks the
+// most even share of fine planes to stream (each item streams its chunk's
+// planes plus 3 of its neighbours'), the items dealt to the blocks in turn.
+// Leaves slab_ty = 0 (the other kernels) otherwise.
+template <typename TW>
+cudaError_t configure_slab(mgard_plan *P, mgard_level &L, bool finest)
+{
+    L.slab_ty = 0;
+    const int es = (int)(finest ? P->elem_user : P->elem_ws);
+    if (P->slab_off || P->per_dim || P->act != ACT_3D || es != 4) return cudaSuccess;
+    const int64_t n2 = L.n[2], m0 = L.m[0], m1 = L.m[1];
+    if ((n2 - 1) % 64 != 0 || (n2 - 1) / 2 > kSlabMaxThreads || m0 < 2) return cudaSuccess;
+    // (rows per band, ring slots) in order of preference, as tuned: the first
+    // whose shared memory fits a block
+    int ty = 0, ns = 0, bps = 0;
+    static const int pref[6][2] = {{8, 2}, {4, 3}, {4, 2}, {8, 3}, {8, 4}, {4, 4}};
+    for (const auto &c : pref) {
+        const int cty = P->slab_tyreq > 0 ? P->slab_tyreq : c[0];
+        const int cns = P->slab_nsreq > 0 ? P->slab_nsreq : c[1];
+        if (m1 < cty) continue;
+        int b = 0;
+        if (slab_occupancy<TW>(cty, (int)n2, cns, &b) != cudaSuccess || b < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        ty = cty;
+        ns = cns;
+        bps = b;
+        break;
+    }
+    if (ty == 0) return cudaSuccess;  // not available here: the other kernels
+    const int64_t nb = (m1 + ty - 1) / ty;
+    const int64_t slots = (int64_t)bps * P->num_sms;
+    auto planes = [&](int64_t zc, int64_t nzc, int64_t c) -> int64_t {
+        const int64_t Zs = c * zc, Ze = (c == nzc - 1) ? m0 : Zs + zc;
+        const int64_t zlo = Zs > 0 ? 2 * Zs - 2 : 0, zhi = 2 * std::min(Ze, m0 - 1);
+        return zhi - zlo + 1;
+    };
+    int64_t best_zc = 0, best_cost = -1;
+    const int64_t zmax = std::max<int64_t>(1, m0 - 1);
+    for (int64_t zc = (P->slab_zreq > 0 ? std::min<int64_t>(P->slab_zreq, zmax) : 2);
+         zc <= (P->slab_zreq > 0 ? std::min<int64_t>(P->slab_zreq, zmax) : std::min<int64_t>(32, zmax)); ++zc) {
+        const int64_t nzc = (m0 - 1 + zc - 1) / zc;
+        const int64_t items = nb * std::max<int64_t>(1, nzc);
+        const int64_t grid = std::min(items, slots);
+        std::vector<int64_t> load(grid, 0);
+        for (int64_t i = 0; i < items; ++i) load[i % grid] += planes(zc, std::max<int64_t>(1, nzc), i / nb);
+        const int64_t cost = *std::max_element(load.begin(), load.end());
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best_zc = zc;
+        }
+    }
+    if (best_zc <= 0) return cudaSuccess;
+    const int64_t nzc = std::max<int64_t>(1, (m0 - 1 + best_zc - 1) / best_zc);
+    const int64_t items = nb * nzc;
+    if (items >= (int64_t(1) << 31)) return cudaSuccess;
+    L.slab_ty = ty;
+    L.slab_ns = ns;
+    L.slab_sb = slab_slot_bytes_of(ty, (int)n2);
+    L.slab_nb = (int)nb;
+    L.slab_zc = (int)best_zc;
+    L.slab_nzc = (int)nzc;
+    L.slab_grid = (int)std::min(items, slots);
+    return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1221,8 +1334,20 @@ static cudaError_t configure_plan(mgard_plan *P)
         case MGARD_F64: err = configure_rc<double, double>(P, lv, j == 0); break;
         default: err = configure_rc<float, double>(P, lv, j == 0); break;
         }
+        if (err == cudaSuccess) err = (P->dtype == MGARD_F32) ? configure_slab<float>(P, lv, j == 0)
+                                                              : configure_slab<double>(P, lv, j == 0);
     }
     if (err == cudaSuccess) err = configure_coop(P);
+    return err;
+}
+
+// Slab configuration of every level again (after a tuning change).
+static cudaError_t configure_plan_slab(mgard_plan *P)
+{
+    cudaError_t err = cudaSuccess;
+    for (int j = 0; j < P->L && err == cudaSuccess; ++j)
+        err = (P->dtype == MGARD_F32) ? configure_slab<float>(P, P->lv[j], j == 0)
+                                      : configure_slab<double>(P, P->lv[j], j == 0);
     return err;
 }
 
@@ -1275,6 +1400,8 @@ mgard_status mg_plan_in_place(int ndim, const int64_t *dims, int nlevels, mgard_
     cudaError_t err = cudaMemcpyAsync(P->tab64, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, stream);
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(P->tab32, tab32.data(), tab32.size() * sizeof(float), cudaMemcpyHostToDevice, stream);
+    // not the slab kernel: its copy-wait status word would need an allocation
+    P->slab_off = true;
     if (err == cudaSuccess) err = configure_plan(P);
     if (err != cudaSuccess) {
         delete P;
@@ -1341,6 +1468,8 @@ static mgard_status plan_create(int ndim, const int64_t *dims, int nlevels, cons
     if (err == cudaSuccess) err = cudaMalloc(&P->tab32, tab32.size() * sizeof(float));
     if (err == cudaSuccess) err = cudaMemcpy(P->tab64, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(P->tab32, tab32.data(), tab32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMalloc(&P->d_status, sizeof(unsigned));
+    if (err == cudaSuccess) err = cudaMemset(P->d_status, 0, sizeof(unsigned));
     if (err == cudaSuccess && !P->per_dim) err = configure_plan(P);
     if (err != cudaSuccess) {
         mgard_plan_destroy(P);
@@ -1385,6 +1514,7 @@ mgard_status mgard_plan_destroy(mgard_plan *P)
         if (P->tab64) cudaFree(P->tab64);
         if (P->tab32) cudaFree(P->tab32);
     }
+    if (P->d_status) cudaFree(P->d_status);
     for (auto &r : P->prof_pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -1631,6 +1761,33 @@ mgard_status mgard_plan_tune(mgard_plan *P, int level, int param, int value)
         if (e2 != cudaSuccess) return cuda_fail(e2, "plan_tune: row-chunk configuration");
         return MGARD_OK;
     }
+    case 10:
+    case 11:
+    case 12:
+    case 13: {
+        if (param == 10) {
+            if (value != 0 && value != 1) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: slab switch");
+            P->slab_off = value != 0;
+        } else if (param == 11) {
+            if (value < 0) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: slab planes per chunk");
+            P->slab_zreq = value;
+        } else if (param == 12) {
+            if (value != 0 && value != 4 && value != 8) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: slab band rows");
+            P->slab_tyreq = value;
+        } else {
+            if (value != 0 && (value < 2 || value > kSlabMaxSlots))
+                return fail(MGARD_ERR_INVALID_ARG, "plan_tune: slab ring slots");
+            P->slab_nsreq = value;
+        }
+        cudaError_t e2 = configure_plan_slab(P);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "plan_tune: slab configuration");
+        return MGARD_OK;
+    }
+    case 14:
+        if (value < 0) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: slab wait hook");
+        P->slab_hook = value > 0 ? 1 : 0;
+        P->slab_wait_ns = value > 0 ? (unsigned long long)value * 1000ull : 2000000000ull;
+        return MGARD_OK;
     case 4:
         if (value != 0 && value != 1) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: cooperative switch");
         P->coop_off = value != 0;
@@ -1662,6 +1819,11 @@ int mgard_plan_get_tune(const mgard_plan *P, int level, int param)
     case 7: return P->rc_off;
     case 9: return P->rc_zreq;
     case 8: return L.rc_q[1] > 0 ? 32 * (16 / (int)(level == 0 ? P->elem_user : P->elem_ws)) * L.rc_q[1] : 0;
+    case 10: return P->slab_off ? 1 : 0;
+    case 11: return L.slab_ty > 0 ? L.slab_zc : 0;
+    case 12: return L.slab_ty;
+    case 13: return L.slab_ty > 0 ? L.slab_ns : 0;
+    case 14: return P->slab_hook ? (int)(P->slab_wait_ns / 1000ull) : 0;
     default: return -1;
     }
 }
@@ -1669,11 +1831,23 @@ int mgard_plan_get_tune(const mgard_plan *P, int level, int param)
 mgard_status mgard_plan_check(const mgard_plan *P, const void *d_ws, void *stream)
 {
     if (!P) return fail(MGARD_ERR_INVALID_ARG, "plan_check: plan is NULL");
-    if (P->coop_auto >= P->L) return MGARD_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the slab kernel's sticky copy-wait word (read and cleared)
+    if (P->d_status) {
+        unsigned sw = 0;
+        cudaError_t err = cudaMemcpyAsync(&sw, P->d_status, sizeof(sw), cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+        if (err == cudaSuccess && sw != 0) err = cudaMemsetAsync(P->d_status, 0, sizeof(unsigned), st);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+        if (err != cudaSuccess) return cuda_fail(err, "plan_check");
+        if (sw != 0) return fail(MGARD_ERR_TIMEOUT, "a copy wait of the slab load-vector kernel ran out");
+    }
+    // the grid-barrier word, when the plan runs the cooperative kernel (its
+    // launch clears the word; otherwise the workspace holds anything)
+    if (P->coop_j >= P->L) return MGARD_OK;
     if (!d_ws) return fail(MGARD_ERR_INVALID_ARG, "plan_check: d_ws is NULL");
     unsigned word = 0;
     const char *src = static_cast<const char *>(d_ws) + P->coop_bar_off + 2 * sizeof(unsigned);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t err = cudaMemcpyAsync(&word, src, sizeof(word), cudaMemcpyDeviceToHost, st);
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
     if (err != cudaSuccess) return cuda_fail(err, "plan_check");

@@ -110,4 +110,25 @@ struct RcParams {
     const void *fx;            // LU factors of M_{l-1} along dim 2, 3 per coarse node (type TW)
 };
 
+// Load vector and coarse gather of a 3D level from whole-row slabs staged in
+// shared memory by bulk asynchronous copies (slab.cuh): 4-byte level arrays
+// with rows of n2 = 128 k + 1 nodes, one block of (n2 - 1) / 4 threads per
+// band of coarse rows x chunk of coarse planes.
+struct SlabParams {
+    const void *A;             // level array (float), n0 x n1 x n2
+    void *F;                   // load vector on N_{l-1} (type TW)
+    void *V;                   // values of A at N_{l-1} (type TW)
+    int n0, n1, n2, m0, m1, m2;
+    const void *k0, *k1, *k2;  // K = P^T M_l rows, 5 per coarse node (float)
+    int nb;                    // bands of TY coarse rows (the last shifted back)
+    int zchunk, nzc;           // coarse planes per chunk, chunk count
+    int nitems;                // nb * nzc
+    int ns;                    // ring slots (planes staged at once)
+    int slot_bytes;            // bytes per slot, a 16-byte multiple
+    int kuni1;                 // 1: the interior rows of k1 are all equal
+    int hook;                  // test hook: each block's first copy wait runs out
+    unsigned *status;          // sticky status word: bit 0 = a copy wait ran out
+    unsigned long long wait_ns;  // limit of one copy wait
+};
+
 }  // namespace mg

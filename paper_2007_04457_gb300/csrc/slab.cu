@@ -1,0 +1,64 @@
+// Launchers of the slab load-vector kernel (slab.cuh), for FP32 level arrays
+// with FP32 (plain) or FP64 (mixed precision) coarse arrays.
+#include "launch.cuh"
+#include "slab.cuh"
+
+namespace mg {
+
+namespace {
+
+template <typename TW>
+void (*slab_fn(int ty))(SlabParams)
+{
+    if (ty == 4) return k_slab<TW, 4>;
+    if (ty == 8) return k_slab<TW, 8>;
+    return nullptr;
+}
+
+}  // namespace
+
+int slab_slot_bytes_of(int ty, int n2)
+{
+    if (ty == 4) return slab_slot_bytes<4>(n2);
+    if (ty == 8) return slab_slot_bytes<8>(n2);
+    return 0;
+}
+
+size_t slab_smem_bytes(int ty, int n2, int ns)
+{
+    return (size_t)kSlabBarBytes + (size_t)ns * (size_t)slab_slot_bytes_of(ty, n2);
+}
+
+template <typename TW>
+cudaError_t slab_occupancy(int ty, int n2, int ns, int *blocks_per_sm)
+{
+    auto fn = slab_fn<TW>(ty);
+    if (!fn || ns < 2 || ns > kSlabMaxSlots || (n2 - 1) % 64 != 0 || (n2 - 1) / 2 > kSlabMaxThreads)
+        return cudaErrorInvalidValue;
+    const size_t smem = slab_smem_bytes(ty, n2, ns);
+    cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, (n2 - 1) / 2, smem);
+}
+
+template <typename TW>
+cudaError_t launch_slab(int ty, const SlabParams &p, int grid, cudaStream_t st)
+{
+    auto fn = slab_fn<TW>(ty);
+    if (!fn || p.nitems <= 0 || grid <= 0 || p.slot_bytes != slab_slot_bytes_of(ty, p.n2)) return cudaErrorInvalidValue;
+    const size_t smem = slab_smem_bytes(ty, p.n2, p.ns);
+    // the limit is per function: plans with other shapes may have lowered it
+    cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    fn<<<grid, (p.n2 - 1) / 2, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+template cudaError_t slab_occupancy<float>(int, int, int, int *);
+template cudaError_t slab_occupancy<double>(int, int, int, int *);
+template cudaError_t launch_slab<float>(int, const SlabParams &, int, cudaStream_t);
+template cudaError_t launch_slab<double>(int, const SlabParams &, int, cudaStream_t);
+
+}  // namespace mg
