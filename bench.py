@@ -131,9 +131,9 @@ def measured_peak():
 # there cannot alter the code, launch or memory traffic of a kernel defined
 # elsewhere.  Keys: the kernel names recorded in profiles/traffic.txt.
 _OWN_HEADER = {"coefficient sweep": "rowchunk.cuh", "interpolation sweep": "rowchunk.cuh",
-               "restriction": "restrict_strip.cuh", "prolong": "prolong.cuh"}
+               "restriction": "slab.cuh", "prolong": "prolong.cuh"}
 _DEVICE_ONLY_HEADERS = ("adjoint.cuh", "multi.cuh", "prolong.cuh", "restrict.cuh", "restrict_strip.cuh",
-                        "rowchunk.cuh", "small.cuh", "solve.cuh", "sweep.cuh")
+                        "rowchunk.cuh", "slab.cuh", "small.cuh", "solve.cuh", "sweep.cuh")
 
 
 def kernel_source_hash(kernel=None):
@@ -805,7 +805,8 @@ def main():
         per_launch_ms = g["ms"] / g["launches"]
         kb = g["bytes"] / g["launches"]
         achieved = kb / (per_launch_ms / 1e3) / 1e9
-        fn = {"restriction": "k_restrict_strip" if plan_tune_get(mgard, plan, 7) & 2 else "k_rc_restrict",
+        fn = {"restriction": ("k_slab" if mgard.mgard_plan_get_tune(plan.handle, 0, 12) > 0 else
+                              "k_restrict_strip" if plan_tune_get(mgard, plan, 7) & 2 else "k_rc_restrict"),
               "coefficient sweep": "k_rc_sweep<MODE_DEC>", "interpolation sweep": "k_rc_sweep<MODE_REC>",
               "solve x/y": "k_solve_chunks", "solve z + correction": "k_solve_lines",
               "coarse placement": "k_scatter"}.get(name, name)

@@ -190,8 +190,8 @@ MGARD_API mgard_status mgard_recompose_classes(const mgard_plan *plan, int nclas
  *            per work item of the row-chunk kernels (0 = automatic).
  *   param 10 plan-wide: 0 = the slab load-vector kernel on the levels it
  *            takes (default): 3D levels whose array holds 4-byte elements
- *            (FP32, and level 0 of the mixed scheme) in rows of 128 k + 1
- *            nodes, k <= 8.  A block takes a band of coarse rows over whole
+ *            (FP32, and level 0 of the mixed scheme) in rows of 64 k + 1
+ *            nodes, k <= 16.  A block takes a band of coarse rows over whole
  *            rows and a chunk of coarse planes; each fine plane's rows that
  *            feed the band, one contiguous range, are staged in shared memory
  *            by a single bulk asynchronous copy.  It reads whole 16-byte
@@ -199,13 +199,16 @@ MGARD_API mgard_status mgard_recompose_classes(const mgard_plan *plan, int nclas
  *            words that hold its ends.  1 = the strip / tile / row-chunk
  *            kernels instead.  The forms differ only in floating-point
  *            rounding order.
- *   param 11 plan-wide: coarse planes per slab work item (0 = automatic:
- *            the count that deals the blocks the most even share of planes).
- *   param 12 plan-wide: coarse rows per slab band, 4 or 8 (0 = automatic:
- *            8, or 4 on levels with fewer than 8 coarse rows).
+ *   param 11 coarse planes per slab work item of the level (0 = automatic:
+ *            the largest count that still gives every resident block two
+ *            items).
+ *   param 12 plan-wide: coarse rows per slab band, 4, 6 or 8 (0 = automatic:
+ *            6, or fewer on levels with fewer coarse rows).
  *   param 13 plan-wide: ring slots (planes staged at once) of the slab
- *            kernel, 2 .. 16 (0 = automatic: 4); a count whose shared memory
+ *            kernel, 2 .. 16 (0 = automatic: 2); a count whose shared memory
  *            does not fit leaves the affected levels to the other kernels.
+ *   param 15 plan-wide: the slab kernel's register budget, for 2 or 3
+ *            blocks per SM (0 = automatic: 3 where they fit).
  *   param 14 plan-wide test hook: v > 0 announces each slab block's first
  *            copy with 16 bytes more than it moves, so its wait runs out
  *            after v microseconds (the block records it and returns; the
@@ -215,8 +218,8 @@ MGARD_API mgard_status mgard_recompose_classes(const mgard_plan *plan, int nclas
  *   mgard_plan_get_tune also reports param 5: the first level the
  *   cooperative kernel runs (-1: none), param 8: the row-chunk
  *   restriction's segment width of the level (512 or 256 columns; 0: not a
- *   row-chunk level), and for params 11 .. 13 the level's values (0: not a
- *   slab level).
+ *   row-chunk level), and for params 11 .. 13 and 15 the level's values
+ *   (0: not a slab level).
  * Returns MGARD_ERR_INVALID_ARG for an unknown parameter or value. */
 MGARD_API mgard_status mgard_plan_tune(mgard_plan *plan, int level, int param, int value);
 

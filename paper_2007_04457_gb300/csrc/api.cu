@@ -76,6 +76,8 @@ struct mgard_level {
     int rc_nzc[2] = {0, 0};      // chunk counts
     // slab load-vector kernel (slab.cuh): used when slab_ty > 0
     int slab_ty = 0, slab_ns = 0, slab_sb = 0;  // coarse rows per band, ring slots, slot bytes
+    int slab_mb = 0;                            // register variant: blocks per SM (2 or 3)
+    int slab_zreq = 0;                          // tune: coarse planes per chunk (0: automatic)
     int slab_nb = 0, slab_zc = 0, slab_nzc = 0, slab_grid = 0;
 };
 
@@ -118,7 +120,8 @@ struct mgard_plan {
     int rc_off = kRcDefaultOff;       // tune: row-chunk kernels kept out (bit 0 sweeps, bit 1 restriction)
     int rc_zreq = 0;                  // tune: coarse intervals / planes per row-chunk item (0: automatic)
     bool slab_off = false;            // tune: the slab load-vector kernel kept out
-    int slab_zreq = 0, slab_tyreq = 0, slab_nsreq = 0;  // tune: its planes per chunk, rows per band, slots (0: automatic)
+    int slab_tyreq = 0, slab_nsreq = 0;  // tune: its rows per band, ring slots (0: automatic)
+    int slab_mbreq = 0;               // tune: its register variant, blocks per SM 2 or 3 (0: automatic)
     int slab_hook = 0;                // tune: test hook (each block's first copy wait runs out)
     unsigned long long slab_wait_ns = 2000000000ull;  // limit of one copy wait
     unsigned *d_status = nullptr;     // device status word of the slab kernel (owned)
@@ -406,7 +409,7 @@ cudaError_t run_slab(const mgard_plan *P, int j, int mode, const void *A, char *
     p.status = P->d_status;
     p.wait_ns = P->slab_wait_ns;
     return timed(P, mode == MODE_DEC ? KIND_RESTRICT_DEC : KIND_RESTRICT_REC, j, st,
-                 [&] { return launch_slab<TW>(L.slab_ty, p, L.slab_grid, st); });
+                 [&] { return launch_slab<TW>(L.slab_ty, L.slab_mb, p, L.slab_grid, st); });
 }
 
 template <typename T, typename TW>
@@ -940,11 +943,9 @@ cudaError_t configure_rc(mgard_plan *P, mgard_level &L, bool finest)
 }
 
 // Slab load-vector configuration of a 3D level whose array holds 4-byte
-// elements and whose rows have n2 = 128 k + 1 nodes (k <= 8): coarse rows per
-// band and ring slots (bands of 8 rows and 4 slots where they fit, or as
-// tuned), and the chunk of coarse planes that gives the blocks the
-// most even share of fine planes to stream (each item streams its chunk's
-// planes plus 3 of its neighbours'), the items dealt to the blocks in turn.
+// elements and whose rows have n2 = 64 k + 1 nodes (k <= 16): coarse rows per
+// band, ring slots and register variant (bands of 6 rows, 2 slots and three
+// blocks per SM where they fit, or as tuned), and the coarse planes per chunk.
 // Leaves slab_ty = 0 (the other kernels) otherwise.
 template <typename TW>
 cudaError_t configure_slab(mgard_plan *P, mgard_level &L, bool finest)
@@ -956,44 +957,38 @@ cudaError_t configure_slab(mgard_plan *P, mgard_level &L, bool finest)
     if ((n2 - 1) % 64 != 0 || (n2 - 1) / 2 > kSlabMaxThreads || m0 < 2) return cudaSuccess;
     // (rows per band, ring slots) in order of preference, as tuned: the first
     // whose shared memory fits a block
-    int ty = 0, ns = 0, bps = 0;
-    static const int pref[6][2] = {{8, 2}, {4, 3}, {4, 2}, {8, 3}, {8, 4}, {4, 4}};
+    int ty = 0, ns = 0, bps = 0, minb = 0;
+    static const int pref[7][3] = {{6, 2, 3}, {8, 2, 2}, {4, 2, 3}, {4, 3, 3}, {8, 3, 2}, {8, 4, 2}, {4, 4, 2}};
     for (const auto &c : pref) {
         const int cty = P->slab_tyreq > 0 ? P->slab_tyreq : c[0];
         const int cns = P->slab_nsreq > 0 ? P->slab_nsreq : c[1];
+        const int cmb = P->slab_mbreq > 0 ? P->slab_mbreq : c[2];
         if (m1 < cty) continue;
         int b = 0;
-        if (slab_occupancy<TW>(cty, (int)n2, cns, &b) != cudaSuccess || b < 1) {
+        if (slab_occupancy<TW>(cty, (int)n2, cns, cmb, &b) != cudaSuccess || b < 1) {
             cudaGetLastError();
             continue;
         }
         ty = cty;
         ns = cns;
+        minb = cmb;
         bps = b;
         break;
     }
     if (ty == 0) return cudaSuccess;  // not available here: the other kernels
     const int64_t nb = (m1 + ty - 1) / ty;
     const int64_t slots = (int64_t)bps * P->num_sms;
-    auto planes = [&](int64_t zc, int64_t nzc, int64_t c) -> int64_t {
-        const int64_t Zs = c * zc, Ze = (c == nzc - 1) ? m0 : Zs + zc;
-        const int64_t zlo = Zs > 0 ? 2 * Zs - 2 : 0, zhi = 2 * std::min(Ze, m0 - 1);
-        return zhi - zlo + 1;
-    };
-    int64_t best_zc = 0, best_cost = -1;
+    // about two items per resident block (blocks that finish early leave the
+    // memory system to the others, so enough items matter more than even
+    // shares; each chunk also streams 3 of its neighbours' planes), at least
+    // 2 coarse planes per chunk
     const int64_t zmax = std::max<int64_t>(1, m0 - 1);
-    for (int64_t zc = (P->slab_zreq > 0 ? std::min<int64_t>(P->slab_zreq, zmax) : 2);
-         zc <= (P->slab_zreq > 0 ? std::min<int64_t>(P->slab_zreq, zmax) : std::min<int64_t>(32, zmax)); ++zc) {
-        const int64_t nzc = (m0 - 1 + zc - 1) / zc;
-        const int64_t items = nb * std::max<int64_t>(1, nzc);
-        const int64_t grid = std::min(items, slots);
-        std::vector<int64_t> load(grid, 0);
-        for (int64_t i = 0; i < items; ++i) load[i % grid] += planes(zc, std::max<int64_t>(1, nzc), i / nb);
-        const int64_t cost = *std::max_element(load.begin(), load.end());
-        if (best_cost < 0 || cost < best_cost) {
-            best_cost = cost;
-            best_zc = zc;
-        }
+    int64_t best_zc = 0;
+    if (L.slab_zreq > 0) {
+        best_zc = std::min<int64_t>(L.slab_zreq, zmax);
+    } else {
+        const int64_t want = std::max<int64_t>(1, (2 * slots + nb - 1) / nb);  // chunks
+        best_zc = std::max<int64_t>(std::min<int64_t>(2, zmax), (zmax + want - 1) / want);
     }
     if (best_zc <= 0) return cudaSuccess;
     const int64_t nzc = std::max<int64_t>(1, (m0 - 1 + best_zc - 1) / best_zc);
@@ -1001,6 +996,7 @@ cudaError_t configure_slab(mgard_plan *P, mgard_level &L, bool finest)
     if (items >= (int64_t(1) << 31)) return cudaSuccess;
     L.slab_ty = ty;
     L.slab_ns = ns;
+    L.slab_mb = minb;
     L.slab_sb = slab_slot_bytes_of(ty, (int)n2);
     L.slab_nb = (int)nb;
     L.slab_zc = (int)best_zc;
@@ -1764,16 +1760,21 @@ mgard_status mgard_plan_tune(mgard_plan *P, int level, int param, int value)
     case 10:
     case 11:
     case 12:
-    case 13: {
+    case 13:
+    case 15: {
         if (param == 10) {
             if (value != 0 && value != 1) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: slab switch");
             P->slab_off = value != 0;
         } else if (param == 11) {
             if (value < 0) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: slab planes per chunk");
-            P->slab_zreq = value;
+            L.slab_zreq = value;
         } else if (param == 12) {
-            if (value != 0 && value != 4 && value != 8) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: slab band rows");
+            if (value != 0 && value != 4 && value != 6 && value != 8)
+                return fail(MGARD_ERR_INVALID_ARG, "plan_tune: slab band rows");
             P->slab_tyreq = value;
+        } else if (param == 15) {
+            if (value != 0 && value != 2 && value != 3) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: slab blocks per SM");
+            P->slab_mbreq = value;
         } else {
             if (value != 0 && (value < 2 || value > kSlabMaxSlots))
                 return fail(MGARD_ERR_INVALID_ARG, "plan_tune: slab ring slots");
@@ -1824,6 +1825,7 @@ int mgard_plan_get_tune(const mgard_plan *P, int level, int param)
     case 12: return L.slab_ty;
     case 13: return L.slab_ty > 0 ? L.slab_ns : 0;
     case 14: return P->slab_hook ? (int)(P->slab_wait_ns / 1000ull) : 0;
+    case 15: return L.slab_ty > 0 ? L.slab_mb : 0;
     default: return -1;
     }
 }

@@ -112,18 +112,19 @@ template <typename TX, typename TW>
 cudaError_t launch_persist(int mode, const PersistParams &p, int grid, size_t smem, cudaStream_t st);
 
 // Load vector + coarse gather of a 3D FP32 level from whole-row slabs staged
-// by bulk asynchronous copies (slab.cuh): ty = coarse rows per band (4 or
-// 8), ns = ring slots (2 .. kSlabMaxSlots), rows of n2 = 64 k + 1 nodes
-// (k <= 16), blocks of (n2 - 1) / 2 threads.
+// by bulk asynchronous copies (slab.cuh): ty = coarse rows per band (4, 6
+// or 8), ns = ring slots (2 .. kSlabMaxSlots), rows of n2 = 64 k + 1 nodes
+// (k <= 16), blocks of (n2 - 1) / 2 threads; minb = 3 compiles rows of up
+// to 513 nodes for three blocks per SM (fewer registers), else two.
 constexpr int kSlabMaxSlots = 16;
 constexpr int kSlabMaxThreads = 512;  // rows of up to 1025 nodes
 int slab_slot_bytes_of(int ty, int n2);
 size_t slab_smem_bytes(int ty, int n2, int ns);
 
 template <typename TW>
-cudaError_t slab_occupancy(int ty, int n2, int ns, int *blocks_per_sm);
+cudaError_t slab_occupancy(int ty, int n2, int ns, int minb, int *blocks_per_sm);
 
 template <typename TW>
-cudaError_t launch_slab(int ty, const SlabParams &p, int grid, cudaStream_t st);
+cudaError_t launch_slab(int ty, int minb, const SlabParams &p, int grid, cudaStream_t st);
 
 }  // namespace mg

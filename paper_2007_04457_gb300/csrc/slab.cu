@@ -7,12 +7,26 @@ namespace mg {
 
 namespace {
 
-template <typename TW>
-void (*slab_fn(int ty))(SlabParams)
+using SlabFn = void (*)(SlabParams);
+
+// rows of up to 513 nodes: 256-thread blocks with registers for `minb`
+// blocks per SM (3, or 2 with more registers); longer rows: 512 threads
+template <typename TW, int TY>
+SlabFn slab_fn_ty(int n2, int minb)
 {
-    if (ty == 4) return k_slab<TW, 4>;
-    if (ty == 8) return k_slab<TW, 8>;
-    return nullptr;
+    if ((n2 - 1) / 2 > 256) return k_slab<TW, TY, 512, 1>;
+    return minb >= 3 ? k_slab<TW, TY, 256, 3> : k_slab<TW, TY, 256, 2>;
+}
+
+template <typename TW>
+SlabFn slab_fn(int ty, int n2, int minb)
+{
+    switch (ty) {
+    case 4: return slab_fn_ty<TW, 4>(n2, minb);
+    case 6: return slab_fn_ty<TW, 6>(n2, minb);
+    case 8: return slab_fn_ty<TW, 8>(n2, minb);
+    default: return nullptr;
+    }
 }
 
 }  // namespace
@@ -20,6 +34,7 @@ void (*slab_fn(int ty))(SlabParams)
 int slab_slot_bytes_of(int ty, int n2)
 {
     if (ty == 4) return slab_slot_bytes<4>(n2);
+    if (ty == 6) return slab_slot_bytes<6>(n2);
     if (ty == 8) return slab_slot_bytes<8>(n2);
     return 0;
 }
@@ -30,9 +45,9 @@ size_t slab_smem_bytes(int ty, int n2, int ns)
 }
 
 template <typename TW>
-cudaError_t slab_occupancy(int ty, int n2, int ns, int *blocks_per_sm)
+cudaError_t slab_occupancy(int ty, int n2, int ns, int minb, int *blocks_per_sm)
 {
-    auto fn = slab_fn<TW>(ty);
+    auto fn = slab_fn<TW>(ty, n2, minb);
     if (!fn || ns < 2 || ns > kSlabMaxSlots || (n2 - 1) % 64 != 0 || (n2 - 1) / 2 > kSlabMaxThreads)
         return cudaErrorInvalidValue;
     const size_t smem = slab_smem_bytes(ty, n2, ns);
@@ -43,9 +58,9 @@ cudaError_t slab_occupancy(int ty, int n2, int ns, int *blocks_per_sm)
 }
 
 template <typename TW>
-cudaError_t launch_slab(int ty, const SlabParams &p, int grid, cudaStream_t st)
+cudaError_t launch_slab(int ty, int minb, const SlabParams &p, int grid, cudaStream_t st)
 {
-    auto fn = slab_fn<TW>(ty);
+    auto fn = slab_fn<TW>(ty, p.n2, minb);
     if (!fn || p.nitems <= 0 || grid <= 0 || p.slot_bytes != slab_slot_bytes_of(ty, p.n2)) return cudaErrorInvalidValue;
     const size_t smem = slab_smem_bytes(ty, p.n2, p.ns);
     // the limit is per function: plans with other shapes may have lowered it
@@ -56,9 +71,9 @@ cudaError_t launch_slab(int ty, const SlabParams &p, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template cudaError_t slab_occupancy<float>(int, int, int, int *);
-template cudaError_t slab_occupancy<double>(int, int, int, int *);
-template cudaError_t launch_slab<float>(int, const SlabParams &, int, cudaStream_t);
-template cudaError_t launch_slab<double>(int, const SlabParams &, int, cudaStream_t);
+template cudaError_t slab_occupancy<float>(int, int, int, int, int *);
+template cudaError_t slab_occupancy<double>(int, int, int, int, int *);
+template cudaError_t launch_slab<float>(int, int, const SlabParams &, int, cudaStream_t);
+template cudaError_t launch_slab<double>(int, int, const SlabParams &, int, cudaStream_t);
 
 }  // namespace mg

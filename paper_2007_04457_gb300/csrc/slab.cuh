@@ -307,11 +307,12 @@ __device__ __forceinline__ float slab_last_col(const float *slot, int s0, int n1
     return ge;
 }
 
-// One block per band x chunk item, (n2 - 1) / 2 = m2 - 1 threads: thread t
-// owns coarse column t; the last warp also computes the final column m2 - 1
-// (lane j its coarse row Y0 + j).
-template <typename TW, int TY>
-__global__ void __launch_bounds__(kSlabMaxThreads) k_slab(SlabParams p)
+// One block per band x chunk item, (n2 - 1) / 2 = m2 - 1 <= MAXT threads:
+// thread t owns coarse column t; the last warp also computes the final
+// column m2 - 1 (lane j its coarse row Y0 + j).  MINB: blocks per SM the
+// register allocation is sized for.
+template <typename TW, int TY, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_slab(SlabParams p)
 {
     static_assert(2 * TY + 3 <= 32, "a band's fine rows fit one warp");
     extern __shared__ __align__(128) unsigned char slab_smem[];

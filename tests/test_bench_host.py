@@ -45,7 +45,9 @@ def test_traffic_key_follows_own_and_shared_sources(csrc_copy):
     assert bench.kernel_source_hash(INTERP) != before[INTERP]
     assert bench.kernel_source_hash(RESTRICT) == before[RESTRICT]
     assert bench.kernel_source_hash("prolong") == before["prolong"]
-    _touch(csrc_copy / "restrict_strip.cuh")
+    _touch(csrc_copy / "restrict_strip.cuh")             # the strip kernel is no longer the restriction
+    assert bench.kernel_source_hash(RESTRICT) == before[RESTRICT]
+    _touch(csrc_copy / "slab.cuh")
     assert bench.kernel_source_hash(RESTRICT) != before[RESTRICT]
     mid = {k: bench.kernel_source_hash(k) for k in (INTERP, "prolong")}
     _touch(csrc_copy / "api.cu")   # host code shared by every kernel

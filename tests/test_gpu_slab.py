@@ -6,8 +6,8 @@ kernels it replaces (tuning param 10 = 1 keeps it out).
 Every level runs the per-level kernels here (tuning param 3 = 1), so the
 slab kernel takes every 3D level with FP32 level arrays and rows of
 128 k + 1 nodes, not only the finest.  Shapes cover rows of 129, 257, 513
-and 1025 nodes (one to eight warps per block), bands of 8 and of 4 coarse
-rows (a level with fewer than 8), a last band shifted back over its
+and 1025 nodes (two to sixteen warps per block), bands of 6 and of 4 coarse
+rows (a level with fewer than 6), a last band shifted back over its
 neighbour, FP32 and the mixed scheme (FP32 level 0, FP64 coarse arrays),
 uniform and graded coordinates and partial level counts; the chunk, band
 and ring-slot choices are swept on one shape; and a copy wait that runs
@@ -46,7 +46,7 @@ def _relerr(got, want):
 
 CASES = [
     # shape, dtype, nlevels, nonuniform
-    ((9, 17, 129), "f32", -1, False),         # one warp per block, bands of 8 coarse rows
+    ((9, 17, 129), "f32", -1, False),         # two warps per block, bands of 6 coarse rows
     ((5, 9, 129), "f32", -1, False),          # 5 coarse rows: bands of 4
     ((17, 33, 257), "f32", -1, True),         # graded grid, levels 0 and 1 by the slab kernel
     ((9, 17, 513), "f32_mixed", -1, False),   # FP64 coarse arrays
@@ -71,7 +71,7 @@ def _run(shape, dtype, nlevels, nonuniform, slab_on=True, tune=()):
 @pytest.mark.parametrize("shape,dtype,nlevels,nonuniform", CASES)
 def test_slab_matches_oracle(shape, dtype, nlevels, nonuniform):
     mg, plan, coords = _run(shape, dtype, nlevels, nonuniform)
-    assert mg.mgard_plan_get_tune(plan.handle, 0, 12) in (4, 8), "the slab kernel takes level 0"
+    assert mg.mgard_plan_get_tune(plan.handle, 0, 12) in (4, 6, 8), "the slab kernel takes level 0"
     u = synth.sinusoid_field(shape, 12, seed=3, dtype=np.float32)
     t = torch.from_numpy(u).cuda()
     plan.decompose(t)
@@ -110,6 +110,7 @@ def test_slab_agrees_with_strip_kernels(shape, dtype, nlevels, nonuniform):
     ((11, 1),), ((11, 2),), ((11, 5),), ((11, 40),),       # coarse planes per chunk
     ((13, 2),), ((13, 3),), ((13, 8),),                   # ring slots
     ((12, 4),), ((12, 4), (11, 3), (13, 5)),              # bands of 4 rows
+    ((12, 8),), ((12, 8), (15, 2)), ((15, 3),),           # bands of 8 rows; register variants
 ])
 def test_slab_launch_shapes(tune):
     shape = (17, 33, 257)
@@ -117,7 +118,7 @@ def test_slab_launch_shapes(tune):
     for param, value in tune:
         if param == 11:
             assert mg.mgard_plan_get_tune(plan.handle, 0, 11) == min(value, (shape[0] - 1) // 2)
-        elif param in (12, 13):
+        elif param in (12, 13, 15):
             assert mg.mgard_plan_get_tune(plan.handle, 0, param) == value
     u = synth.sinusoid_field(shape, 12, seed=6, dtype=np.float32)
     t = torch.from_numpy(u).cuda()
