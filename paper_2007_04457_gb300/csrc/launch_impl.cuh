@@ -131,6 +131,31 @@ cudaError_t launch_solve_chunks(const SolveParams &p, int num_sms, cudaStream_t 
     return cudaGetLastError();
 }
 
+// k_solve_strided: 16 warps (chunks of at most CH = ceil(m / 16) nodes) per
+// panel of 32 lines; CH 9, 17 or 33 (lines of up to 528 nodes; 8-byte
+// elements up to 272, where the chunks still fit the registers).
+template <typename TW>
+cudaError_t launch_solve_strided(const SolveParams &p, int num_sms, cudaStream_t st)
+{
+    const int nw = std::min(kSolveStridedWarps, p.m);
+    const int ch = (p.m + nw - 1) / nw;
+    if (sizeof(TW) == 8 && ch > 17) return cudaErrorInvalidValue;  // spills: the caller takes another kernel
+    void (*fn)(SolveParams) = ch <= 9 ? k_solve_strided<TW, 9> : ch <= 17 ? k_solve_strided<TW, 17>
+                                                                             : k_solve_strided<TW, 33>;
+    if (ch > 33) return cudaErrorInvalidValue;
+    const size_t smem = solve_strided_elems<TW>(p.m, nw) * sizeof(TW);
+    cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int bps = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, 32 * nw, smem);
+    if (err != cudaSuccess) return err;
+    const int64_t panels = (p.nlines + 31) / 32;
+    const int64_t grid = std::min<int64_t>(panels, (int64_t)std::max(1, bps) * num_sms);
+    fn<<<(unsigned)grid, 32 * nw, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
 // k_solve_lines: one thread per line, the factors of the line in shared memory.
 template <typename TW>
 cudaError_t launch_solve_lines(const SolveParams &p, int num_sms, cudaStream_t st)
@@ -148,23 +173,22 @@ cudaError_t launch_solve_lines(const SolveParams &p, int num_sms, cudaStream_t s
     return cudaGetLastError();
 }
 
-// nw_req = -1, or 0 for a dimension whose stride exceeds its length (in a
-// cube the slowest one) with enough lines for every SM: k_solve_lines
-// (measured slower than the chunks along the other dimensions, several times
-// along the contiguous one, where its stores evict the lines its loads still
-// need); nw_req = 0 otherwise: k_solve_chunks for lines up to 576
-// nodes (and shared memory for the contiguous case); else (or nw_req > 0)
-// the shared-memory panel kernel with nw_req warps (0: about 16 nodes per
-// chunk).
+// nw_req = -1: k_solve_lines (one thread per line); nw_req = 0: along a
+// strided dimension k_solve_strided for lines up to 528 nodes, along the
+// contiguous one k_solve_chunks for lines up to 576 nodes (the panel staged
+// in shared memory); else (or nw_req > 0) the shared-memory panel kernel with
+// nw_req warps (0: about 16 nodes per chunk).
 template <typename TW>
 cudaError_t launch_solve(const SolveParams &p_in, int nw_req, int num_sms, cudaStream_t st)
 {
     SolveParams p = p_in;
     if (p.nlines <= 0) return cudaSuccess;
     const bool lines_fit = (size_t)3 * p.m * sizeof(TW) <= 100 * 1024;
-    if (lines_fit && (nw_req == -1 || (nw_req == 0 && p.inner > p.m && p.nlines >= (int64_t)kSolveLinesPerSm * num_sms)))
-        return launch_solve_lines<TW>(p, num_sms, st);
+    if (lines_fit && nw_req == -1) return launch_solve_lines<TW>(p, num_sms, st);
     if (nw_req < 0) nw_req = 0;
+    if (nw_req == 0 && p.inner > 1 && p.m <= (sizeof(TW) == 4 ? 33 : 17) * kSolveStridedWarps &&
+        (int64_t)p.m * p.stride < (int64_t(1) << 31) && (size_t)3 * p.m * sizeof(TW) <= 100 * 1024)
+        return launch_solve_strided<TW>(p, num_sms, st);
     if (nw_req == 0 && p.m <= 32 * kSolveChunkWarps && (int64_t)p.m * p.stride < (int64_t(1) << 31)) {
         const int ch = (p.m <= 16 * kSolveChunkWarps) ? 16 : 32;
         const int nw = (p.m + ch - 1) / ch;

@@ -398,6 +398,122 @@ __global__ void __launch_bounds__(32 * kSolveChunkWarps) k_solve_chunks(SolvePar
     cp_async_wait<0>();
 }
 
+// k_solve_strided: lines along a dimension that is not the contiguous one.
+// A block takes panels of 32 consecutive lines (lane = line: every load and
+// store of a warp touches 32 neighbouring elements), its nw warps a chunk of
+// every line each (chunk w = nodes [w m / nw, (w + 1) m / nw), at most CH),
+// held in registers together with the V values it updates.  Per sweep a warp
+// runs its chunk's recurrence from a zero carry, publishes the chunk-end
+// value, composes the carries of the chunks before it (each chunk is the
+// affine map y_out = T + P y_in, P the product of its -a_i, or of its -q_i
+// backward, tabulated per warp) and re-runs the chunk from its true carry.
+// DRAM traffic: F read once, written once (or V read and written once).
+template <typename TW>
+inline size_t solve_strided_elems(int m, int nw)
+{
+    return 3 * (size_t)m + 2 * (size_t)nw + 2 * 32 * (size_t)nw;
+}
+
+constexpr int kSolveStridedWarps = 16;
+
+// Registers sized for two blocks per SM where the chunk and its V values fit
+// them (4-byte elements, CH <= 17), else one.
+template <typename TW, int CH>
+struct StridedMinBlocks {
+    static constexpr int value = (sizeof(TW) == 4 && CH <= 17) ? 2 : 1;
+};
+
+template <typename TW, int CH>
+__global__ void __launch_bounds__(32 * kSolveStridedWarps, StridedMinBlocks<TW, CH>::value) k_solve_strided(SolveParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int m = p.m;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    TW *sfac = reinterpret_cast<TW *>(smem_raw);  // (a, inv, q) per node
+    TW *Pw = sfac + 3 * m;                         // per chunk: product of -a_i
+    TW *Qw = Pw + nw;                              // per chunk: product of -q_i
+    TW *ca = Qw + nw;                              // forward chunk-end values [nw][32]
+    TW *cb = ca + 32 * nw;                         // backward chunk-start values [nw][32]
+    const TW *fac = static_cast<const TW *>(p.fac);
+    TW *F = static_cast<TW *>(p.F);
+    TW *V = static_cast<TW *>(p.V);
+    const TW *in = p.src ? static_cast<const TW *>(p.src) : F;
+    for (int i = threadIdx.x; i < 3 * m; i += blockDim.x) sfac[i] = fac[i];
+    __syncthreads();
+    const int s = (w * m) / nw, len = ((w + 1) * m) / nw - s;
+    if (lane == 0) {
+        TW pa = TW(1), pq = TW(1);
+        for (int j = 0; j < len; ++j) {
+            pa = -sfac[3 * (s + j)] * pa;
+            pq = -sfac[3 * (s + j) + 2] * pq;
+        }
+        Pw[w] = pa;
+        Qw[w] = pq;
+    }
+    __syncthreads();
+    const int64_t inner = p.inner;
+    const int stride = (int)p.stride;  // a line spans m * stride < 2^31 elements (checked by the launcher)
+    const int64_t npanels = (p.nlines + 31) / 32;
+    const TW sg = (p.vmode == 2) ? TW(-1) : TW(1);
+    // the factors are read where they are used (one broadcast load each),
+    // not kept in registers: the chunk and its V values need them
+    const volatile TW *vfac = sfac;
+    for (int64_t panel = blockIdx.x; panel < npanels; panel += gridDim.x) {
+        const int64_t line = panel * 32 + lane;
+        const bool lv = line < p.nlines;
+        const int64_t base = lv ? (line / inner) * (inner * m) + line % inner + (int64_t)s * stride : 0;
+        const TW *fin = in + base;
+        TW y[CH], vv[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) y[j] = (j < len && lv) ? fin[j * stride] : TW(0);
+        if (p.vmode != 0) {
+            const TW *vin = V + base;
+#pragma unroll
+            for (int j = 0; j < CH; ++j) vv[j] = (j < len && lv) ? vin[j * stride] : TW(0);
+        }
+        // forward y_i = f_i - a_i y_{i-1}: chunk-end value from a zero carry
+        TW t = TW(0);
+#pragma unroll
+        for (int j = 0; j < CH; ++j)
+            if (j < len) t = y[j] - vfac[3 * (s + j)] * t;
+        ca[w * 32 + lane] = t;
+        __syncthreads();
+        TW c = TW(0);
+        for (int k = 0; k < w; ++k) c = ca[k * 32 + lane] + Pw[k] * c;
+        t = c;
+#pragma unroll
+        for (int j = 0; j < CH; ++j)
+            if (j < len) {
+                t = y[j] - vfac[3 * (s + j)] * t;
+                y[j] = t;
+            }
+        // backward z_i = inv_i y_i - q_i z_{i+1}: chunk-start value from a zero carry
+        t = TW(0);
+#pragma unroll
+        for (int j = CH - 1; j >= 0; --j)
+            if (j < len) t = vfac[3 * (s + j) + 1] * y[j] - vfac[3 * (s + j) + 2] * t;
+        cb[w * 32 + lane] = t;
+        __syncthreads();
+        c = TW(0);
+        for (int k = nw - 1; k > w; --k) c = cb[k * 32 + lane] + Qw[k] * c;
+        t = c;
+#pragma unroll
+        for (int j = CH - 1; j >= 0; --j)
+            if (j < len) {
+                t = vfac[3 * (s + j) + 1] * y[j] - vfac[3 * (s + j) + 2] * t;
+                y[j] = t;
+            }
+        // z into F, or V +- z
+        if (lv) {
+            TW *dst = ((p.vmode == 0) ? F : V) + base;
+#pragma unroll
+            for (int j = 0; j < CH; ++j)
+                if (j < len) dst[j * stride] = (p.vmode == 0) ? y[j] : vv[j] + sg * y[j];
+        }
+        __syncthreads();  // the carries are reused by the next panel
+    }
+}
+
 // One thread per line: the Thomas recurrences of the tabulated LU factors
 // (forward y_i = f_i - a_i y_{i-1}, backward z_i = inv_i y_i - q_i z_{i+1}),
 // U nodes at a time with the next U prefetched into registers before the
