@@ -208,7 +208,13 @@ MGARD_API mgard_status mgard_recompose_classes(const mgard_plan *plan, int nclas
  *            kernel, 2 .. 16 (0 = automatic: 2); a count whose shared memory
  *            does not fit leaves the affected levels to the other kernels.
  *   param 15 plan-wide: the slab kernel's register budget, for 2 or 3
- *            blocks per SM (0 = automatic: 3 where they fit).
+ *            blocks per SM (0 = automatic: 3 where they fit, 2 for the FP64
+ *            coarse rows of the mixed scheme).
+ *   param 16 plan-wide: 1 = the slab kernel also solves M_{l-1} along the
+ *            contiguous dimension, one warp per finished row, and the
+ *            separate solve of that dimension is skipped; 0 = the solve
+ *            kernels do it (default: measured faster on this GPU).  The
+ *            forms differ only in rounding order.
  *   param 14 plan-wide test hook: v > 0 announces each slab block's first
  *            copy with 16 bytes more than it moves, so its wait runs out
  *            after v microseconds (the block records it and returns; the
@@ -218,7 +224,7 @@ MGARD_API mgard_status mgard_recompose_classes(const mgard_plan *plan, int nclas
  *   mgard_plan_get_tune also reports param 5: the first level the
  *   cooperative kernel runs (-1: none), param 8: the row-chunk
  *   restriction's segment width of the level (512 or 256 columns; 0: not a
- *   row-chunk level), and for params 11 .. 13 and 15 the level's values
+ *   row-chunk level), and for params 11 .. 13, 15 and 16 the level's values
  *   (0: not a slab level).
  * Returns MGARD_ERR_INVALID_ARG for an unknown parameter or value. */
 MGARD_API mgard_status mgard_plan_tune(mgard_plan *plan, int level, int param, int value);

@@ -78,6 +78,7 @@ struct mgard_level {
     int slab_ty = 0, slab_ns = 0, slab_sb = 0;  // coarse rows per band, ring slots, slot bytes
     int slab_mb = 0;                            // register variant: blocks per SM (2 or 3)
     int slab_zreq = 0;                          // tune: coarse planes per chunk (0: automatic)
+    bool slab_xs = false;                       // the slab kernel also solves along dim 2
     int slab_nb = 0, slab_zc = 0, slab_nzc = 0, slab_grid = 0;
 };
 
@@ -122,6 +123,7 @@ struct mgard_plan {
     bool slab_off = false;            // tune: the slab load-vector kernel kept out
     int slab_tyreq = 0, slab_nsreq = 0;  // tune: its rows per band, ring slots (0: automatic)
     int slab_mbreq = 0;               // tune: its register variant, blocks per SM 2 or 3 (0: automatic)
+    bool slab_xs_on = false;          // tune: the slab kernel also solves along dim 2 (measured slower)
     int slab_hook = 0;                // tune: test hook (each block's first copy wait runs out)
     unsigned long long slab_wait_ns = 2000000000ull;  // limit of one copy wait
     unsigned *d_status = nullptr;     // device status word of the slab kernel (owned)
@@ -382,7 +384,7 @@ bool slab_on(const mgard_plan *P, int j) { return P->lv[j].slab_ty > 0; }
 // Leading dims whose solve the level's load-vector kernel already did.
 int solved_first(const mgard_plan *P, int j, const void *A)
 {
-    if (slab_on(P, j)) return 0;
+    if (slab_on(P, j)) return P->lv[j].slab_xs ? 1 : 0;
     return (rc_on(P, j, A, 1) && P->lv[j].rc_xs) ? 1 : 0;
 }
 
@@ -408,8 +410,9 @@ cudaError_t run_slab(const mgard_plan *P, int j, int mode, const void *A, char *
     p.hook = P->slab_hook;
     p.status = P->d_status;
     p.wait_ns = P->slab_wait_ns;
+    p.fx = tab_ptr<TW>(P, L.t_off[2]);
     return timed(P, mode == MODE_DEC ? KIND_RESTRICT_DEC : KIND_RESTRICT_REC, j, st,
-                 [&] { return launch_slab<TW>(L.slab_ty, L.slab_mb, p, L.slab_grid, st); });
+                 [&] { return launch_slab<TW>(L.slab_ty, L.slab_mb, L.slab_xs, p, L.slab_grid, st); });
 }
 
 template <typename T, typename TW>
@@ -955,17 +958,20 @@ cudaError_t configure_slab(mgard_plan *P, mgard_level &L, bool finest)
     if (P->slab_off || P->per_dim || P->act != ACT_3D || es != 4) return cudaSuccess;
     const int64_t n2 = L.n[2], m0 = L.m[0], m1 = L.m[1];
     if ((n2 - 1) % 64 != 0 || (n2 - 1) / 2 > kSlabMaxThreads || m0 < 2) return cudaSuccess;
-    // (rows per band, ring slots) in order of preference, as tuned: the first
-    // whose shared memory fits a block
+    // (rows per band, ring slots, blocks per SM) in order of preference, as
+    // tuned: the first whose shared memory fits a block; the dim-2 solve in
+    // the kernel when switched on
+    const bool xs = P->slab_xs_on;
     int ty = 0, ns = 0, bps = 0, minb = 0;
     static const int pref[7][3] = {{6, 2, 3}, {8, 2, 2}, {4, 2, 3}, {4, 3, 3}, {8, 3, 2}, {8, 4, 2}, {4, 4, 2}};
     for (const auto &c : pref) {
         const int cty = P->slab_tyreq > 0 ? P->slab_tyreq : c[0];
         const int cns = P->slab_nsreq > 0 ? P->slab_nsreq : c[1];
-        const int cmb = P->slab_mbreq > 0 ? P->slab_mbreq : c[2];
+        // FP64 coarse rows (mixed scheme): the two-block register budget
+        const int cmb = P->slab_mbreq > 0 ? P->slab_mbreq : (sizeof(TW) == 8 ? 2 : c[2]);
         if (m1 < cty) continue;
         int b = 0;
-        if (slab_occupancy<TW>(cty, (int)n2, cns, cmb, &b) != cudaSuccess || b < 1) {
+        if (slab_occupancy<TW>(cty, (int)n2, cns, cmb, xs, &b) != cudaSuccess || b < 1) {
             cudaGetLastError();
             continue;
         }
@@ -997,6 +1003,7 @@ cudaError_t configure_slab(mgard_plan *P, mgard_level &L, bool finest)
     L.slab_ty = ty;
     L.slab_ns = ns;
     L.slab_mb = minb;
+    L.slab_xs = xs;
     L.slab_sb = slab_slot_bytes_of(ty, (int)n2);
     L.slab_nb = (int)nb;
     L.slab_zc = (int)best_zc;
@@ -1538,7 +1545,8 @@ int mgard_plan_launches(const mgard_plan *P, int recompose)
     const int J = coop ? P->coop_j : P->small_j;
     int n = 0;
     for (int j = 0; j < J; ++j) {
-        const bool xs = P->lv[j].rc_q[0] > 0 && !(P->rc_off & 2) && P->lv[j].rc_xs;
+        const bool xs = P->lv[j].slab_ty > 0 ? P->lv[j].slab_xs
+                                             : P->lv[j].rc_q[0] > 0 && !(P->rc_off & 2) && P->lv[j].rc_xs;
         n += 1 + P->ndim - (xs ? 1 : 0) + tail;
     }
     return n + (J < P->L ? 1 : 0);
@@ -1761,7 +1769,8 @@ mgard_status mgard_plan_tune(mgard_plan *P, int level, int param, int value)
     case 11:
     case 12:
     case 13:
-    case 15: {
+    case 15:
+    case 16: {
         if (param == 10) {
             if (value != 0 && value != 1) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: slab switch");
             P->slab_off = value != 0;
@@ -1775,6 +1784,9 @@ mgard_status mgard_plan_tune(mgard_plan *P, int level, int param, int value)
         } else if (param == 15) {
             if (value != 0 && value != 2 && value != 3) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: slab blocks per SM");
             P->slab_mbreq = value;
+        } else if (param == 16) {
+            if (value != 0 && value != 1) return fail(MGARD_ERR_INVALID_ARG, "plan_tune: slab dim-2 solve switch");
+            P->slab_xs_on = value != 0;
         } else {
             if (value != 0 && (value < 2 || value > kSlabMaxSlots))
                 return fail(MGARD_ERR_INVALID_ARG, "plan_tune: slab ring slots");
@@ -1826,6 +1838,7 @@ int mgard_plan_get_tune(const mgard_plan *P, int level, int param)
     case 13: return L.slab_ty > 0 ? L.slab_ns : 0;
     case 14: return P->slab_hook ? (int)(P->slab_wait_ns / 1000ull) : 0;
     case 15: return L.slab_ty > 0 ? L.slab_mb : 0;
+    case 16: return L.slab_ty > 0 ? (L.slab_xs ? 1 : 0) : (P->slab_xs_on ? 1 : 0);
     default: return -1;
     }
 }

@@ -119,12 +119,13 @@ cudaError_t launch_persist(int mode, const PersistParams &p, int grid, size_t sm
 constexpr int kSlabMaxSlots = 16;
 constexpr int kSlabMaxThreads = 512;  // rows of up to 1025 nodes
 int slab_slot_bytes_of(int ty, int n2);
-size_t slab_smem_bytes(int ty, int n2, int ns);
+size_t slab_smem_bytes(int ty, int n2, int ns, bool xs, int tw_bytes);
 
 template <typename TW>
-cudaError_t slab_occupancy(int ty, int n2, int ns, int minb, int *blocks_per_sm);
+cudaError_t slab_occupancy(int ty, int n2, int ns, int minb, bool xs, int *blocks_per_sm);
 
+// xs: the kernel also solves M_{l-1} along dim 2 (p.fx) before storing F
 template <typename TW>
-cudaError_t launch_slab(int ty, int minb, const SlabParams &p, int grid, cudaStream_t st);
+cudaError_t launch_slab(int ty, int minb, bool xs, const SlabParams &p, int grid, cudaStream_t st);
 
 }  // namespace mg

@@ -129,6 +129,7 @@ struct SlabParams {
     int hook;                  // test hook: each block's first copy wait runs out
     unsigned *status;          // sticky status word: bit 0 = a copy wait ran out
     unsigned long long wait_ns;  // limit of one copy wait
+    const void *fx;            // LU factors of M_{l-1} along dim 2, 3 per coarse node (type TW)
 };
 
 }  // namespace mg

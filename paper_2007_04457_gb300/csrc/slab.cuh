@@ -31,6 +31,7 @@
 
 #include "common.cuh"
 #include "params.h"
+#include "rowchunk.cuh"  // rc_xsolve: a row's tridiagonal solve by one warp
 
 namespace mg {
 
@@ -132,6 +133,16 @@ template <int TY>
 __host__ __device__ inline int slab_slot_bytes(int n2)
 {
     return ((SlabGeom<TY>::NR * n2 * 4 + 32) + 15) / 16 * 16;
+}
+
+// Bytes after the ring for the solve along dim 2 (XS): two buffers of TY
+// rows of m2 (+1) coarse values and the factor table of a row (3 (m2 - 1)
+// values, the final node's apart), in TW.
+template <int TY>
+__host__ __device__ inline int slab_xs_bytes(int n2, int tw_bytes)
+{
+    const int m2 = (n2 - 1) / 2 + 1;
+    return ((2 * TY * (m2 + 1) + 3 * (m2 - 1)) * tw_bytes + 15) / 16 * 16;
 }
 
 // Item geometry: band b = item % nb, chunk c = item / nb.
@@ -307,11 +318,51 @@ __device__ __forceinline__ float slab_last_col(const float *slot, int s0, int n1
     return ge;
 }
 
+// The solve of M_{l-1} along dim 2 of row w of a finished coarse plane
+// (srow, m2 = 32 C2 + 1 values; lane L holds nodes C2 L .. C2 L + C2 - 1,
+// lane 31 also the final one), written back to srow and then to the F row
+// by the warp in order (coalesced).
+template <typename TW, int C2>
+__device__ __forceinline__ void slab_xsolve_row(TW *srow, const TW *sfac, TW xa, TW xi, int lane, TW *frow)
+{
+    constexpr int M2 = 32 * C2 + 1;
+    TW f[C2 + 1];
+#pragma unroll
+    for (int k = 0; k < C2; ++k) f[k] = srow[C2 * lane + k];
+    f[C2] = (lane == 31) ? srow[32 * C2] : TW(0);
+    rc_xsolve<TW, C2>(f, sfac, xa, xi, lane);
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < C2; ++k) srow[C2 * lane + k] = f[k];
+    if (lane == 31) srow[32 * C2] = f[C2];
+    __syncwarp();
+    for (int c = lane; c < M2; c += 32) frow[c] = srow[c];
+}
+
+// C2 = (m2 - 1) / 32 is the block's warp count: 1 .. 8 for blocks of up to
+// 256 threads, 16 for 512
+template <typename TW, int MAXT>
+__device__ __forceinline__ void slab_xsolve_any(int c2, TW *srow, const TW *sfac, TW xa, TW xi, int lane, TW *frow)
+{
+    if constexpr (MAXT > 256) {
+        slab_xsolve_row<TW, 16>(srow, sfac, xa, xi, lane, frow);
+    } else {
+        switch (c2) {
+        case 1: slab_xsolve_row<TW, 1>(srow, sfac, xa, xi, lane, frow); break;
+        case 2: slab_xsolve_row<TW, 2>(srow, sfac, xa, xi, lane, frow); break;
+        case 4: slab_xsolve_row<TW, 4>(srow, sfac, xa, xi, lane, frow); break;
+        default: slab_xsolve_row<TW, 8>(srow, sfac, xa, xi, lane, frow); break;
+        }
+    }
+}
+
 // One block per band x chunk item, (n2 - 1) / 2 = m2 - 1 <= MAXT threads:
 // thread t owns coarse column t; the last warp also computes the final
 // column m2 - 1 (lane j its coarse row Y0 + j).  MINB: blocks per SM the
-// register allocation is sized for.
-template <typename TW, int TY, int MAXT, int MINB>
+// register allocation is sized for.  XS: each finished coarse plane's rows
+// are solved along dim 2 (M_{l-1}, row j by warp j mod the warp count)
+// before they are stored, so the host skips that dimension's solve.
+template <typename TW, int TY, int MAXT, int MINB, bool XS>
 __global__ void __launch_bounds__(MAXT, MINB) k_slab(SlabParams p)
 {
     static_assert(2 * TY + 3 <= 32, "a band's fine rows fit one warp");
@@ -328,6 +379,20 @@ __global__ void __launch_bounds__(MAXT, MINB) k_slab(SlabParams p)
     const bool lastwarp = (t >> 5) == (int)(blockDim.x >> 5) - 1;
     const int n1 = p.n1, n2 = p.n2, m0 = p.m0, m1 = p.m1, m2 = p.m2, NS = p.ns, SB = p.slot_bytes;
     const int64_t plane = (int64_t)n1 * n2, cplane = (int64_t)m1 * m2;
+    const int w = t >> 5, C2 = (m2 - 1) / 32;
+    // XS: two row buffers [TY][m2 + 1] and the dim-2 factor table [3][C2][32]
+    TW *xrow = reinterpret_cast<TW *>(ring + (size_t)NS * SB);
+    TW *xfac = xrow + 2 * TY * (m2 + 1);
+    TW xa = TW(0), xi = TW(0);
+    if constexpr (XS) {
+        const TW *fx = static_cast<const TW *>(p.fx);
+        for (int e = t; e < 3 * (m2 - 1); e += blockDim.x) {
+            const int tt = e / (C2 * 32), k = (e / 32) % C2, l = e % 32;
+            xfac[e] = fx[3 * (C2 * l + k) + tt];
+        }
+        xa = fx[3 * (m2 - 1)];
+        xi = fx[3 * (m2 - 1) + 1];
+    }
 
     if (t == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
@@ -384,12 +449,36 @@ __global__ void __launch_bounds__(MAXT, MINB) k_slab(SlabParams p)
         float accP[TY], accC[TY], accN[TY], eP = 0.f, eC = 0.f, eN = 0.f;
 #pragma unroll
         for (int j = 0; j < TY; ++j) accP[j] = accC[j] = accN[j] = 0.f;
+        // F rows of coarse plane Zo: stored (or, XS, put in the row buffer of
+        // Zo's parity, solved and stored by warp j after the next barrier)
+        int pend = -1;  // XS: the plane whose rows wait for their solve
         auto store = [&](int Zo) {
-            TW *f = F + (int64_t)Zo * cplane + (int64_t)Y0 * m2;
+            if constexpr (XS) {
+                TW *xr = xrow + (Zo & 1) * TY * (m2 + 1);
 #pragma unroll
-            for (int j = 0; j < TY; ++j)
-                if (Y0 + j >= yown) f[(int64_t)j * m2 + t] = static_cast<TW>(accP[j]);
-            if (lastwarp && lane < TY && Y0 + lane >= yown) f[(int64_t)lane * m2 + (m2 - 1)] = static_cast<TW>(eP);
+                for (int j = 0; j < TY; ++j) xr[j * (m2 + 1) + t] = static_cast<TW>(accP[j]);
+                if (lastwarp && lane < TY) xr[lane * (m2 + 1) + (m2 - 1)] = static_cast<TW>(eP);
+                pend = Zo;
+            } else {
+                TW *f = F + (int64_t)Zo * cplane + (int64_t)Y0 * m2;
+#pragma unroll
+                for (int j = 0; j < TY; ++j)
+                    if (Y0 + j >= yown) f[(int64_t)j * m2 + t] = static_cast<TW>(accP[j]);
+                if (lastwarp && lane < TY && Y0 + lane >= yown)
+                    f[(int64_t)lane * m2 + (m2 - 1)] = static_cast<TW>(eP);
+            }
+        };
+        auto solve_pending = [&]() {
+            if constexpr (XS) {
+                if (pend >= 0) {
+                    // row j by warp j mod (warps of the block)
+                    for (int j = w; j < TY; j += (int)(blockDim.x >> 5))
+                        if (Y0 + j >= yown)
+                            slab_xsolve_any<TW, MAXT>(C2, xrow + (pend & 1) * TY * (m2 + 1) + j * (m2 + 1), xfac, xa,
+                                                      xi, lane, F + (int64_t)pend * cplane + (int64_t)(Y0 + j) * m2);
+                }
+                pend = -1;
+            }
         };
 
         for (int z = it.zlo; z <= it.zhi; ++z, ++pos) {
@@ -458,10 +547,17 @@ __global__ void __launch_bounds__(MAXT, MINB) k_slab(SlabParams p)
                 break;
             }
             if (t == 0) issue_next();
+            solve_pending();  // the rows stored before this barrier
         }
         // the last coarse plane of the grid has no contributions beyond it
         // (after the final shift it is in accP)
-        if (!dead && it.zhi == 2 * (m0 - 1) && m0 - 1 >= it.Zs && m0 - 1 < it.Ze) store(m0 - 1);
+        if (!dead && it.zhi == 2 * (m0 - 1) && m0 - 1 >= it.Zs && m0 - 1 < it.Ze) {
+            store(m0 - 1);
+            if constexpr (XS) {
+                __syncthreads();
+                solve_pending();
+            }
+        }
     }
     if (dead) {
         // record it, then let the copies this block issued (from the one

@@ -9,9 +9,11 @@ slab kernel takes every 3D level with FP32 level arrays and rows of
 and 1025 nodes (two to sixteen warps per block), bands of 6 and of 4 coarse
 rows (a level with fewer than 6), a last band shifted back over its
 neighbour, FP32 and the mixed scheme (FP32 level 0, FP64 coarse arrays),
-uniform and graded coordinates and partial level counts; the chunk, band
-and ring-slot choices are swept on one shape; and a copy wait that runs
-out on purpose is reported by mgard_plan_check.
+uniform and graded coordinates and partial level counts, with the solve
+along the contiguous dimension left to the solve kernels (the default) and
+in the kernel (tuning param 16 = 1, also on every CASES shape); the
+chunk, band, ring-slot and register choices are swept on one shape; and a
+copy wait that runs out on purpose is reported by mgard_plan_check.
 """
 import numpy as np
 import pytest
@@ -92,6 +94,21 @@ def test_slab_matches_oracle(shape, dtype, nlevels, nonuniform):
     assert _relerr(c.cpu().numpy().astype(np.float64), back) <= TOL[dtype]
 
 
+@pytest.mark.parametrize("shape,dtype,nlevels,nonuniform", CASES)
+def test_slab_with_dim2_solve_matches_oracle(shape, dtype, nlevels, nonuniform):
+    mg, plan, coords = _run(shape, dtype, nlevels, nonuniform, tune=((16, 1),))
+    assert mg.mgard_plan_get_tune(plan.handle, 0, 16) == 1
+    u = synth.sinusoid_field(shape, 12, seed=9, dtype=np.float32)
+    t = torch.from_numpy(u).cuda()
+    plan.decompose(t)
+    torch.cuda.synchronize()
+    want = oracle.decompose(u.astype(np.float64), nlevels=plan.levels, coords=coords)
+    assert _relerr(t.cpu().numpy().astype(np.float64), want) <= TOL[dtype]
+    plan.recompose(t)
+    torch.cuda.synchronize()
+    assert _relerr(t.cpu().numpy().astype(np.float64), u.astype(np.float64)) <= TOL[dtype]
+
+
 @pytest.mark.parametrize("shape,dtype,nlevels,nonuniform", CASES[:4])
 def test_slab_agrees_with_strip_kernels(shape, dtype, nlevels, nonuniform):
     u = synth.sinusoid_field(shape, 12, seed=4, dtype=np.float32)
@@ -111,6 +128,7 @@ def test_slab_agrees_with_strip_kernels(shape, dtype, nlevels, nonuniform):
     ((13, 2),), ((13, 3),), ((13, 8),),                   # ring slots
     ((12, 4),), ((12, 4), (11, 3), (13, 5)),              # bands of 4 rows
     ((12, 8),), ((12, 8), (15, 2)), ((15, 3),),           # bands of 8 rows; register variants
+    ((16, 1),), ((16, 1), (12, 4)), ((16, 1), (12, 8)),   # the dim-2 solve in the kernel
 ])
 def test_slab_launch_shapes(tune):
     shape = (17, 33, 257)
@@ -118,7 +136,7 @@ def test_slab_launch_shapes(tune):
     for param, value in tune:
         if param == 11:
             assert mg.mgard_plan_get_tune(plan.handle, 0, 11) == min(value, (shape[0] - 1) // 2)
-        elif param in (12, 13, 15):
+        elif param in (12, 13, 15, 16):
             assert mg.mgard_plan_get_tune(plan.handle, 0, param) == value
     u = synth.sinusoid_field(shape, 12, seed=6, dtype=np.float32)
     t = torch.from_numpy(u).cuda()
