@@ -5,8 +5,8 @@
 // mass-transfer stencil K = P^T M_l of Section III-A-2 along each dimension)
 //   F = (K_0 (x) K_1 (x) K_2) C,  C = A on N_l \ N_{l-1}, 0 on N_{l-1}
 //   V = A restricted to N_{l-1}
-// for 3D level arrays of 4-byte elements whose rows have n2 = 128 k + 1
-// nodes (NT = (n2 - 1) / 4 threads per block, k = 1 .. 8).
+// for 3D level arrays of 4-byte elements whose rows have n2 = 64 k + 1
+// nodes (m2 - 1 = (n2 - 1) / 2 threads per block, k = 1 .. 16).
 //
 // A block item is a band of TY coarse rows [Y0, Y0 + TY) over the whole row
 // width and a chunk of coarse planes [Zs, Ze).  The fine rows 2 Y0 - 2 ..
@@ -14,14 +14,15 @@
 // of the array: thread 0 copies it into a ring slot with one cp.async.bulk
 // (its 16-byte aligned cover), counted on the slot's mbarrier, up to NS - 1
 // planes ahead of their use and across item boundaries (the block knows its
-// whole item sequence).  Thread t owns coarse columns 2t and 2t + 1 (fine
-// columns 4t .. 4t + 3) and the last thread also the final column: per fine
-// row it reads the two or three 16-byte words that hold fine columns
-// 4t - 2 .. 4t + 4 from the slot (every row starts at its own offset inside
-// a word since n2 = 1 mod 4; the four offsets are compiled separately),
-// applies the dim-2 stencil, and accumulates the dim-1 stencil into TY
-// register rows; the dim-0 stencil goes into rolling register accumulators
-// over the planes of the chunk.
+// whole item sequence).  Thread t owns coarse column t: per fine row it reads
+// fine columns 2t - 2 .. 2t + 2 from the slot as three 8-byte pairs
+// (conflict-free across a warp; every row starts at its own offset since n2
+// is odd, the two pair alignments are compiled separately), applies the
+// dim-2 stencil and accumulates the dim-1 stencil into TY register rows; the
+// dim-0 stencil goes into rolling register accumulators over the planes of
+// the chunk.  The last warp also computes the final column m2 - 1 (lane j
+// its coarse row Y0 + j).  Optionally (XS) each finished coarse plane's rows
+// are solved along dim 2 before they are stored.
 //
 // A band that would pass the last coarse row is shifted back to end there;
 // its rows that the previous band owns are computed but not stored.  Every

@@ -5,7 +5,7 @@ kernels it replaces (tuning param 10 = 1 keeps it out).
 
 Every level runs the per-level kernels here (tuning param 3 = 1), so the
 slab kernel takes every 3D level with FP32 level arrays and rows of
-128 k + 1 nodes, not only the finest.  Shapes cover rows of 129, 257, 513
+64 k + 1 nodes, not only the finest.  Shapes cover rows of 129, 257, 513
 and 1025 nodes (two to sixteen warps per block), bands of 6 and of 4 coarse
 rows (a level with fewer than 6), a last band shifted back over its
 neighbour, FP32 and the mixed scheme (FP32 level 0, FP64 coarse arrays),
