@@ -131,18 +131,34 @@ cudaError_t launch_solve_chunks(const SolveParams &p, int num_sms, cudaStream_t 
     return cudaGetLastError();
 }
 
-// k_solve_strided: 16 warps (chunks of at most CH = ceil(m / 16) nodes) per
-// panel of 32 lines; CH 9, 17 or 33 (lines of up to 528 nodes; 8-byte
-// elements up to 272, where the chunks still fit the registers).
+// k_solve_strided: chunks of CH = 17 nodes (preferred), 33 (4-byte elements
+// only: 8-byte chunks of 33 do not fit the registers) or 9, nw = ceil(m / CH)
+// <= 16 warps per panel of 32 lines; the kernel needs every chunk CH - 1 or
+// CH nodes long, i.e. ceil(m / nw) = CH.  Returns 0 when no chunk length
+// fits (the caller takes another kernel), else CH and *nw_out.
 template <typename TW>
-cudaError_t launch_solve_strided(const SolveParams &p, int num_sms, cudaStream_t st)
+int solve_strided_shape(const SolveParams &p, int *nw_out)
 {
-    const int nw = std::min(kSolveStridedWarps, p.m);
-    const int ch = (p.m + nw - 1) / nw;
-    if (sizeof(TW) == 8 && ch > 17) return cudaErrorInvalidValue;  // spills: the caller takes another kernel
-    void (*fn)(SolveParams) = ch <= 9 ? k_solve_strided<TW, 9> : ch <= 17 ? k_solve_strided<TW, 17>
-                                                                             : k_solve_strided<TW, 33>;
-    if (ch > 33) return cudaErrorInvalidValue;
+    if (p.inner <= 1 || p.nlines >= (int64_t(1) << 31) || p.inner >= (int64_t(1) << 31) ||
+        (int64_t)p.m * p.stride >= (int64_t(1) << 31) || (size_t)4 * p.m * sizeof(TW) > 100 * 1024)
+        return 0;
+    static const int chs[3] = {17, 33, 9};
+    for (int ch : chs) {
+        if (sizeof(TW) == 8 && ch > 17) continue;
+        const int nw = (p.m + ch - 1) / ch;
+        if (nw >= 1 && nw <= kSolveStridedWarps && (p.m + nw - 1) / nw == ch) {
+            *nw_out = nw;
+            return ch;
+        }
+    }
+    return 0;
+}
+
+template <typename TW>
+cudaError_t launch_solve_strided(const SolveParams &p, int ch, int nw, int num_sms, cudaStream_t st)
+{
+    void (*fn)(SolveParams) = (ch == 17) ? k_solve_strided<TW, 17>
+                                         : (ch == 33) ? k_solve_strided<TW, 33> : k_solve_strided<TW, 9>;
     const size_t smem = solve_strided_elems<TW>(p.m, nw) * sizeof(TW);
     cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -174,7 +190,7 @@ cudaError_t launch_solve_lines(const SolveParams &p, int num_sms, cudaStream_t s
 }
 
 // nw_req = -1: k_solve_lines (one thread per line); nw_req = 0: along a
-// strided dimension k_solve_strided for lines up to 528 nodes, along the
+// strided dimension k_solve_strided where a chunk length fits, along the
 // contiguous one k_solve_chunks for lines up to 576 nodes (the panel staged
 // in shared memory); else (or nw_req > 0) the shared-memory panel kernel with
 // nw_req warps (0: about 16 nodes per chunk).
@@ -186,9 +202,11 @@ cudaError_t launch_solve(const SolveParams &p_in, int nw_req, int num_sms, cudaS
     const bool lines_fit = (size_t)3 * p.m * sizeof(TW) <= 100 * 1024;
     if (lines_fit && nw_req == -1) return launch_solve_lines<TW>(p, num_sms, st);
     if (nw_req < 0) nw_req = 0;
-    if (nw_req == 0 && p.inner > 1 && p.m <= (sizeof(TW) == 4 ? 33 : 17) * kSolveStridedWarps &&
-        (int64_t)p.m * p.stride < (int64_t(1) << 31) && (size_t)3 * p.m * sizeof(TW) <= 100 * 1024)
-        return launch_solve_strided<TW>(p, num_sms, st);
+    if (nw_req == 0) {
+        int snw = 0;
+        const int sch = solve_strided_shape<TW>(p, &snw);
+        if (sch > 0) return launch_solve_strided<TW>(p, sch, snw, num_sms, st);
+    }
     if (nw_req == 0 && p.m <= 32 * kSolveChunkWarps && (int64_t)p.m * p.stride < (int64_t(1) << 31)) {
         const int ch = (p.m <= 16 * kSolveChunkWarps) ? 16 : 32;
         const int nw = (p.m + ch - 1) / ch;

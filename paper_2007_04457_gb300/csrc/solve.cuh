@@ -401,17 +401,19 @@ __global__ void __launch_bounds__(32 * kSolveChunkWarps) k_solve_chunks(SolvePar
 // k_solve_strided: lines along a dimension that is not the contiguous one.
 // A block takes panels of 32 consecutive lines (lane = line: every load and
 // store of a warp touches 32 neighbouring elements), its nw warps a chunk of
-// every line each (chunk w = nodes [w m / nw, (w + 1) m / nw), at most CH),
-// held in registers together with the V values it updates.  Per sweep a warp
-// runs its chunk's recurrence from a zero carry, publishes the chunk-end
-// value, composes the carries of the chunks before it (each chunk is the
-// affine map y_out = T + P y_in, P the product of its -a_i, or of its -q_i
-// backward, tabulated per warp) and re-runs the chunk from its true carry.
-// DRAM traffic: F read once, written once (or V read and written once).
+// every line each (chunk w = nodes [w m / nw, (w + 1) m / nw), CH - 1 or CH
+// of them), held in registers together with the V values it updates.  Per
+// sweep a warp runs its chunk's recurrence from a zero carry, publishes the
+// chunk-end value, composes the carries of the chunks before it (each chunk
+// is the affine map y_out = T + P y_in, P the product of its -a_i, or of its
+// -q_i backward, tabulated per warp) and re-runs the chunk from its true
+// carry.  The factors of a node are packed (a, inv, q) in shared memory and
+// read with one vector load where they are used.  DRAM traffic: F read once,
+// written once (or V read and written once).
 template <typename TW>
 inline size_t solve_strided_elems(int m, int nw)
 {
-    return 3 * (size_t)m + 2 * (size_t)nw + 2 * 32 * (size_t)nw;
+    return 4 * (size_t)m + 2 * (size_t)nw + 2 * 32 * (size_t)nw;
 }
 
 constexpr int kSolveStridedWarps = 16;
@@ -423,14 +425,32 @@ struct StridedMinBlocks {
     static constexpr int value = (sizeof(TW) == 4 && CH <= 17) ? 2 : 1;
 };
 
+// (a, inv, q) of one node from its packed shared-memory entry, loaded where
+// it is used (an asm load: the compiler keeps no copy in registers)
+__device__ __forceinline__ void solve_fac(const float *e, float &a, float &inv, float &q)
+{
+    float pad;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(a), "=f"(inv), "=f"(q), "=f"(pad)
+                 : "r"(static_cast<unsigned>(__cvta_generic_to_shared(e))));
+}
+
+__device__ __forceinline__ void solve_fac(const double *e, double &a, double &inv, double &q)
+{
+    double pad;
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(e));
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(inv) : "r"(s));
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(q), "=d"(pad) : "r"(s + 16));
+}
+
 template <typename TW, int CH>
 __global__ void __launch_bounds__(32 * kSolveStridedWarps, StridedMinBlocks<TW, CH>::value) k_solve_strided(SolveParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int m = p.m;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    TW *sfac = reinterpret_cast<TW *>(smem_raw);  // (a, inv, q) per node
-    TW *Pw = sfac + 3 * m;                         // per chunk: product of -a_i
+    TW *sfac = reinterpret_cast<TW *>(smem_raw);  // (a, inv, q, 0) per node
+    TW *Pw = sfac + 4 * m;                         // per chunk: product of -a_i
     TW *Qw = Pw + nw;                              // per chunk: product of -q_i
     TW *ca = Qw + nw;                              // forward chunk-end values [nw][32]
     TW *cb = ca + 32 * nw;                         // backward chunk-start values [nw][32]
@@ -438,44 +458,56 @@ __global__ void __launch_bounds__(32 * kSolveStridedWarps, StridedMinBlocks<TW, 
     TW *F = static_cast<TW *>(p.F);
     TW *V = static_cast<TW *>(p.V);
     const TW *in = p.src ? static_cast<const TW *>(p.src) : F;
-    for (int i = threadIdx.x; i < 3 * m; i += blockDim.x) sfac[i] = fac[i];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        sfac[4 * i] = fac[3 * i];
+        sfac[4 * i + 1] = fac[3 * i + 1];
+        sfac[4 * i + 2] = fac[3 * i + 2];
+        sfac[4 * i + 3] = TW(0);
+    }
     __syncthreads();
-    const int s = (w * m) / nw, len = ((w + 1) * m) / nw - s;
+    const int s = (w * m) / nw, len = ((w + 1) * m) / nw - s;  // len is CH - 1 or CH
     if (lane == 0) {
         TW pa = TW(1), pq = TW(1);
         for (int j = 0; j < len; ++j) {
-            pa = -sfac[3 * (s + j)] * pa;
-            pq = -sfac[3 * (s + j) + 2] * pq;
+            pa = -sfac[4 * (s + j)] * pa;
+            pq = -sfac[4 * (s + j) + 2] * pq;
         }
         Pw[w] = pa;
         Qw[w] = pq;
     }
     __syncthreads();
-    const int64_t inner = p.inner;
-    const int stride = (int)p.stride;  // a line spans m * stride < 2^31 elements (checked by the launcher)
-    const int64_t npanels = (p.nlines + 31) / 32;
+    const TW *sf = sfac + 4 * s;
+    const bool full = (len == CH);  // the chunk's last register holds a node
+    // line -> first element: lines are (outer, inner) pairs, inner fastest;
+    // 32-bit arithmetic (the launcher checks that every index fits)
+    const unsigned inner = (unsigned)p.inner, nlines = (unsigned)p.nlines;
+    const int stride = (int)p.stride;
+    const unsigned npanels = (nlines + 31) / 32;
     const TW sg = (p.vmode == 2) ? TW(-1) : TW(1);
-    // the factors are read where they are used (one broadcast load each),
-    // not kept in registers: the chunk and its V values need them
-    const volatile TW *vfac = sfac;
-    for (int64_t panel = blockIdx.x; panel < npanels; panel += gridDim.x) {
-        const int64_t line = panel * 32 + lane;
-        const bool lv = line < p.nlines;
-        const int64_t base = lv ? (line / inner) * (inner * m) + line % inner + (int64_t)s * stride : 0;
+    for (unsigned panel = blockIdx.x; panel < npanels; panel += gridDim.x) {
+        const unsigned line = panel * 32 + lane;
+        const bool lv = line < nlines;
+        const unsigned ln = lv ? line : nlines - 1;  // lanes past the end read the last line, store nothing
+        const unsigned outer = (nlines <= inner) ? 0u : ln / inner;
+        const int64_t base = (int64_t)outer * inner * m + (ln - outer * inner) + (int64_t)s * stride;
         const TW *fin = in + base;
         TW y[CH], vv[CH];
 #pragma unroll
-        for (int j = 0; j < CH; ++j) y[j] = (j < len && lv) ? fin[j * stride] : TW(0);
+        for (int j = 0; j < CH; ++j) y[j] = (j < CH - 1 || full) ? fin[j * stride] : TW(0);
         if (p.vmode != 0) {
             const TW *vin = V + base;
 #pragma unroll
-            for (int j = 0; j < CH; ++j) vv[j] = (j < len && lv) ? vin[j * stride] : TW(0);
+            for (int j = 0; j < CH; ++j) vv[j] = (j < CH - 1 || full) ? vin[j * stride] : TW(0);
         }
+        TW a, inv, q;
         // forward y_i = f_i - a_i y_{i-1}: chunk-end value from a zero carry
         TW t = TW(0);
 #pragma unroll
         for (int j = 0; j < CH; ++j)
-            if (j < len) t = y[j] - vfac[3 * (s + j)] * t;
+            if (j < CH - 1 || full) {
+                solve_fac(sf + 4 * j, a, inv, q);
+                t = y[j] - a * t;
+            }
         ca[w * 32 + lane] = t;
         __syncthreads();
         TW c = TW(0);
@@ -483,15 +515,19 @@ __global__ void __launch_bounds__(32 * kSolveStridedWarps, StridedMinBlocks<TW, 
         t = c;
 #pragma unroll
         for (int j = 0; j < CH; ++j)
-            if (j < len) {
-                t = y[j] - vfac[3 * (s + j)] * t;
+            if (j < CH - 1 || full) {
+                solve_fac(sf + 4 * j, a, inv, q);
+                t = y[j] - a * t;
                 y[j] = t;
             }
         // backward z_i = inv_i y_i - q_i z_{i+1}: chunk-start value from a zero carry
         t = TW(0);
 #pragma unroll
         for (int j = CH - 1; j >= 0; --j)
-            if (j < len) t = vfac[3 * (s + j) + 1] * y[j] - vfac[3 * (s + j) + 2] * t;
+            if (j < CH - 1 || full) {
+                solve_fac(sf + 4 * j, a, inv, q);
+                t = inv * y[j] - q * t;
+            }
         cb[w * 32 + lane] = t;
         __syncthreads();
         c = TW(0);
@@ -499,8 +535,9 @@ __global__ void __launch_bounds__(32 * kSolveStridedWarps, StridedMinBlocks<TW, 
         t = c;
 #pragma unroll
         for (int j = CH - 1; j >= 0; --j)
-            if (j < len) {
-                t = vfac[3 * (s + j) + 1] * y[j] - vfac[3 * (s + j) + 2] * t;
+            if (j < CH - 1 || full) {
+                solve_fac(sf + 4 * j, a, inv, q);
+                t = inv * y[j] - q * t;
                 y[j] = t;
             }
         // z into F, or V +- z
@@ -508,7 +545,7 @@ __global__ void __launch_bounds__(32 * kSolveStridedWarps, StridedMinBlocks<TW, 
             TW *dst = ((p.vmode == 0) ? F : V) + base;
 #pragma unroll
             for (int j = 0; j < CH; ++j)
-                if (j < len) dst[j * stride] = (p.vmode == 0) ? y[j] : vv[j] + sg * y[j];
+                if (j < CH - 1 || full) dst[j * stride] = (p.vmode == 0) ? y[j] : vv[j] + sg * y[j];
         }
         __syncthreads();  // the carries are reused by the next panel
     }
