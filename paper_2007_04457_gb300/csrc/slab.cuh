@@ -70,6 +70,13 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
                  : "memory");
 }
 
+// one arrival (release: the caller's earlier shared-memory accesses are
+// ordered before it)
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
 {
     unsigned ok;
@@ -121,7 +128,7 @@ __device__ __forceinline__ void slab_for(Fn &&f)
     }
 }
 
-constexpr int kSlabBarBytes = 128;  // ring barriers, ahead of the slots
+constexpr int kSlabBarBytes = 256;  // ring barriers (full, then empty), ahead of the slots
 
 template <int TY>
 struct SlabGeom {
@@ -395,9 +402,17 @@ __global__ void __launch_bounds__(MAXT, MINB) k_slab(SlabParams p)
         xi = fx[3 * (m2 - 1) + 1];
     }
 
+    // full[s] = bars[s] (the producer's arrival + the copy's bytes); empty[s]
+    // = bars[NS + s] (one arrival per warp once it is done with the slot)
+    __shared__ volatile int s_dead;  // a wait ran out: every warp leaves its loop
+    const int nwarps = (int)(blockDim.x >> 5);
     if (t == 0) {
-        for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&bars[s], 1);
+            mbar_init(&bars[NS + s], (unsigned)nwarps);
+        }
         mbar_init_fence();
+        s_dead = 0;
     }
     __syncthreads();
 
@@ -420,6 +435,13 @@ __global__ void __launch_bounds__(MAXT, MINB) k_slab(SlabParams p)
     auto issue_next = [&]() {
         if (p_item >= p.nitems) return;
         const int s = p_pos % NS;
+        if constexpr (!XS) {
+            // the slot's previous use must be released by every warp
+            if (p_pos >= NS && !mbar_wait(&bars[NS + s], (unsigned)((p_pos / NS - 1) & 1), p.wait_ns)) {
+                s_dead = 1;
+                return;
+            }
+        }
         slab_issue<TY>(A, plane, n1, n2, p_z, p_it.Y0, ring + (size_t)s * SB, &bars[s],
                        (p.hook && p_pos == 0) ? 16u : 0u);
         ++p_pos;
@@ -541,14 +563,28 @@ __global__ void __launch_bounds__(MAXT, MINB) k_slab(SlabParams p)
                 eP = eC;
                 eC = eN;
             }
-            // every thread is done with slot s (and agrees on whether a wait
-            // ran out) before it is refilled
-            if (__syncthreads_or(!ok)) {
-                dead = true;
-                break;
+            if constexpr (XS) {
+                // every thread is done with slot s (and agrees on whether a
+                // wait ran out) before it is refilled
+                if (__syncthreads_or(!ok)) {
+                    dead = true;
+                    break;
+                }
+                if (t == 0) issue_next();
+                solve_pending();  // the rows stored before this barrier
+            } else {
+                // the warp releases slot s; thread 0 refills the slot of the
+                // position NS ahead once every warp has released it, while
+                // the other warps go on with the next staged plane
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars[NS + s]);
+                if (!ok) s_dead = 1;
+                if (t == 0 && !s_dead) issue_next();
+                if (s_dead) {
+                    dead = true;
+                    break;
+                }
             }
-            if (t == 0) issue_next();
-            solve_pending();  // the rows stored before this barrier
         }
         // the last coarse plane of the grid has no contributions beyond it
         // (after the final shift it is in accP)
@@ -560,13 +596,26 @@ __global__ void __launch_bounds__(MAXT, MINB) k_slab(SlabParams p)
             }
         }
     }
-    if (dead) {
-        // record it, then let the copies this block issued (from the one
-        // whose wait ran out on) land, bounded, before its shared memory goes
-        // away
-        if (t == 0) {
+    if constexpr (XS) {
+        if (dead) {
+            // record it, then let the copies this block issued (from the one
+            // whose wait ran out on) land, bounded, before its shared memory
+            // goes away
+            if (t == 0) {
+                atomicOr(p.status, 1u);
+                for (int e = pos; e < p_pos; ++e) (void)mbar_wait(&bars[e % NS], (unsigned)((e / NS) & 1), p.wait_ns);
+            }
+            __syncthreads();
+        }
+    } else {
+        // the warps leave their loops independently; a block where a wait ran
+        // out records it and lets the copies it issued last (one per slot;
+        // earlier ones were consumed) land, bounded, before its shared memory
+        // goes away
+        if (t == 0 && s_dead) {
             atomicOr(p.status, 1u);
-            for (int e = pos; e < p_pos; ++e) (void)mbar_wait(&bars[e % NS], (unsigned)((e / NS) & 1), p.wait_ns);
+            for (int e = max(0, p_pos - NS); e < p_pos; ++e)
+                (void)mbar_wait(&bars[e % NS], (unsigned)((e / NS) & 1), p.wait_ns);
         }
         __syncthreads();
     }
