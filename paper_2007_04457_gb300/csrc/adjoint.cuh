@@ -30,6 +30,7 @@ constexpr int kAdjThreads = 256;
 template <typename T, typename TW, int ACT>
 __global__ void __launch_bounds__(kAdjThreads) k_gather(PlaceParams p)
 {
+    pdl_wait();  // programmatic dependent launch: the predecessor has finished
     constexpr bool HZ = (ACT & 4) != 0, HY = (ACT & 2) != 0;
     const T *__restrict__ A = static_cast<const T *>(p.A);
     TW *__restrict__ V = const_cast<TW *>(static_cast<const TW *>(p.V));
@@ -67,6 +68,7 @@ __device__ __forceinline__ int kt_support(int64_t j, int64_t m, const TW *k, int
 template <typename T, typename TW, int ACT>
 __global__ void __launch_bounds__(kAdjThreads) k_adj_odd(AdjParams p)
 {
+    pdl_wait();  // programmatic dependent launch: the predecessor has finished
     constexpr bool HZ = (ACT & 4) != 0, HY = (ACT & 2) != 0;
     T *__restrict__ A = static_cast<T *>(p.A);
     const TW *__restrict__ Z = static_cast<const TW *>(p.Z);
@@ -123,6 +125,7 @@ __device__ __forceinline__ int pt_support(int64_t E, int64_t n, const T *w, int6
 template <typename T, typename TW, int ACT>
 __global__ void __launch_bounds__(kAdjThreads) k_adj_even(AdjParams p)
 {
+    pdl_wait();  // programmatic dependent launch: the predecessor has finished
     constexpr bool HZ = (ACT & 4) != 0, HY = (ACT & 2) != 0;
     T *__restrict__ A = static_cast<T *>(p.A);
     const TW *__restrict__ B = static_cast<const TW *>(p.Z);  // compact base, or null: A itself
@@ -187,6 +190,7 @@ __device__ __forceinline__ void kt_pair(int64_t P, int64_t m, const TW *k, TW (&
 template <typename T, typename TW, int ACT>
 __global__ void __launch_bounds__(32 * kAdj2Warps) k_adj_odd2(AdjParams p)
 {
+    pdl_wait();  // programmatic dependent launch: the predecessor has finished
     constexpr bool HZ = (ACT & 4) != 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *__restrict__ A = static_cast<T *>(p.A);
@@ -281,6 +285,7 @@ __global__ void __launch_bounds__(32 * kAdj2Warps) k_adj_odd2(AdjParams p)
 template <typename T, typename TW, int ACT>
 __global__ void __launch_bounds__(32 * kAdj2Warps) k_adj_even2(AdjParams p)
 {
+    pdl_wait();  // programmatic dependent launch: the predecessor has finished
     constexpr bool HZ = (ACT & 4) != 0;
     T *__restrict__ A = static_cast<T *>(p.A);
     const TW *__restrict__ B = static_cast<const TW *>(p.Z);  // compact base, or null: A itself

@@ -90,6 +90,17 @@ __device__ __forceinline__ T lerp2(T wl, T a, T wr, T b)
     return fma_rn(wl, a, mul_rn(wr, b));
 }
 
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream-serialization attribute (launch_pdl) is scheduled as the blocks of
+// its predecessor on the stream exit, so its launch and first blocks overlap
+// the predecessor's last wave: pdl_wait() returns once the predecessor has
+// completed and its memory operations are visible (at once for a kernel
+// launched without the attribute), so every such kernel calls it before
+// touching memory its predecessor writes or reads.  (An explicit early
+// trigger, which lets the successor's blocks wait on the SMs from the start,
+// measured slower.)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 // Streaming (evict-first) global store for data that is not read again soon.
 template <typename T>
 __device__ __forceinline__ void st_stream(T *p, T v)

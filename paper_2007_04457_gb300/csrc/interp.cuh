@@ -40,6 +40,7 @@ constexpr int kScatterWarps = 8;
 template <typename T, typename TW, int ACT>
 __global__ void __launch_bounds__(32 * kScatterWarps) k_scatter(PlaceParams p)
 {
+    pdl_wait();
     constexpr bool HZ = (ACT & 4) != 0, HY = (ACT & 2) != 0;
     T *A = static_cast<T *>(p.A);
     const TW *__restrict__ V = static_cast<const TW *>(p.V);

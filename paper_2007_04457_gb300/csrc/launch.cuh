@@ -11,6 +11,25 @@
 
 namespace mg {
 
+// Launch with programmatic dependent launch allowed: the kernel may start
+// while its predecessor on the stream finishes, so it must call pdl_wait()
+// (common.cuh) before it touches memory the predecessor writes or reads.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, args...);
+}
+
 // Tile shapes of the load-vector kernel selectable per level (coarse nodes in
 // dims 1 x 2; a last tile absorbs the final node of a dimension):
 //   2D/3D: cfg 0 = 8 x 64, cfg 1 = 4 x 64, cfg 2 = 16 x 64 (a block per tile),

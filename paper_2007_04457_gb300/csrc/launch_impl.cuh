@@ -103,7 +103,7 @@ cudaError_t launch_restrict(int act, int mode, int cfg, const RestrictParams &p,
     (void)mode;
     detail::RestrictEntry e;
     if (!detail::restrict_pick<T, TW>(act, cfg, &e)) return cudaErrorInvalidValue;
-    e.fn<<<grid, kRestrictThreads, e.smem, st>>>(p);
+    { const cudaError_t le = launch_pdl(e.fn, dim3(grid), dim3(kRestrictThreads), e.smem, st, p); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 
@@ -127,8 +127,7 @@ cudaError_t launch_solve_chunks(const SolveParams &p, int num_sms, cudaStream_t 
     if (err != cudaSuccess) return err;
     const int64_t panels = (p.nlines + 31) / 32;
     const int64_t grid = std::min<int64_t>(panels, (int64_t)std::max(1, bps) * num_sms);
-    fn<<<(unsigned)grid, dim3(32, nw), smem, st>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(fn, dim3((unsigned)grid), dim3(32, nw), smem, st, p);
 }
 
 // k_solve_strided: chunks of CH = 17 nodes (preferred), 33 (4-byte elements
@@ -168,8 +167,7 @@ cudaError_t launch_solve_strided(const SolveParams &p, int ch, int nw, int num_s
     if (err != cudaSuccess) return err;
     const int64_t panels = (p.nlines + 31) / 32;
     const int64_t grid = std::min<int64_t>(panels, (int64_t)std::max(1, bps) * num_sms);
-    fn<<<(unsigned)grid, 32 * nw, smem, st>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(fn, dim3((unsigned)grid), dim3(32 * nw), smem, st, p);
 }
 
 // k_solve_lines: one thread per line, the factors of the line in shared memory.
@@ -185,7 +183,7 @@ cudaError_t launch_solve_lines(const SolveParams &p, int num_sms, cudaStream_t s
     if (err != cudaSuccess) return err;
     const int64_t blocks = (p.nlines + kSolveLineThreads - 1) / kSolveLineThreads;
     const int64_t grid = std::min<int64_t>(blocks, (int64_t)std::max(1, bps) * num_sms);
-    k_solve_lines<TW><<<(unsigned)grid, kSolveLineThreads, smem, st>>>(p);
+    { const cudaError_t le = launch_pdl(k_solve_lines<TW>, dim3((unsigned)grid), dim3(kSolveLineThreads), smem, st, p); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 
@@ -234,7 +232,7 @@ cudaError_t launch_solve(const SolveParams &p_in, int nw_req, int num_sms, cudaS
         attr_set[which] = true;
     }
     const int64_t panels = (p.nlines + lpb - 1) / lpb;
-    fn<<<(unsigned)std::min<int64_t>(panels, 1 << 30), dim3(32, nw), smem, st>>>(p);
+    { const cudaError_t le = launch_pdl(fn, dim3((unsigned)std::min<int64_t>(panels, 1 << 30)), dim3(32, nw), smem, st, p); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 
@@ -294,8 +292,8 @@ cudaError_t launch_sweep2(int act, PlaceParams p, int num_sms, cudaStream_t st)
     }
     const int64_t items = tiles * p.nzc;
     const int64_t blocks = std::min<int64_t>((items + kSweepWarps - 1) / kSweepWarps, 1 << 30);
-    if (act == ACT_3D) k_sweep2<T, TW, ACT_3D><<<(unsigned)blocks, 32 * kSweepWarps, 0, st>>>(p);
-    else k_sweep2<T, TW, ACT_2D><<<(unsigned)blocks, 32 * kSweepWarps, 0, st>>>(p);
+    if (act == ACT_3D) { const cudaError_t le = launch_pdl(k_sweep2<T, TW, ACT_3D>, dim3((unsigned)blocks), dim3(32 * kSweepWarps), 0, st, p); if (le != cudaSuccess) return le; }
+    else { const cudaError_t le = launch_pdl(k_sweep2<T, TW, ACT_2D>, dim3((unsigned)blocks), dim3(32 * kSweepWarps), 0, st, p); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 
@@ -308,9 +306,9 @@ cudaError_t launch_sweep(int act, PlaceParams p, int num_sms, cudaStream_t st)
     const int64_t items = ((p.n2 + 31) / 32) * ((act & 2) ? (p.n1 + R - 1) / R : 1) * p.nzc;
     const int64_t blocks = std::min<int64_t>((items + kSweepWarps - 1) / kSweepWarps, 1 << 30);
     switch (act) {
-    case ACT_1D: k_sweep<T, TW, ACT_1D, MODE><<<(unsigned)blocks, 32 * kSweepWarps, 0, st>>>(p); break;
-    case ACT_2D: k_sweep<T, TW, ACT_2D, MODE><<<(unsigned)blocks, 32 * kSweepWarps, 0, st>>>(p); break;
-    case ACT_3D: k_sweep<T, TW, ACT_3D, MODE><<<(unsigned)blocks, 32 * kSweepWarps, 0, st>>>(p); break;
+    case ACT_1D: return launch_pdl(k_sweep<T, TW, ACT_1D, MODE>, dim3((unsigned)blocks), dim3(32 * kSweepWarps), 0, st, p);
+    case ACT_2D: return launch_pdl(k_sweep<T, TW, ACT_2D, MODE>, dim3((unsigned)blocks), dim3(32 * kSweepWarps), 0, st, p);
+    case ACT_3D: return launch_pdl(k_sweep<T, TW, ACT_3D, MODE>, dim3((unsigned)blocks), dim3(32 * kSweepWarps), 0, st, p);
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -331,9 +329,9 @@ cudaError_t launch_scatter(int act, const PlaceParams &p, cudaStream_t st)
     const int64_t blocks = std::min<int64_t>((rows + kScatterWarps - 1) / kScatterWarps, 1 << 20);
     const dim3 g((unsigned)blocks), b(32 * kScatterWarps);
     switch (act) {
-    case ACT_1D: k_scatter<T, TW, ACT_1D><<<g, b, 0, st>>>(p); break;
-    case ACT_2D: k_scatter<T, TW, ACT_2D><<<g, b, 0, st>>>(p); break;
-    case ACT_3D: k_scatter<T, TW, ACT_3D><<<g, b, 0, st>>>(p); break;
+    case ACT_1D: return launch_pdl(k_scatter<T, TW, ACT_1D>, g, b, 0, st, p);
+    case ACT_2D: return launch_pdl(k_scatter<T, TW, ACT_2D>, g, b, 0, st, p);
+    case ACT_3D: return launch_pdl(k_scatter<T, TW, ACT_3D>, g, b, 0, st, p);
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -347,9 +345,9 @@ cudaError_t launch_interp(int act, const PlaceParams &p, int num_sms, cudaStream
 
 #define MG_ACT_SWITCH(KERNEL, G, B, P)                                          \
     switch (act) {                                                             \
-    case ACT_1D: KERNEL<T, TW, ACT_1D><<<G, B, 0, st>>>(P); break;             \
-    case ACT_2D: KERNEL<T, TW, ACT_2D><<<G, B, 0, st>>>(P); break;             \
-    case ACT_3D: KERNEL<T, TW, ACT_3D><<<G, B, 0, st>>>(P); break;             \
+    case ACT_1D: return launch_pdl(KERNEL<T, TW, ACT_1D>, G, B, 0, st, P);     \
+    case ACT_2D: return launch_pdl(KERNEL<T, TW, ACT_2D>, G, B, 0, st, P);     \
+    case ACT_3D: return launch_pdl(KERNEL<T, TW, ACT_3D>, G, B, 0, st, P);     \
     default: return cudaErrorInvalidValue;                                     \
     }
 
@@ -373,7 +371,7 @@ cudaError_t launch_adj_odd(int act, const AdjParams &p, cudaStream_t st)
         if (err != cudaSuccess) return err;
         const int64_t items = ((act == ACT_3D) ? (p.n0 + 1) / 2 : 1) * ((p.n1 + 1) / 2);
         const int64_t blocks = std::min<int64_t>((items + kAdj2Warps - 1) / kAdj2Warps, int64_t(1) << 30);
-        fn<<<(unsigned)blocks, 32 * kAdj2Warps, smem2, st>>>(p);
+        { const cudaError_t le = launch_pdl(fn, dim3((unsigned)blocks), dim3(32 * kAdj2Warps), smem2, st, p); if (le != cudaSuccess) return le; }
         return cudaGetLastError();
     }
     dim3 g, b;
@@ -388,8 +386,8 @@ cudaError_t launch_adj_even(int act, const AdjParams &p, cudaStream_t st)
     if (act != ACT_1D) {
         const int64_t items = p.m0 * p.m1;
         const int64_t blocks = std::min<int64_t>((items + kAdj2Warps - 1) / kAdj2Warps, int64_t(1) << 30);
-        if (act == ACT_3D) k_adj_even2<T, TW, ACT_3D><<<(unsigned)blocks, 32 * kAdj2Warps, 0, st>>>(p);
-        else k_adj_even2<T, TW, ACT_2D><<<(unsigned)blocks, 32 * kAdj2Warps, 0, st>>>(p);
+        if (act == ACT_3D) { const cudaError_t le = launch_pdl(k_adj_even2<T, TW, ACT_3D>, dim3((unsigned)blocks), dim3(32 * kAdj2Warps), 0, st, p); if (le != cudaSuccess) return le; }
+        else { const cudaError_t le = launch_pdl(k_adj_even2<T, TW, ACT_2D>, dim3((unsigned)blocks), dim3(32 * kAdj2Warps), 0, st, p); if (le != cudaSuccess) return le; }
         return cudaGetLastError();
     }
     dim3 g, b;
@@ -405,7 +403,7 @@ cudaError_t launch_small(int mode, const SmallParams &p, size_t smem, cudaStream
     cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    fn<<<1, kSmallThreads, smem, st>>>(p);
+    { const cudaError_t le = launch_pdl(fn, dim3(1), dim3(kSmallThreads), smem, st, p); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 
@@ -416,7 +414,7 @@ cudaError_t launch_small_adj(int dir, const SmallParams &p, size_t smem, cudaStr
     cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    fn<<<1, kSmallThreads, smem, st>>>(p);
+    { const cudaError_t le = launch_pdl(fn, dim3(1), dim3(kSmallThreads), smem, st, p); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 
@@ -469,7 +467,7 @@ cudaError_t launch_prolong(const ProlongParams &p, int num_sms, cudaStream_t st)
     if (items >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
     const int64_t need = (items + kProlongThreads / 32 - 1) / (kProlongThreads / 32);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms * per_sm));
-    k_prolong<T, TW><<<(unsigned)grid, kProlongThreads, 0, st>>>(q);
+    { const cudaError_t le = launch_pdl(k_prolong<T, TW>, dim3((unsigned)grid), dim3(kProlongThreads), 0, st, q); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 

@@ -36,6 +36,7 @@ constexpr int kProlongRows = 64;   // finest rows (dim 1) per work item
 template <typename T, typename TW>
 __global__ void __launch_bounds__(kProlongThreads, sizeof(TW) == 4 ? kProlongBlocksPerSm : 5) k_prolong(ProlongParams p)
 {
+    pdl_wait();  // programmatic dependent launch: the predecessor has finished
     T *__restrict__ out = static_cast<T *>(p.out);
     const TW *__restrict__ V = static_cast<const TW *>(p.V);
     const TW *__restrict__ w0 = static_cast<const TW *>(p.w0);

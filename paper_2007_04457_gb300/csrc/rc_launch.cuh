@@ -106,8 +106,7 @@ cudaError_t launch_rc(int kind, int Q, int mode, bool hz, bool u, bool xs, const
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
     }
-    fn<<<grid, 32 * kRcWarps, smem, st>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(fn, dim3(grid), dim3(32 * kRcWarps), smem, st, p);
 }
 
 #define MG_INSTANTIATE_RC(T, TW)                                                                            \

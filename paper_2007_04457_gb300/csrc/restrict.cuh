@@ -125,6 +125,7 @@ template <typename T, typename TW, int ACT, int TY_>
 __global__ void __launch_bounds__(kRestrictThreads, (restrict_min_blocks<T, TY_>()))
 k_restrict(RestrictParams p)
 {
+    pdl_wait();  // programmatic dependent launch: the predecessor has finished
     using G = RestrictGeom<T, ACT, TY_>;
     constexpr bool HZ = G::HZ, HY = G::HY;
     constexpr int TY = G::TY, RYM = G::RYM, SP = G::SP, HP = G::HP;
@@ -384,6 +385,7 @@ k_restrict(RestrictParams p)
 template <typename T, typename TW>
 __global__ void __launch_bounds__(256) k_restrict1d(RestrictParams p)
 {
+    pdl_wait();  // programmatic dependent launch: the predecessor has finished
     const T *__restrict__ A = static_cast<const T *>(p.A);
     TW *__restrict__ F = static_cast<TW *>(p.F);
     TW *__restrict__ V = static_cast<TW *>(p.V);

@@ -123,6 +123,7 @@ __device__ __forceinline__ void strip_plane(const T *__restrict__ plane, int n1,
 template <typename T, typename TW, bool HZ>
 __global__ void __launch_bounds__(kStripThreads, 2) k_restrict_strip(RestrictParams p)
 {
+    pdl_wait();  // programmatic dependent launch: the predecessor has finished
     constexpr int TY = StripRows<T>::value;
     const T *__restrict__ A = static_cast<const T *>(p.A);
     TW *__restrict__ F = static_cast<TW *>(p.F);

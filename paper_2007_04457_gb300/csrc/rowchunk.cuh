@@ -387,6 +387,7 @@ __global__ void __launch_bounds__(32 * kRcWarps) k_rc_sweep(RcParams p)
     const int L = threadIdx.x & 31;
     const int n1 = p.n1, n2 = p.n2, m0 = p.m0, m1 = p.m1, m2 = p.m2, S = p.S;
     const int64_t plane = (int64_t)n1 * n2;
+    pdl_wait();
 
     for (int item = blockIdx.x * kRcWarps + (threadIdx.x >> 5); item < p.nitems; item += gridDim.x * kRcWarps) {
         const int s = item % S;
@@ -663,6 +664,7 @@ inline size_t rc_restrict_smem(int S, bool ku, bool xs)
 template <typename T, typename TW, int Q, bool HZ, bool KU, bool XS, int TY>
 __global__ void __launch_bounds__(32 * kRcWarps) k_rc_restrict(RcParams p)
 {
+    pdl_wait();
     constexpr int E = VecE<T>::value, W = 32 * E, NC = E / 2, WC = 32 * NC;
     constexpr int C2 = NC * Q;      // coarse nodes per lane and segment
     constexpr int NR = 2 * TY + 3;  // fine rows feeding TY coarse rows

@@ -78,8 +78,7 @@ cudaError_t launch_slab(int ty, int minb, bool xs, const SlabParams &p, int grid
     cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    fn<<<grid, (p.n2 - 1) / 2, smem, st>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(fn, dim3(grid), dim3((p.n2 - 1) / 2), smem, st, p);
 }
 
 template cudaError_t slab_occupancy<float>(int, int, int, int, bool, int *);

@@ -453,6 +453,9 @@ __global__ void __launch_bounds__(MAXT, MINB) k_slab(SlabParams p)
             }
         }
     };
+    // the predecessor on the stream (programmatic dependent launch) has
+    // finished with the level array, F and V
+    pdl_wait();
     if (t == 0)
         for (int s = 0; s < NS; ++s) issue_next();
 

@@ -510,6 +510,7 @@ __device__ void small_adj_run(const SmallParams &p, unsigned char *smem_raw)
 template <typename T, typename TW, int DIR>
 __global__ void __launch_bounds__(kSmallThreads, 1) k_small_adj(SmallParams p)
 {
+    pdl_wait();  // programmatic dependent launch: the predecessor has finished
     extern __shared__ __align__(16) unsigned char smem_raw[];
     small_adj_run<T, TW, DIR>(p, smem_raw);
 }
@@ -517,6 +518,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_adj(SmallParams p)
 template <typename T, typename TW, int MODE>
 __global__ void __launch_bounds__(kSmallThreads, 1) k_small(SmallParams p)
 {
+    pdl_wait();  // programmatic dependent launch: the predecessor has finished
     extern __shared__ __align__(16) unsigned char smem_raw[];
     small_run<T, TW, MODE>(p, smem_raw);
 }

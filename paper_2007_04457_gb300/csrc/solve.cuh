@@ -139,6 +139,7 @@ constexpr int kSolveRegWarps = 18;
 template <typename TW, int CH>
 __global__ void __launch_bounds__(CH > 0 ? 32 * kSolveRegWarps : 1024, 2) k_solve_panel(SolveParams p)
 {
+    pdl_wait();  // programmatic dependent launch: the predecessor has finished
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TW *carry_a = reinterpret_cast<TW *>(smem_raw);
     TW *carry_b = carry_a + 32 * 32;
@@ -312,6 +313,7 @@ __global__ void __launch_bounds__(32 * kSolveChunkWarps) k_solve_chunks(SolvePar
     };
 
     int buf = 0;
+    pdl_wait();  // the predecessor on the stream has finished with F and V
     stage(blockIdx.x, 0);
     cp_async_commit();
     __syncthreads();  // Pf, Qb ready
@@ -478,6 +480,7 @@ __global__ void __launch_bounds__(32 * kSolveStridedWarps, StridedMinBlocks<TW, 
     __syncthreads();
     const TW *sf = sfac + 4 * s;
     const bool full = (len == CH);  // the chunk's last register holds a node
+    pdl_wait();  // the predecessor on the stream has finished with F and V
     // line -> first element: lines are (outer, inner) pairs, inner fastest;
     // 32-bit arithmetic (the launcher checks that every index fits)
     const unsigned inner = (unsigned)p.inner, nlines = (unsigned)p.nlines;
@@ -573,6 +576,7 @@ struct LineUnroll {
 template <typename TW>
 __global__ void __launch_bounds__(kSolveLineThreads) k_solve_lines(SolveParams p)
 {
+    pdl_wait();  // programmatic dependent launch: the predecessor has finished
     constexpr int U = LineUnroll<TW>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TW *tab = reinterpret_cast<TW *>(smem_raw);

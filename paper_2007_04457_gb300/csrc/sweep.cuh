@@ -54,6 +54,7 @@ template <typename T, typename TW, int ACT, int MODE>
 __global__ void __launch_bounds__(32 * kSweepWarps, (SweepMinBlocks<(int)sizeof(T), MODE>::value))
 k_sweep(PlaceParams p)
 {
+    pdl_wait();  // programmatic dependent launch: the predecessor has finished
     constexpr bool HZ = (ACT & 4) != 0, HY = (ACT & 2) != 0;
     constexpr bool DEC = (MODE == MODE_DEC);
     constexpr int R = SweepRows<ACT, (int)sizeof(T)>::value;
@@ -238,6 +239,7 @@ constexpr int kSweep2Blocks = 3;     // resident blocks the registers are sized 
 template <typename T, typename TW, int ACT>
 __global__ void __launch_bounds__(32 * kSweepWarps, kSweep2Blocks) k_sweep2(PlaceParams p)
 {
+    pdl_wait();  // programmatic dependent launch: the predecessor has finished
     constexpr bool HZ = (ACT & 4) != 0;
     constexpr int R = 8;           // fine rows per item
     constexpr int RE = R / 2 + 1;  // even rows with the halo row
