@@ -445,40 +445,112 @@ __device__ __forceinline__ void solve_fac(const double *e, double &a, double &in
     asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(q), "=d"(pad) : "r"(s + 16));
 }
 
+// Shared memory of the chunked solves: the packed factors (4 m), the chunk
+// products Pw, Qw (nw each) and the carries ca, cb (32 nw each), in TW.
+template <typename TW>
+struct ChunkSmem {
+    TW *sfac, *Pw, *Qw, *ca, *cb;
+};
+
+// Packs the factors of the line's nodes as (a, inv, q, 0) and tabulates each
+// chunk's products of its -a_i and -q_i; chunk w = nodes [w m / nw,
+// (w + 1) m / nw).  Reads only the plan's factor table.
+template <typename TW>
+__device__ __forceinline__ ChunkSmem<TW> chunk_setup(unsigned char *smem_raw, const TW *fac, int m, int w, int nw,
+                                                     int lane)
+{
+    ChunkSmem<TW> c;
+    c.sfac = reinterpret_cast<TW *>(smem_raw);
+    c.Pw = c.sfac + 4 * m;
+    c.Qw = c.Pw + nw;
+    c.ca = c.Qw + nw;
+    c.cb = c.ca + 32 * nw;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        c.sfac[4 * i] = fac[3 * i];
+        c.sfac[4 * i + 1] = fac[3 * i + 1];
+        c.sfac[4 * i + 2] = fac[3 * i + 2];
+        c.sfac[4 * i + 3] = TW(0);
+    }
+    __syncthreads();
+    const int s = (w * m) / nw, len = ((w + 1) * m) / nw - s;
+    if (lane == 0) {
+        TW pa = TW(1), pq = TW(1);
+        for (int j = 0; j < len; ++j) {
+            pa = -c.sfac[4 * (s + j)] * pa;
+            pq = -c.sfac[4 * (s + j) + 2] * pq;
+        }
+        c.Pw[w] = pa;
+        c.Qw[w] = pq;
+    }
+    __syncthreads();
+    return c;
+}
+
+// M_{l-1} z = f on chunk w of the 32 lines of a panel (lane = line): y holds
+// the chunk's right-hand sides (CH - 1 or CH of them: the last only when
+// `full`); on return it holds z.  Per sweep the chunk runs from a zero carry,
+// publishes its end value, composes the carries of the chunks before it and
+// re-runs from its true carry.  Two block barriers; the caller puts one more
+// between panels (the carries are reused).
+template <typename TW, int CH>
+__device__ __forceinline__ void chunk_solve_panel(TW (&y)[CH], const ChunkSmem<TW> &c, const TW *sf, bool full, int w,
+                                                  int nw, int lane)
+{
+    TW a, inv, q;
+    // forward y_i = f_i - a_i y_{i-1}: chunk-end value from a zero carry
+    TW t = TW(0);
+#pragma unroll
+    for (int j = 0; j < CH; ++j)
+        if (j < CH - 1 || full) {
+            solve_fac(sf + 4 * j, a, inv, q);
+            t = y[j] - a * t;
+        }
+    c.ca[w * 32 + lane] = t;
+    __syncthreads();
+    TW cr = TW(0);
+    for (int k = 0; k < w; ++k) cr = c.ca[k * 32 + lane] + c.Pw[k] * cr;
+    t = cr;
+#pragma unroll
+    for (int j = 0; j < CH; ++j)
+        if (j < CH - 1 || full) {
+            solve_fac(sf + 4 * j, a, inv, q);
+            t = y[j] - a * t;
+            y[j] = t;
+        }
+    // backward z_i = inv_i y_i - q_i z_{i+1}: chunk-start value from a zero carry
+    t = TW(0);
+#pragma unroll
+    for (int j = CH - 1; j >= 0; --j)
+        if (j < CH - 1 || full) {
+            solve_fac(sf + 4 * j, a, inv, q);
+            t = inv * y[j] - q * t;
+        }
+    c.cb[w * 32 + lane] = t;
+    __syncthreads();
+    cr = TW(0);
+    for (int k = nw - 1; k > w; --k) cr = c.cb[k * 32 + lane] + c.Qw[k] * cr;
+    t = cr;
+#pragma unroll
+    for (int j = CH - 1; j >= 0; --j)
+        if (j < CH - 1 || full) {
+            solve_fac(sf + 4 * j, a, inv, q);
+            t = inv * y[j] - q * t;
+            y[j] = t;
+        }
+}
+
 template <typename TW, int CH>
 __global__ void __launch_bounds__(32 * kSolveStridedWarps, StridedMinBlocks<TW, CH>::value) k_solve_strided(SolveParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int m = p.m;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    TW *sfac = reinterpret_cast<TW *>(smem_raw);  // (a, inv, q, 0) per node
-    TW *Pw = sfac + 4 * m;                         // per chunk: product of -a_i
-    TW *Qw = Pw + nw;                              // per chunk: product of -q_i
-    TW *ca = Qw + nw;                              // forward chunk-end values [nw][32]
-    TW *cb = ca + 32 * nw;                         // backward chunk-start values [nw][32]
-    const TW *fac = static_cast<const TW *>(p.fac);
+    const ChunkSmem<TW> cs = chunk_setup<TW>(smem_raw, static_cast<const TW *>(p.fac), m, w, nw, lane);
     TW *F = static_cast<TW *>(p.F);
     TW *V = static_cast<TW *>(p.V);
     const TW *in = p.src ? static_cast<const TW *>(p.src) : F;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        sfac[4 * i] = fac[3 * i];
-        sfac[4 * i + 1] = fac[3 * i + 1];
-        sfac[4 * i + 2] = fac[3 * i + 2];
-        sfac[4 * i + 3] = TW(0);
-    }
-    __syncthreads();
     const int s = (w * m) / nw, len = ((w + 1) * m) / nw - s;  // len is CH - 1 or CH
-    if (lane == 0) {
-        TW pa = TW(1), pq = TW(1);
-        for (int j = 0; j < len; ++j) {
-            pa = -sfac[4 * (s + j)] * pa;
-            pq = -sfac[4 * (s + j) + 2] * pq;
-        }
-        Pw[w] = pa;
-        Qw[w] = pq;
-    }
-    __syncthreads();
-    const TW *sf = sfac + 4 * s;
+    const TW *sf = cs.sfac + 4 * s;
     const bool full = (len == CH);  // the chunk's last register holds a node
     pdl_wait();  // the predecessor on the stream has finished with F and V
     // line -> first element: lines are (outer, inner) pairs, inner fastest;
@@ -502,47 +574,7 @@ __global__ void __launch_bounds__(32 * kSolveStridedWarps, StridedMinBlocks<TW, 
 #pragma unroll
             for (int j = 0; j < CH; ++j) vv[j] = (j < CH - 1 || full) ? vin[j * stride] : TW(0);
         }
-        TW a, inv, q;
-        // forward y_i = f_i - a_i y_{i-1}: chunk-end value from a zero carry
-        TW t = TW(0);
-#pragma unroll
-        for (int j = 0; j < CH; ++j)
-            if (j < CH - 1 || full) {
-                solve_fac(sf + 4 * j, a, inv, q);
-                t = y[j] - a * t;
-            }
-        ca[w * 32 + lane] = t;
-        __syncthreads();
-        TW c = TW(0);
-        for (int k = 0; k < w; ++k) c = ca[k * 32 + lane] + Pw[k] * c;
-        t = c;
-#pragma unroll
-        for (int j = 0; j < CH; ++j)
-            if (j < CH - 1 || full) {
-                solve_fac(sf + 4 * j, a, inv, q);
-                t = y[j] - a * t;
-                y[j] = t;
-            }
-        // backward z_i = inv_i y_i - q_i z_{i+1}: chunk-start value from a zero carry
-        t = TW(0);
-#pragma unroll
-        for (int j = CH - 1; j >= 0; --j)
-            if (j < CH - 1 || full) {
-                solve_fac(sf + 4 * j, a, inv, q);
-                t = inv * y[j] - q * t;
-            }
-        cb[w * 32 + lane] = t;
-        __syncthreads();
-        c = TW(0);
-        for (int k = nw - 1; k > w; --k) c = cb[k * 32 + lane] + Qw[k] * c;
-        t = c;
-#pragma unroll
-        for (int j = CH - 1; j >= 0; --j)
-            if (j < CH - 1 || full) {
-                solve_fac(sf + 4 * j, a, inv, q);
-                t = inv * y[j] - q * t;
-                y[j] = t;
-            }
+        chunk_solve_panel<TW, CH>(y, cs, sf, full, w, nw, lane);
         // z into F, or V +- z
         if (lv) {
             TW *dst = ((p.vmode == 0) ? F : V) + base;
