@@ -138,7 +138,7 @@ cudaError_t launch_solve_chunks(const SolveParams &p, int num_sms, cudaStream_t 
 template <typename TW>
 int solve_strided_shape(const SolveParams &p, int *nw_out)
 {
-    if (p.inner <= 1 || p.nlines >= (int64_t(1) << 31) || p.inner >= (int64_t(1) << 31) ||
+    if (p.inner < 1 || p.nlines >= (int64_t(1) << 31) || p.inner >= (int64_t(1) << 31) ||
         (int64_t)p.m * p.stride >= (int64_t(1) << 31) || (size_t)4 * p.m * sizeof(TW) > 100 * 1024)
         return 0;
     static const int chs[3] = {17, 33, 9};
@@ -153,12 +153,17 @@ int solve_strided_shape(const SolveParams &p, int *nw_out)
     return 0;
 }
 
+// contiguous lines (inner = 1): k_solve_rowpanel, else k_solve_strided
 template <typename TW>
 cudaError_t launch_solve_strided(const SolveParams &p, int ch, int nw, int num_sms, cudaStream_t st)
 {
-    void (*fn)(SolveParams) = (ch == 17) ? k_solve_strided<TW, 17>
-                                         : (ch == 33) ? k_solve_strided<TW, 33> : k_solve_strided<TW, 9>;
-    const size_t smem = solve_strided_elems<TW>(p.m, nw) * sizeof(TW);
+    const bool rows = (p.inner == 1);
+    void (*fn)(SolveParams);
+    if (rows)
+        fn = (ch == 17) ? k_solve_rowpanel<TW, 17> : (ch == 33) ? k_solve_rowpanel<TW, 33> : k_solve_rowpanel<TW, 9>;
+    else
+        fn = (ch == 17) ? k_solve_strided<TW, 17> : (ch == 33) ? k_solve_strided<TW, 33> : k_solve_strided<TW, 9>;
+    const size_t smem = (rows ? solve_rowpanel_elems<TW>(p.m, nw) : solve_strided_elems<TW>(p.m, nw)) * sizeof(TW);
     cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -187,10 +192,10 @@ cudaError_t launch_solve_lines(const SolveParams &p, int num_sms, cudaStream_t s
     return cudaGetLastError();
 }
 
-// nw_req = -1: k_solve_lines (one thread per line); nw_req = 0: along a
-// strided dimension k_solve_strided where a chunk length fits, along the
-// contiguous one k_solve_chunks for lines up to 576 nodes (the panel staged
-// in shared memory); else (or nw_req > 0) the shared-memory panel kernel with
+// nw_req = -1: k_solve_lines (one thread per line); nw_req = 0: where a
+// chunk length fits, k_solve_strided along a strided dimension and
+// k_solve_rowpanel along the contiguous one, else k_solve_chunks for lines
+// up to 576 nodes; else (or nw_req > 0) the shared-memory panel kernel with
 // nw_req warps (0: about 16 nodes per chunk).
 template <typename TW>
 cudaError_t launch_solve(const SolveParams &p_in, int nw_req, int num_sms, cudaStream_t st)
@@ -203,7 +208,9 @@ cudaError_t launch_solve(const SolveParams &p_in, int nw_req, int num_sms, cudaS
     if (nw_req == 0) {
         int snw = 0;
         const int sch = solve_strided_shape<TW>(p, &snw);
-        if (sch > 0) return launch_solve_strided<TW>(p, sch, snw, num_sms, st);
+        // contiguous lines: the two staged panels must fit beside the tables
+        const bool fits = p.inner > 1 || solve_rowpanel_elems<TW>(p.m, snw) * sizeof(TW) <= 110 * 1024;
+        if (sch > 0 && fits) return launch_solve_strided<TW>(p, sch, snw, num_sms, st);
     }
     if (nw_req == 0 && p.m <= 32 * kSolveChunkWarps && (int64_t)p.m * p.stride < (int64_t(1) << 31)) {
         const int ch = (p.m <= 16 * kSolveChunkWarps) ? 16 : 32;

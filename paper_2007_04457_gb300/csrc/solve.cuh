@@ -586,6 +586,84 @@ __global__ void __launch_bounds__(32 * kSolveStridedWarps, StridedMinBlocks<TW, 
     }
 }
 
+// k_solve_rowpanel: lines along the contiguous dimension.  A panel of 32
+// consecutive lines is one contiguous, 16-byte aligned block of 32 m
+// elements, staged with 16-byte cp.async copies into one of two buffers
+// while the block solves the panel in the other (pitch m, odd, so that the
+// lanes of a warp, one line each, read different banks); the chunked solve
+// is the one of k_solve_strided; z goes back into the buffer and out with
+// coalesced stores (z into F, or V +- z).
+template <typename TW>
+inline size_t solve_rowpanel_elems(int m, int nw)
+{
+    return solve_strided_elems<TW>(m, nw) + 4 + 2 * (size_t)((32 * m + 3) & ~3);
+}
+
+template <typename TW, int CH>
+__global__ void __launch_bounds__(32 * kSolveStridedWarps, StridedMinBlocks<TW, CH>::value) k_solve_rowpanel(SolveParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int m = p.m;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const ChunkSmem<TW> cs = chunk_setup<TW>(smem_raw, static_cast<const TW *>(p.fac), m, w, nw, lane);
+    TW *stg = reinterpret_cast<TW *>((reinterpret_cast<uintptr_t>(cs.cb + 32 * nw) + 15) & ~uintptr_t(15));
+    const int tpitch = (32 * m + 3) & ~3;
+    TW *F = static_cast<TW *>(p.F);
+    TW *V = static_cast<TW *>(p.V);
+    const TW *in = p.src ? static_cast<const TW *>(p.src) : F;
+    const int s = (w * m) / nw, len = ((w + 1) * m) / nw - s;  // len is CH - 1 or CH
+    const TW *sf = cs.sfac + 4 * s;
+    const bool full = (len == CH);
+    const int64_t nlines = p.nlines, npanels = (nlines + 31) / 32;
+    const TW sg = (p.vmode == 2) ? TW(-1) : TW(1);
+    auto lines_of = [&](int64_t panel) { return (int)min64(32, nlines - panel * 32); };
+    auto stage = [&](int64_t panel, int b) {
+        if (panel >= npanels) return;
+        const TW *src = in + panel * 32 * m;
+        TW *dst = stg + b * tpitch;
+        const int tot = lines_of(panel) * m;
+        constexpr int E = 16 / sizeof(TW);
+        const int nchunk = tot / E;
+        for (int c = tid; c < nchunk; c += nthr) cp_async16(dst + c * E, src + c * E);
+        for (int e = nchunk * E + tid; e < tot; e += nthr) cp_async_elem(dst + e, src + e, true);
+    };
+    pdl_wait();  // the predecessor on the stream has finished with F and V
+    int buf = 0;
+    stage(blockIdx.x, 0);
+    cp_async_commit();
+    for (int64_t panel = blockIdx.x; panel < npanels; panel += gridDim.x) {
+        stage(panel + gridDim.x, buf ^ 1);  // the next panel, in flight during this one
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const int nl = lines_of(panel);
+        TW *t = stg + buf * tpitch;
+        const TW *row = t + min(lane, nl - 1) * m + s;  // lanes past the end solve a copy of the last line
+        TW y[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) y[j] = (j < CH - 1 || full) ? row[j] : TW(0);
+        chunk_solve_panel<TW, CH>(y, cs, sf, full, w, nw, lane);
+        if (lane < nl) {
+            TW *rw = t + lane * m + s;
+#pragma unroll
+            for (int j = 0; j < CH; ++j)
+                if (j < CH - 1 || full) rw[j] = y[j];
+        }
+        __syncthreads();
+        const int64_t g0 = panel * 32 * (int64_t)m;
+        const int tot = nl * m;
+        if (p.vmode == 0) {
+            for (int e = tid; e < tot; e += nthr) F[g0 + e] = t[e];
+        } else {
+            for (int e = tid; e < tot; e += nthr) V[g0 + e] = V[g0 + e] + sg * t[e];
+        }
+        buf ^= 1;
+        __syncthreads();  // the buffer, the carries: reused by the next panel
+    }
+    cp_async_wait<0>();
+}
+
 // One thread per line: the Thomas recurrences of the tabulated LU factors
 // (forward y_i = f_i - a_i y_{i-1}, backward z_i = inv_i y_i - q_i z_{i+1}),
 // U nodes at a time with the next U prefetched into registers before the
