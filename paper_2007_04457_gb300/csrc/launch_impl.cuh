@@ -192,10 +192,11 @@ cudaError_t launch_solve_lines(const SolveParams &p, int num_sms, cudaStream_t s
     return cudaGetLastError();
 }
 
-// nw_req = -1: k_solve_lines (one thread per line); nw_req = 0: where a
-// chunk length fits, k_solve_strided along a strided dimension and
-// k_solve_rowpanel along the contiguous one, else k_solve_chunks for lines
-// up to 576 nodes; else (or nw_req > 0) the shared-memory panel kernel with
+// nw_req = -1: k_solve_lines (one thread per line); nw_req = 0: FP64
+// working arrays along the slowest dimension (or strided lines too long for
+// the register chunks) k_solve_lines, else where a chunk length fits
+// k_solve_strided along a strided dimension and k_solve_rowpanel along the
+// contiguous one, else k_solve_chunks for lines up to 576 nodes; else (or nw_req > 0) the shared-memory panel kernel with
 // nw_req warps (0: about 16 nodes per chunk).
 template <typename TW>
 cudaError_t launch_solve(const SolveParams &p_in, int nw_req, int num_sms, cudaStream_t st)
@@ -208,6 +209,16 @@ cudaError_t launch_solve(const SolveParams &p_in, int nw_req, int num_sms, cudaS
     if (nw_req == 0) {
         int snw = 0;
         const int sch = solve_strided_shape<TW>(p, &snw);
+        // FP64 working arrays are bound by the FP64 units, where the chunked
+        // kernels' second pass over every chunk costs: one thread per line
+        // (the least arithmetic) for the slowest dimension (nlines <= inner)
+        // when it has at least 128 lines per SM, and for strided lines too
+        // long for the register chunks (measured: 513^3 FP64 z solve 0.67 ->
+        // 0.45 ms per step, 1025^2 x 513 mixed step 16.5 -> 13.3 ms; with
+        // 16.6K lines the chunks stay faster, with 33K the lines)
+        const bool slowest = p.nlines <= p.inner && p.nlines >= (int64_t)(kSolveLinesPerSm / 2) * num_sms;
+        if (sizeof(TW) == 8 && lines_fit && p.inner > 1 && (slowest || sch == 0))
+            return launch_solve_lines<TW>(p, num_sms, st);
         // contiguous lines: the two staged panels must fit beside the tables
         const bool fits = p.inner > 1 || solve_rowpanel_elems<TW>(p.m, snw) * sizeof(TW) <= 110 * 1024;
         if (sch > 0 && fits) return launch_solve_strided<TW>(p, sch, snw, num_sms, st);
