@@ -152,11 +152,14 @@ MGARD_API mgard_status mgard_recompose_classes(const mgard_plan *plan, int nclas
  *            block, 3 = 8 x 30 (FP64: 4 x 30) per warp (levels with at least
  *            30 coarse columns and one strip of rows; the default where it
  *            applies)
- *   param 1  correction solves: 0 = automatic (one thread per line along a
- *            dimension whose stride exceeds its length when the level has at
- *            least 256 such lines per SM, else chunks of about 16 nodes per
- *            warp), -1 = one thread per line, 1..32 = that many warps
- *            (chunks) per line in the shared-memory panel kernel
+ *   param 1  correction solves: 0 = automatic (a warp per chunk of 9, 17
+ *            or 33 (FP32 only) nodes of every line, 32 lines across the
+ *            lanes, where a line splits evenly into at most 16 chunks; with FP64 working
+ *            arrays one thread per line instead along the slowest dimension
+ *            when it has at least 128 lines per SM and along strided
+ *            dimensions too long for those chunks; else chunks of about 16
+ *            nodes per warp), -1 = one thread per line, 1..32 = that many
+ *            warps (chunks) per line in the shared-memory panel kernel
  *   param 2  coarse planes per restriction work item (0 = automatic)
  *   param 3  plan-wide (any valid level): 0 = run the coarse end of the
  *            hierarchy in a single launch per direction (default); 1 = run

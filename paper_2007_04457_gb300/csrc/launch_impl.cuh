@@ -214,9 +214,9 @@ cudaError_t launch_solve(const SolveParams &p_in, int nw_req, int num_sms, cudaS
         // (the least arithmetic) for the slowest dimension (nlines <= inner)
         // when it has at least 128 lines per SM, and for strided lines too
         // long for the register chunks (measured: 513^3 FP64 z solve 0.67 ->
-        // 0.45 ms per step, 1025^2 x 513 mixed step 16.5 -> 13.3 ms; with
+        // 0.45 ms per step, 1025^2 x 513 mixed step 16.5 -> 13.2 ms; with
         // 16.6K lines the chunks stay faster, with 33K the lines)
-        const bool slowest = p.nlines <= p.inner && p.nlines >= (int64_t)(kSolveLinesPerSm / 2) * num_sms;
+        const bool slowest = p.nlines <= p.inner && p.nlines >= (int64_t)kSolveLinesPerSm * num_sms;
         if (sizeof(TW) == 8 && lines_fit && p.inner > 1 && (slowest || sch == 0))
             return launch_solve_lines<TW>(p, num_sms, st);
         // contiguous lines: the two staged panels must fit beside the tables

@@ -676,7 +676,7 @@ __global__ void __launch_bounds__(32 * kSolveStridedWarps, StridedMinBlocks<TW, 
 // pass reads src when given and writes y into F, the backward pass writes z
 // into F or V +- z into V.
 constexpr int kSolveLineThreads = 256;
-constexpr int kSolveLinesPerSm = 256;  // lines per SM from which one thread per line pays
+constexpr int kSolveLinesPerSm = 128;  // lines per SM from which one thread per line pays (FP64)
 
 template <typename TW>
 struct LineUnroll {
