@@ -808,7 +808,7 @@ def main():
         fn = {"restriction": ("k_slab" if mgard.mgard_plan_get_tune(plan.handle, 0, 12) > 0 else
                               "k_restrict_strip" if plan_tune_get(mgard, plan, 7) & 2 else "k_rc_restrict"),
               "coefficient sweep": "k_rc_sweep<MODE_DEC>", "interpolation sweep": "k_rc_sweep<MODE_REC>",
-              "solve x/y": "k_solve_chunks (x), k_solve_strided (y)", "solve z + correction": "k_solve_strided",
+              "solve x/y": "k_solve_rowpanel (x), k_solve_strided (y)", "solve z + correction": "k_solve_strided",
               "coarse placement": "k_scatter"}.get(name, name)
         roof = {"bound": "hbm", "kernel": f"{name} ({fn}, finest level, both directions)", "achieved": achieved,
                 "peak": peak, "peak_source": f"{peak_src} hbm_gbs", "unit": "GB/s",
