@@ -159,6 +159,8 @@ k_restrict(RestrictParams p)
         const int64_t X0 = (int64_t)tx * kRestrictTX;
         const int TYo = HY ? (ty == p.tiles_y - 1 ? (int)(m1 - Y0) : TY) : 1;
         const int TXo = (tx == p.tiles_x - 1) ? (int)(m2 - X0) : kRestrictTX;
+        const bool wide = TXo > kRestrictTX;  // a last tile with the 65th coarse column
+        const int NO = TYo * TXo;             // coarse nodes of the tile per plane
         const int RY = HY ? 2 * TYo + 3 : 1;
         const int64_t gy0 = HY ? 2 * Y0 - 2 : 0;   // fine row of slab row 0
         const int64_t gx0 = 2 * X0 - 4;            // fine column of slab column 0
@@ -226,6 +228,17 @@ k_restrict(RestrictParams p)
         T accP[PPT], accC[PPT], accN[PPT];
 #pragma unroll
         for (int i = 0; i < PPT; ++i) accP[i] = accC[i] = accN[i] = T(0);
+        // output slot i of this thread: coarse node pos = tid + i NT of the
+        // tile's TYo x TXo nodes, row-major (the same every step of the tile);
+        // slots run in order, so the first one past the tile ends the loop,
+        // and an interior 16 x 64 tile fills exactly four slots per thread
+        auto out_slot = [&](int i, int &Y, int &X) -> bool {
+            const int pos = tid + i * NT;
+            if (pos >= NO) return false;
+            Y = (TXo == kRestrictTX) ? (pos >> 6) : pos / TXo;
+            X = pos - Y * TXo;
+            return true;
+        };
 
         for (int64_t Z = Zfirst; Z <= Zlast; ++Z) {
             const int s = (int)((Z - Zfirst) & 1);
@@ -274,11 +287,17 @@ k_restrict(RestrictParams p)
                     if (L == 0) { cl2 = chl2; cl3 = chl1; }
                     const T crr = (L == 31) ? ch128 : cr0;
                     T ha, hb;
-                    stencil2(ka, kb, cl2, cl3, C, crr, ha, hb);
+                    if (ro) {
+                        stencil2(ka, kb, cl2, cl3, C, crr, ha, hb);
+                    } else {  // C[0], C[2], cl2, crr are 0: the nonzero taps only
+                        ha = fma_rn(ka[3], C[1], mul_rn(ka[1], cl3));
+                        hb = fma_rn(kb[3], C[3], mul_rn(kb[1], C[1]));
+                    }
                     T *hrow = He + r * HP;
                     hrow[2 * L] = ha;
                     hrow[2 * L + 1] = hb;
-                    if (L == 31) hrow[64] = fma_rn(kc[2], ch128, fma_rn(kc[0], C[2], mul_rn(kc[1], C[3])));
+                    if (wide && L == 31)
+                        hrow[64] = fma_rn(kc[2], ch128, fma_rn(kc[0], C[2], mul_rn(kc[1], C[3])));
                 }
                 // odd plane: every node is a coefficient node
                 if (has_odd) {
@@ -294,7 +313,8 @@ k_restrict(RestrictParams p)
                     T *hrow = Ho + r * HP;
                     hrow[2 * L] = ha;
                     hrow[2 * L + 1] = hb;
-                    if (L == 31) hrow[64] = fma_rn(kc[2], oh128, fma_rn(kc[0], v[2], mul_rn(kc[1], v[3])));
+                    if (wide && L == 31)
+                        hrow[64] = fma_rn(kc[2], oh128, fma_rn(kc[0], v[2], mul_rn(kc[1], v[3])));
                 }
             }
             __syncthreads();  // restricted rows complete; the slabs of this step are free
@@ -313,10 +333,8 @@ k_restrict(RestrictParams p)
             }
 #pragma unroll
             for (int i = 0; i < PPT; ++i) {
-                const int pos = tid + i * NT;
-                if (pos >= G::OUTS) break;
-                const int Y = pos / HP, X = pos - (pos / HP) * HP;
-                if (Y >= TYo || X >= TXo) continue;
+                int Y, X;
+                if (!out_slot(i, Y, X)) break;
                 T ge, go = T(0);
                 if constexpr (HY) {
                     const T *kk = sky + 5 * Y;
@@ -348,11 +366,9 @@ k_restrict(RestrictParams p)
                 if (Z - 1 >= Zs && Z - 1 < Ze) {
 #pragma unroll
                     for (int i = 0; i < PPT; ++i) {
-                        const int pos = tid + i * NT;
-                        if (pos >= G::OUTS) break;
-                        const int Y = pos / HP, X = pos - (pos / HP) * HP;
-                        if (Y < TYo && X < TXo)
-                            F[((Z - 1) * m1 + Y0 + Y) * m2 + X0 + X] = static_cast<TW>(accP[i]);
+                        int Y, X;
+                        if (!out_slot(i, Y, X)) break;
+                        F[((Z - 1) * m1 + Y0 + Y) * m2 + X0 + X] = static_cast<TW>(accP[i]);
                     }
                 }
 #pragma unroll
@@ -369,11 +385,9 @@ k_restrict(RestrictParams p)
         if (Zlast == Zend && Zend >= Zs && Zend < Ze) {
 #pragma unroll
             for (int i = 0; i < PPT; ++i) {
-                const int pos = tid + i * NT;
-                if (pos >= G::OUTS) break;
-                const int Y = pos / HP, X = pos - (pos / HP) * HP;
-                if (Y < TYo && X < TXo)
-                    F[(Zend * m1 + Y0 + Y) * m2 + X0 + X] = static_cast<TW>(HZ ? accP[i] : accC[i]);
+                int Y, X;
+                if (!out_slot(i, Y, X)) break;
+                F[(Zend * m1 + Y0 + Y) * m2 + X0 + X] = static_cast<TW>(HZ ? accP[i] : accC[i]);
             }
         }
         cp_async_wait<0>();
