@@ -241,14 +241,11 @@ cudaError_t launch_solve(const SolveParams &p_in, int nw_req, int num_sms, cudaS
     p.lpb = lpb;
     const bool reg = (p.chunk <= 16) && (nw <= kSolveRegWarps);
     void (*fn)(SolveParams) = reg ? k_solve_panel<TW, 16> : k_solve_panel<TW, 0>;
-    static bool attr_set[2] = {false, false};
-    const int which = reg ? 0 : 1;
-    if (!attr_set[which]) {
-        cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCap);
-        if (err != cudaSuccess) return err;
-        attr_set[which] = true;
-    }
+    // set on every call, like the other launchers: the attribute belongs to
+    // the current device, and a process may drive several
+    const cudaError_t err = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCap);
+    if (err != cudaSuccess) return err;
     const int64_t panels = (p.nlines + lpb - 1) / lpb;
     { const cudaError_t le = launch_pdl(fn, dim3((unsigned)std::min<int64_t>(panels, 1 << 30)), dim3(32, nw), smem, st, p); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
