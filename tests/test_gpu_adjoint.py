@@ -158,5 +158,5 @@ def test_loss_gradient_257_cubed_fp32_matches_oracle():
     loss.backward()
     got = u.grad.cpu().numpy().astype(np.float64)
     lref, want = _loss_oracle_grad(u32.astype(np.float64), m.astype(np.float64))
-    assert abs(float(loss) - lref) <= 1e-3 * lref
+    assert abs(float(loss.detach()) - lref) <= 1e-3 * lref
     assert _relerr(got, want) <= 1e-3, _relerr(got, want)

@@ -91,6 +91,7 @@ def test_noalloc_rejects_shape_beyond_scratch():
     assert _relerr(small, want) <= TOL["f32"]
 
 
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")  # nothing is queued: the refusal is the point
 def test_noalloc_refuses_stream_capture():
     """The call uploads its tables from host memory it frees on return, so it
     refuses a stream under capture before queueing anything; afterwards it
